@@ -1,0 +1,310 @@
+"""Benchmark of the encrypted FFT on GB300 (one JSON line on rank 0).
+
+Default workload: 1-D encrypted FFT, N = 64, 16-bit two's-complement fixed
+point (8 integer, 8 fraction bits), real inputs uniform in [-8, 8), imaginary
+part 0, one request, under the noisy leveled GSW parameters (n = 1,
+chi = 1, m = Ng, ell the smallest multiple of 32 whose static noise bound
+stays below q/4). One step = one evaluation of the whole FFT circuit on the
+device (every gate of every level), inputs resident in HBM.
+
+Keys in the JSON line beyond the base contract:
+  roofline      dominant kernel (the gate product) against the INT32 ALU peak
+  cpu_baseline  the CPU oracle on a bounded prefix of the same circuit
+  e2e           the same FFT through sfft_eval_fft_host (pinned host buffers,
+                H2D of the input ciphertexts and D2H of the outputs timed)
+  gates_per_s   ciphertext products per second
+Multi-GPU (torchrun): every rank runs an independent replica (the FFT of one
+request does not shard); value = FFTs/s summed over ranks.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# INT32 ALU peak of one GB300: 152 SMs x 128 INT32 lanes x 2.07 GHz (one
+# 32-bit add or logic op per lane per clock).
+SMS, INT_LANES, SM_MAX_GHZ = 152, 128, 2.070
+ALU_PEAK_OPS = SMS * INT_LANES * SM_MAX_GHZ * 1e9
+
+CONFIGS = {
+    # name: (N1, N2, F, f, lo, hi, params)
+    "fft64_16bit_noisy": (64, 1, 16, 8, -8.0, 8.0, "P1"),
+    "fft8_8bit_toy": (8, 1, 8, 4, -1.0, 1.0, "P0"),
+    "fft16x16_image_noisy": (16, 16, 16, 6, None, None, "P1"),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="fft64_16bit_noisy", choices=sorted(CONFIGS))
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="budget of the bounded oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi samples (SM clock, max clock, throttle reasons) during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                      "--format=csv,noheader,nounits"], capture_output=True,
+                                     text=True, timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4)
+                          if len(s) > 4 + k and s[4 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+def workload(cfg_name):
+    import paper_1611_08769_gb300 as sf
+    from synthetic import image_2d, signal_1d
+    N1, N2, F, f, lo, hi, pset = CONFIGS[cfg_name]
+    if pset == "P1":
+        ell = sf.min_ell(N1, N2, F, f, n=1, chi=1)
+        params = sf.param_set("P1", ell)
+    else:
+        params = sf.param_set(pset)
+    if N2 == 1:
+        re_, im_ = signal_1d(N1, lo, hi, seed=0)
+    else:
+        re_, im_ = image_2d(N1, N2, seed=0)
+    return params, (N1, N2, F, f), re_, im_
+
+
+def cpu_oracle_sample(params, dims, re_, im_, budget_s):
+    """Oracle on a bounded prefix of the circuit; returns (fft_per_s, detail)."""
+    from oracle import circuit, fixedpoint as fx, gsw
+    N1, N2, F, f = dims
+    p = gsw.Params(params.n, params.ell, params.m, params.chi)
+    c = circuit.fft_circuit(N1, N2, F, f)
+    keys = gsw.Keys(p, 0)
+    cts = {}
+    zero, one = gsw.zero_ct(p), gsw.one_ct(p)
+    need = set()
+    for op, a, b, o in c.gates:
+        need.add(a)
+        if b is not None:
+            need.add(b)
+
+    def get(w):
+        if w == circuit.ZERO:
+            return zero
+        if w == circuit.ONE:
+            return one
+        if w not in cts:   # inputs (wires 0 .. 2F N - 1) are encrypted on first use, untimed
+            k = w
+            sample, rem = divmod(k, 2 * F)
+            part, bit = divmod(rem, F)
+            x = re_[sample] if part == 0 else im_[sample]
+            cts[w] = gsw.encrypt(keys, fx.to_bits(fx.quantize(x, F, f), F)[bit], 0, k)
+        return cts[w]
+
+    done = 0
+    dt = 0.0
+    for op, a, b, o in c.gates:
+        A, B = (b, a) if (b is not None and c.d(b) > c.d(a)) else (a, b)
+        xa, xb = get(A), None if B is None else get(B)
+        t1 = time.perf_counter()
+        cts[o] = gsw.gate(p, xa, xb, gsw.GATE_CODES[op])
+        dt += time.perf_counter() - t1
+        done += 1
+        if dt > budget_s:
+            break
+    per_gate = dt / done
+    fft_s = per_gate * len(c.gates)
+    detail = (f"first {done} of {len(c.gates)} oracle gates (AND/XOR/OR/NOT, evaluated separately) "
+              f"of the same circuit and parameters, {dt:.1f} s; FFT time extrapolated "
+              f"{fft_s:.1f} s")
+    return 1.0 / fft_s, done / dt, detail
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    params, dims, re_, im_ = workload(args.config)
+    budget = max(1.0, args.cpu_seconds / max(1, args.steps + args.warmup))
+    vals = []
+    for s in range(args.warmup + args.steps):
+        fps, gps, detail = cpu_oracle_sample(params, dims, re_, im_, budget)
+        if s >= args.warmup:
+            vals.append(fps)
+    v = statistics.mean(vals)
+    N1, N2, F, f = dims
+    line = {"impl": "reference", "metric": "encrypted FFTs/s", "value": v, "unit": "FFT/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 / v, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": args.config, "N1": N1, "N2": N2, "F": F, "f": f,
+                       "n": params.n, "ell": params.ell, "m": params.m, "chi": params.chi},
+            "cpu_baseline": {"value": v, "unit": "FFT/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": detail},
+            "e2e": {"value": v, "unit": "FFT/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_1611_08769_gb300 as sf
+    from paper_1611_08769_gb300 import build as sfbuild
+
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    sfbuild.build()
+    params, dims, re_, im_ = workload(args.config)
+    N1, N2, F, f = dims
+    keys = sf.keygen(params, 0)
+    cw = sf.ct_words(params)
+    pub = torch.from_numpy(keys.public().view(np.int32)).cuda()
+    plan = sf.Plan(params, N1, N2, F, f)
+    info = plan.info
+    d_in = torch.empty((info["inputs"], cw), dtype=torch.int32, device="cuda")
+    sf.encrypt_bits_device(params, pub, re_, im_, F, f, 0, d_in)
+    d_out = torch.empty((info["outputs"], cw), dtype=torch.int32, device="cuda")
+    scratch = torch.empty(max(1, info["scratch_bytes"] // 4), dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        plan.eval_fft(d_in, d_out, scratch, stream)
+    torch.cuda.synchronize()
+
+    # device-timed region: inputs resident in HBM (larger than L2)
+    plan.set_timing(True)
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            plan.eval_fft(d_in, d_out, scratch, stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    gate_ms, launches, gates_timed = plan.timing()
+    plan.set_timing(False)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    fft_per_s = world * 1000.0 / ms
+
+    # end to end through the C ABI with host buffers (H2D in, D2H out, each step)
+    h_in = d_in.cpu().pin_memory()
+    h_out = torch.empty_like(d_out, device="cpu").pin_memory()
+    plan.eval_fft_host(h_in, h_out, d_in, d_out, scratch, stream)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        plan.eval_fft_host(h_in, h_out, d_in, d_out, scratch, stream)
+    e2e_ms = (time.perf_counter() - t0) * 1000.0 / args.steps
+    barrier()
+    if world > 1:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    # roofline of the gate kernel: limb adds per product = Ng^2 (n+1) L
+    Ng, L = (params.n + 1) * params.ell, params.ell // 32
+    ops_per_product = Ng * Ng * (params.n + 1) * L
+    avg_launch_ms = gate_ms / max(1, launches)
+    achieved = ops_per_product * gates_timed / (gate_ms / 1000.0) if gate_ms > 0 else 0.0
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        fps, gps, detail = cpu_oracle_sample(params, dims, re_, im_, args.cpu_seconds)
+        cpu = {"value": fps, "unit": "FFT/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": detail, "gates_per_s": gps}
+
+    if rank == 0:
+        line = {
+            "metric": "encrypted FFTs/s", "value": fft_per_s, "unit": "FFT/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic",
+            "config": {"workload": args.config, "N1": N1, "N2": N2, "F": F, "f": f,
+                       "n": params.n, "ell": params.ell, "m": params.m, "chi": params.chi,
+                       "products_per_fft": info["products"], "levels": info["levels"],
+                       "evaluator": "plain level-by-level",
+                       "l2": f"inputs {info['inputs'] * cw * 4 / 1e9:.2f} GB > L2 (129 MB)"},
+            "gates_per_s": fft_per_s * info["products"],
+            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": ALU_PEAK_OPS / 1e12,
+                         "unit": "Tops/s (32-bit limb adds)", "frac": achieved / ALU_PEAK_OPS,
+                         "traffic": None, "kernel": "k_gate_generic",
+                         "avg_launch_ms": avg_launch_ms,
+                         "peak_source": "derived: 152 SMs x 128 INT32 lanes x 2.07 GHz"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": world * 1000.0 / e2e_ms, "unit": "FFT/s",
+                    "h2d_bytes_per_step": info["inputs"] * cw * 4,
+                    "d2h_bytes_per_step": info["outputs"] * cw * 4},
+            "gpu_launches": args.steps * (info["levels"] + 1),
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,203 @@
+/*
+ * sfft.h -- C ABI of the GB300 encrypted-FFT library.
+ *
+ * The library evaluates the paper's secure FFT: a radix-2 FFT over
+ * bit-wise GSW-encrypted two's-complement fixed-point words, computed as a
+ * circuit of homomorphic gates (Sec. 4) on one GPU. The calls follow the
+ * paper's client/server workflow (Sec. 1, Fig. 1): key generation (step 1),
+ * encryption of the signal bit by bit (step 2), evaluation of the FFT on the
+ * server (step 4) and decryption (step 6).
+ *
+ * Conventions (every call):
+ *  - Returns SFFT_OK (0) or a negative SFFT_E* code; sfft_last_error() gives
+ *    a thread-local message for the last failure on the calling thread.
+ *  - Pointers named h_* are host memory, d_* are device memory on the
+ *    current CUDA device; neither is retained after the call returns.
+ *  - Opaque handles (sfft_keys, sfft_plan, sfft_batch, sfft_server) are
+ *    owned by the library and released with the matching *_free call.
+ *  - Scheme parameters: q = 2^ell with ell a multiple of 32; Ng = (n+1) ell.
+ *    A ciphertext is stored compressed, C' = BitDecomp^-1(C): Ng rows of
+ *    (n+1) elements of Z_q, each as L = ell/32 uint32 limbs, least
+ *    significant limb first, row-major -- sfft_ct_words() words in all.
+ *    Read as a little-endian bit string, row i is row i of the N x N binary
+ *    GSW matrix (Sec. 3; Sec. 7 gives the N^2 ciphertext size).
+ *  - Signals: sample k of a signal occupies ciphertexts (2k + part) * F + b
+ *    for part 0 (real) / 1 (imaginary) and bit b = 0 .. F-1 (LSB first).
+ *    2-D signals are N1 x N2 images, sample k = r * N2 + c.
+ *  - Arithmetic wraps mod 2^F (two's complement); overflow is not an error.
+ *  - Device calls are asynchronous on the given CUDA stream (NULL = legacy
+ *    default stream) unless stated otherwise.
+ */
+#ifndef SFFT_H
+#define SFFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  SFFT_OK = 0,
+  SFFT_EINVAL = -1,   /* bad argument (null pointer, size, non power of two) */
+  SFFT_ENOMEM = -2,   /* host or device allocation failed / budget exceeded */
+  SFFT_ECUDA = -3,    /* a CUDA call failed */
+  SFFT_ETIMEOUT = -4, /* a bounded wait ran out */
+  SFFT_EPARAM = -5,   /* parameters unsupported or inconsistent (n, ell, F, f) */
+  SFFT_EBUSY = -6,    /* resource in use */
+  SFFT_ENOTFOUND = -7 /* unknown ticket */
+};
+
+/* GSW'13 parameters (Sec. 3 names the scheme but not its parameters).
+ * n: LWE dimension; ell: log2 q (multiple of 32); m: rows of the public key
+ * (the device paths need m == Ng); chi: error bound, e uniform in [-chi, chi]
+ * (0 = noise-free toy parameters). */
+typedef struct sfft_params {
+  uint32_t n, ell, m, chi;
+} sfft_params;
+
+typedef struct sfft_keys sfft_keys;
+typedef struct sfft_plan sfft_plan;
+typedef struct sfft_batch sfft_batch;
+typedef struct sfft_server sfft_server;
+
+const char* sfft_last_error(void);
+const char* sfft_version(void);
+
+/* Words (uint32) of one compressed ciphertext: Ng * (n+1) * ell/32. */
+uint64_t sfft_ct_words(const sfft_params* p);
+
+/* ---------------------------------------------------------------- client */
+
+/* Step 1, KeyGen (GSW'13 Sec. 3): t <- Z_q^n, s = (1, -t), B <- Z_q^{m x n},
+ * e <- [-chi, chi]^m, A = [B t + e | B]. All randomness is the counter-based
+ * SplitMix64 stream of ``seed`` (domains t = 1, B = 2, e = 3). Host only. */
+int sfft_keygen(const sfft_params* p, uint64_t seed, sfft_keys** out);
+void sfft_keys_free(sfft_keys* k);
+
+/* Copies the public matrix A (m x (n+1) elements, limb layout as a
+ * ciphertext) to h_out (cap_words >= m*(n+1)*ell/32). */
+int sfft_keys_public(const sfft_keys* k, uint32_t* h_out, uint64_t cap_words);
+
+/* Step 2, Enc of a fixed-point signal (Sec. 4 fixed point; Sec. 5
+ * truncation): raw = floor(x * 2^f) mod 2^F for every sample, then every
+ * bit mu is encrypted as C' = R A + mu P (mod q), R the Ng x m binary matrix
+ * drawn from stream domain 4 for ciphertext index (2k + part) * F + b.
+ * h_im may be NULL (imaginary part 0). Writes count*2*F ciphertexts to
+ * h_ct_out (host). CPU implementation, for small parameters. */
+int sfft_encrypt_bits(const sfft_keys* k, const double* h_re, const double* h_im,
+                      uint64_t count, uint32_t F, uint32_t f, uint64_t enc_seed,
+                      uint32_t* h_ct_out);
+
+/* Same ciphertexts, computed on the GPU (requires m == Ng): d_pub is the
+ * public matrix on the device (layout of sfft_keys_public), d_ct_out receives
+ * count*2*F ciphertexts. The R bits are generated inside the kernel. */
+int sfft_encrypt_bits_device(const sfft_params* p, const uint32_t* d_pub,
+                             const double* h_re, const double* h_im, uint64_t count,
+                             uint32_t F, uint32_t f, uint64_t enc_seed,
+                             uint32_t* d_ct_out, void* stream);
+
+/* Step 6, Dec (GSW'13; Lemma 2): x = <C'_{ell-1}, s> mod q, bit = [q/4 <= x
+ * < 3q/4], words reassembled LSB first, value = signed word / 2^f.
+ * h_rows points at row ell-1 of ciphertext 0; ciphertext j's row is
+ * row_stride_words further on (row_stride_words = sfft_ct_words for a
+ * packed ciphertext array, (n+1)*ell/32 for rows gathered by
+ * sfft_gather_dec_rows). Writes count values to h_re / h_im (either may be
+ * NULL) and the raw signed words to h_raw (NULL ok; 2*count entries,
+ * re/im interleaved). Host only. */
+int sfft_decrypt(const sfft_keys* k, const uint32_t* h_rows, uint64_t row_stride_words,
+                 uint64_t count, uint32_t F, uint32_t f, double* h_re, double* h_im,
+                 int64_t* h_raw);
+
+/* Copies row ell-1 of each of n_ct device ciphertexts into d_rows (n_ct rows
+ * of (n+1)*ell/32 words): what a client needs to decrypt. */
+int sfft_gather_dec_rows(const sfft_params* p, const uint32_t* d_ct, uint64_t n_ct,
+                         uint32_t* d_rows, void* stream);
+
+/* ------------------------------------------------------------- circuits */
+
+/* Smallest ell (multiple of 32, <= 8192) for which the static worst-case
+ * noise bound of the FFT circuit stays below q/4 with m = Ng and error bound
+ * chi (the leveled reading of the scheme's noise management; Sec. 5 ends by
+ * pointing at refreshing). 0 if none. */
+uint32_t sfft_min_ell(uint32_t N1, uint32_t N2, uint32_t F, uint32_t f, uint32_t n,
+                      uint32_t chi);
+
+typedef struct sfft_plan_info {
+  uint64_t inputs, outputs;     /* ciphertexts in / out */
+  uint64_t gates_and, gates_xor, gates_or, gates_not; /* logical gates after folding */
+  uint64_t products;            /* ciphertext products (one per HA, AND, XOR, OR) */
+  uint64_t levels;              /* multiplicative depth = launches of the plain evaluator */
+  uint64_t max_level_width;     /* products in the widest level */
+  uint64_t scratch_slots;       /* ciphertext slots of scratch needed by sfft_eval_fft */
+  uint64_t scratch_bytes;
+  uint64_t ct_words;
+  uint32_t noise_bits;          /* bit length of the largest wire noise bound */
+  uint32_t noise_ok;            /* bound < q/4 */
+} sfft_plan_info;
+
+/* Builds the canonical gate circuit of a 1-D (N2 == 1) or row-column 2-D FFT
+ * of F-bit words with f fraction bits (Sec. 4: bit reversal, butterflies of
+ * fixed-point Wallace constant multipliers and ripple adders/subtractors;
+ * Lemmas 3-9), levelises it (all products of one multiplicative depth form a
+ * level) and uploads its gate descriptors to the device. Fails with EPARAM
+ * if the static noise bound reaches q/4. flags: SFFT_PLAN_* below. */
+#define SFFT_PLAN_ALLOW_NOISY 1u   /* build even if the noise bound fails */
+int sfft_plan_create(const sfft_params* p, uint32_t N1, uint32_t N2, uint32_t F, uint32_t f,
+                     uint32_t flags, sfft_plan** out);
+int sfft_plan_info_get(const sfft_plan* plan, sfft_plan_info* info);
+void sfft_plan_free(sfft_plan* plan);
+
+/* Step 4 on the server, plain level-by-level form: one kernel launch per
+ * level, every product of the level evaluated in parallel. d_in holds
+ * info.inputs ciphertexts, d_out receives info.outputs; d_scratch holds at
+ * least info.scratch_bytes (caller-allocated, contents undefined on entry).
+ * Device pointers must be 16-byte aligned. */
+int sfft_eval_fft(sfft_plan* plan, const uint32_t* d_in, uint32_t* d_out,
+                  uint32_t* d_scratch, uint64_t scratch_bytes, void* stream);
+
+/* Same, end to end from host buffers: copies h_in to d_in, evaluates, copies
+ * d_out to h_out and waits for the stream. Pinned host memory is fastest. */
+int sfft_eval_fft_host(sfft_plan* plan, const uint32_t* h_in, uint32_t* h_out,
+                       uint32_t* d_in, uint32_t* d_out, uint32_t* d_scratch,
+                       uint64_t scratch_bytes, void* stream);
+
+/* Host-only statistics of the compiled circuit (no device memory touched):
+ * fills every field of sfft_plan_info as sfft_plan_create would. */
+int sfft_circuit_info(const sfft_params* p, uint32_t N1, uint32_t N2, uint32_t F, uint32_t f,
+                      sfft_plan_info* info);
+
+/* Host-only plaintext run of the compiled device program (test hook): the
+ * same levels, scratch slots, output fix-ups and adjusted gate coefficients
+ * as the device evaluator, applied to bits (A~ = 1 - a when complemented;
+ * out = c0 + c1 a + c2 b + c3 A~ b). h_in_bits: info.inputs bytes (0/1),
+ * h_out_bits: info.outputs bytes. */
+int sfft_program_eval_plain(const sfft_params* p, uint32_t N1, uint32_t N2, uint32_t F,
+                            uint32_t f, const uint8_t* h_in_bits, uint8_t* h_out_bits);
+
+/* Kernel timing: when on, CUDA events are recorded on the launching stream
+ * around every gate-kernel launch of sfft_eval_fft*. sfft_plan_timing waits
+ * for them, returns the summed gate-kernel milliseconds, the number of
+ * gate-kernel launches and the products they evaluated since the last read,
+ * then resets. */
+int sfft_plan_set_timing(sfft_plan* plan, int on);
+int sfft_plan_timing(sfft_plan* plan, double* gate_ms, uint64_t* launches, uint64_t* products);
+
+/* Evaluates a single level of gates given explicitly (test hook): gate g
+ * computes, with A = d_a[g] (complemented to P - A first when
+ * (flags[g] & 1)) and B = d_b[g],
+ *   d_out0[g] = c0 P + c1 A + c2 B + c3 BitDecomp(A) B    (code0 = c0..c3)
+ *   d_out1[g] likewise with code1 when flags[g] & 2.
+ * d_a/d_b/d_out0/d_out1 are arrays of n_gates ciphertexts; codes are 4
+ * signed nibbles c0 | c1 << 4 | c2 << 8 | c3 << 12 (two's complement). */
+int sfft_gate_level(const sfft_params* p, const uint32_t* d_a, const uint32_t* d_b,
+                    uint32_t* d_out0, uint32_t* d_out1, const uint16_t* h_code0,
+                    const uint16_t* h_code1, const uint8_t* h_flags, uint64_t n_gates,
+                    void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SFFT_H */

@@ -287,12 +287,26 @@ def stats(c):
     s = {"NOT": 0, "AND": 0, "XOR": 0, "OR": 0}
     for op, *_ in c.gates:
         s[op] += 1
-    # an HA's XOR and AND share one product when their operands are the same pair
+    # One product per distinct (kind, A, B) after value numbering: an HA's XOR
+    # and AND share it, and identical gates (e.g. the repeated sign-extension
+    # columns of a Wallace tree) compute identical ciphertexts. A wire's value
+    # number is (base wire, complemented?) so that NOT(NOT x) is x.
+    canon = {ZERO: (ZERO, 0), ONE: (ZERO, 1)}
+    for w in c.inputs:
+        canon[w] = (w, 0)
+    seen = {}
     pairs = set()
-    for op, a, b, _ in c.gates:
-        if op != "NOT":
-            A, B = (b, a) if c.d(b) > c.d(a) else (a, b)
-            pairs.add((A, B))
+    for op, a, b, o in c.gates:
+        if op == "NOT":
+            base, neg = canon[a]
+            canon[o] = (base, 1 - neg)
+            continue
+        A, B = (b, a) if c.d(b) > c.d(a) else (a, b)
+        key = (op, canon[A], canon[B])
+        if key not in seen:
+            seen[key] = (o, 0)
+        canon[o] = seen[key]
+        pairs.add(("OR" if op == "OR" else "HA", canon[A], canon[B]))
     s["products"] = len(pairs)
-    s["depth"] = max(c.depth) if c.depth else 0
+    s["depth"] = max((c.depth[o] for _, _, _, o in c.gates), default=0)
     return s

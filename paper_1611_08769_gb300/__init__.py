@@ -1,0 +1,205 @@
+"""GB300-native encrypted FFT (GSW'13 gate circuits on sm_103a).
+
+Thin Python binding over the C ABI in ``include/sfft.h``; every step of the
+computation runs in the native library's CUDA kernels. PyTorch supplies
+device memory and streams only.
+
+Client calls (host): ``keygen``, ``encrypt_bits``, ``decrypt``.
+Server calls (device): ``Plan`` (``sfft_plan_create``) with ``eval_fft`` /
+``eval_fft_host``, ``encrypt_bits_device``, ``gather_dec_rows``,
+``gate_level`` (single-level test hook).
+"""
+import ctypes
+
+import numpy as np
+
+from . import native
+from .native import SfftError, check, lib, sfft_params, sfft_plan_info
+
+PLAN_ALLOW_NOISY = 1
+
+__all__ = ["Params", "Keys", "Plan", "keygen", "encrypt_bits", "encrypt_bits_device", "decrypt",
+           "gather_dec_rows", "min_ell", "gate_level", "ct_words", "SfftError", "version"]
+
+PARAM_SETS = {
+    # toy, noise-free (chi = 0): exact decryption at any depth; insecure by construction
+    "P0": (1, 32, 64, 0),
+    # noise-free multi-limb throughput set
+    "P2": (1, 128, 256, 0),
+}
+
+
+def Params(n, ell, m=None, chi=0):
+    """GSW parameters; m defaults to Ng = (n+1) ell."""
+    return sfft_params(n, ell, (n + 1) * ell if m is None else m, chi)
+
+
+def param_set(name, ell=None):
+    """'P0', 'P2', or 'P1' (chi = 1, m = Ng, ell given -- see min_ell)."""
+    if name == "P1":
+        return Params(1, ell, None, 1)
+    n, e, m, chi = PARAM_SETS[name]
+    return Params(n, e, m, chi)
+
+
+def version():
+    return lib().sfft_version().decode()
+
+
+def ct_words(p):
+    return int(lib().sfft_ct_words(ctypes.byref(p)))
+
+
+def _dptr(t):
+    return ctypes.c_void_p(0 if t is None else int(t.data_ptr()))
+
+
+def _stream(stream):
+    if stream is None:
+        return ctypes.c_void_p(0)
+    return ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class Keys:
+    """Secret/public key pair of one client (host-owned)."""
+
+    def __init__(self, params, seed):
+        self.params = params
+        h = ctypes.c_void_p()
+        check(lib().sfft_keygen(ctypes.byref(params), seed, ctypes.byref(h)))
+        self._h = h
+
+    def public(self):
+        p = self.params
+        out = np.zeros(p.m * (p.n + 1) * (p.ell // 32), dtype=np.uint32)
+        check(lib().sfft_keys_public(self._h, out.ctypes.data_as(native.c_u32_p), out.size))
+        return out
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            lib().sfft_keys_free(h)
+            self._h = None
+
+
+def keygen(params, seed):
+    return Keys(params, seed)
+
+
+def encrypt_bits(keys, re, im, F, f, enc_seed):
+    """Host encryption of a fixed-point signal -> uint32 array (2 F count, ct_words)."""
+    re = _f64(re)
+    im = None if im is None else _f64(im)
+    cw = ct_words(keys.params)
+    out = np.zeros((len(re) * 2 * F, cw), dtype=np.uint32)
+    check(lib().sfft_encrypt_bits(keys._h, re.ctypes.data_as(native.c_double_p),
+                                  None if im is None else im.ctypes.data_as(native.c_double_p),
+                                  len(re), F, f, enc_seed, out.ctypes.data_as(native.c_u32_p)))
+    return out
+
+
+def encrypt_bits_device(params, d_pub, re, im, F, f, enc_seed, d_out, stream=None):
+    """GPU encryption into the device tensor d_out (2 F count ciphertexts)."""
+    re = _f64(re)
+    im = None if im is None else _f64(im)
+    check(lib().sfft_encrypt_bits_device(
+        ctypes.byref(params), _dptr(d_pub), re.ctypes.data_as(native.c_double_p),
+        None if im is None else im.ctypes.data_as(native.c_double_p), len(re), F, f, enc_seed,
+        _dptr(d_out), _stream(stream)))
+
+
+def decrypt(keys, rows, row_stride_words, count, F, f):
+    """Host decryption; returns (re, im, raw) numpy arrays."""
+    rows = np.ascontiguousarray(rows, dtype=np.uint32)
+    re = np.zeros(count)
+    im = np.zeros(count)
+    raw = np.zeros(2 * count, dtype=np.int64)
+    check(lib().sfft_decrypt(keys._h, rows.ctypes.data_as(native.c_u32_p), row_stride_words,
+                             count, F, f, re.ctypes.data_as(native.c_double_p),
+                             im.ctypes.data_as(native.c_double_p), raw.ctypes.data_as(native.c_i64_p)))
+    return re, im, raw
+
+
+def gather_dec_rows(params, d_ct, n_ct, d_rows, stream=None):
+    check(lib().sfft_gather_dec_rows(ctypes.byref(params), _dptr(d_ct), n_ct, _dptr(d_rows),
+                                     _stream(stream)))
+
+
+def min_ell(N1, N2, F, f, n=1, chi=1):
+    return int(lib().sfft_min_ell(N1, N2, F, f, n, chi))
+
+
+def circuit_info(params, N1, N2, F, f):
+    """Host-only statistics of the compiled FFT circuit (sfft_circuit_info)."""
+    info = sfft_plan_info()
+    check(lib().sfft_circuit_info(ctypes.byref(params), N1, N2, F, f, ctypes.byref(info)))
+    return {k: getattr(info, k) for k, _ in sfft_plan_info._fields_}
+
+
+def program_eval_plain(params, N1, N2, F, f, in_bits):
+    """Host-only plaintext run of the compiled device program (sfft_program_eval_plain)."""
+    in_bits = np.ascontiguousarray(in_bits, dtype=np.uint8)
+    out = np.zeros(len(in_bits), dtype=np.uint8)
+    check(lib().sfft_program_eval_plain(ctypes.byref(params), N1, N2, F, f,
+                                        in_bits.ctypes.data_as(native.c_u8_p),
+                                        out.ctypes.data_as(native.c_u8_p)))
+    return out
+
+
+class Plan:
+    """Compiled FFT circuit resident on the device (sfft_plan_create)."""
+
+    def __init__(self, params, N1, N2, F, f, flags=0):
+        self.params = params
+        self.N1, self.N2, self.F, self.f = N1, N2, F, f
+        h = ctypes.c_void_p()
+        check(lib().sfft_plan_create(ctypes.byref(params), N1, N2, F, f, flags, ctypes.byref(h)))
+        self._h = h
+        info = sfft_plan_info()
+        check(lib().sfft_plan_info_get(h, ctypes.byref(info)))
+        self.info = {k: getattr(info, k) for k, _ in sfft_plan_info._fields_}
+
+    def eval_fft(self, d_in, d_out, d_scratch, stream=None):
+        nbytes = 0 if d_scratch is None else d_scratch.numel() * d_scratch.element_size()
+        check(lib().sfft_eval_fft(self._h, _dptr(d_in), _dptr(d_out), _dptr(d_scratch), nbytes,
+                                  _stream(stream)))
+
+    def eval_fft_host(self, h_in, h_out, d_in, d_out, d_scratch, stream=None):
+        nbytes = 0 if d_scratch is None else d_scratch.numel() * d_scratch.element_size()
+        check(lib().sfft_eval_fft_host(self._h, _dptr(h_in), _dptr(h_out), _dptr(d_in),
+                                       _dptr(d_out), _dptr(d_scratch), nbytes, _stream(stream)))
+
+    def set_timing(self, on):
+        check(lib().sfft_plan_set_timing(self._h, 1 if on else 0))
+
+    def timing(self):
+        """(gate-kernel ms, launches, products) since the last read."""
+        ms = ctypes.c_double()
+        n = ctypes.c_uint64()
+        g = ctypes.c_uint64()
+        check(lib().sfft_plan_timing(self._h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(g)))
+        return ms.value, n.value, g.value
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            lib().sfft_plan_free(h)
+            self._h = None
+
+
+def gate_level(params, d_a, d_b, d_out0, d_out1, code0, code1, flags, stream=None):
+    code0 = np.ascontiguousarray(code0, dtype=np.uint16)
+    code1 = np.ascontiguousarray(code1, dtype=np.uint16)
+    flags = np.ascontiguousarray(flags, dtype=np.uint8)
+    check(lib().sfft_gate_level(ctypes.byref(params), _dptr(d_a), _dptr(d_b), _dptr(d_out0),
+                                _dptr(d_out1), code0.ctypes.data_as(native.c_u16_p),
+                                code1.ctypes.data_as(native.c_u16_p),
+                                flags.ctypes.data_as(native.c_u8_p), len(code0), _stream(stream)))
+
+
+def pack_code(c0, c1, c2, c3):
+    return (c0 & 15) | ((c1 & 15) << 4) | ((c2 & 15) << 8) | ((c3 & 15) << 12)

@@ -1,0 +1,355 @@
+// C ABI: FFT plans and the plain level-by-level evaluator, device encryption,
+// the single-level gate hook and decryption-row gathering.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "common.h"
+#include "kernels.cuh"
+#include "netlist.h"
+#include "plan.h"
+#include "scheme.h"
+
+namespace sfft {
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(SFFT_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+int upload(const void* h, size_t bytes, void** d) {
+  *d = nullptr;
+  if (bytes == 0) return SFFT_OK;
+  cudaError_t e = cudaMalloc(d, bytes);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+  e = cudaMemcpy(*d, h, bytes, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy");
+  return SFFT_OK;
+}
+
+KArgs make_args(const Shape& s) {
+  KArgs a{};
+  a.Ng = s.Ng;
+  a.W = s.W;
+  a.L = s.L;
+  a.ell = s.ell;
+  a.ctw = s.ctw;
+  return a;
+}
+
+// Launches one level of gates with the integer kernel.
+int launch_gates(const KArgs& a, cudaStream_t st) {
+  if (a.n == 0) return SFFT_OK;
+  const uint64_t tasks = a.n * (a.Ng / 32);
+  const uint64_t blocks = (tasks * 32 + 255) / 256;
+  if (a.W <= 2)
+    k_gate_generic<2><<<(unsigned)blocks, 256, 0, st>>>(a);
+  else if (a.W <= 4)
+    k_gate_generic<4><<<(unsigned)blocks, 256, 0, st>>>(a);
+  else
+    k_gate_generic<8><<<(unsigned)blocks, 256, 0, st>>>(a);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SFFT_OK : cuda_fail(e, "gate kernel launch");
+}
+
+cudaEvent_t Timer::next() {
+  if (used == pool.size()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    pool.push_back(e);
+  }
+  return pool[used++];
+}
+
+double Timer::drain_ms() {
+  double ms = 0;
+  for (size_t k = 0; k + 1 < used; k += 2) {
+    cudaEventSynchronize(pool[k + 1]);
+    float t = 0;
+    cudaEventElapsedTime(&t, pool[k], pool[k + 1]);
+    ms += t;
+  }
+  used = 0;
+  return ms;
+}
+
+Timer::~Timer() {
+  for (cudaEvent_t e : pool) cudaEventDestroy(e);
+}
+
+int run_program(const Shape& s, const DeviceProgram& dp, const uint32_t* d_in, uint32_t* d_out,
+                uint32_t* d_scratch, uint64_t scratch_bytes, cudaStream_t st, Timer* tm) {
+  if (!d_in || !d_out) return fail(SFFT_EINVAL, "null buffer");
+  if (scratch_bytes < dp.scratch_slots * s.ctw * 4 || (dp.scratch_slots && !d_scratch))
+    return fail(SFFT_EINVAL, "scratch buffer too small");
+  KArgs a = make_args(s);
+  a.base[REG_SCRATCH] = d_scratch;
+  a.base[REG_IN] = const_cast<uint32_t*>(d_in);
+  a.base[REG_OUT] = d_out;
+  a.base[REG_GEN] = nullptr;
+  for (size_t l = 0; l + 1 < dp.level_off.size(); l++) {
+    a.desc = dp.desc + dp.level_off[l];
+    a.aux = dp.aux + dp.level_off[l];
+    a.n = dp.level_off[l + 1] - dp.level_off[l];
+    const bool timed = tm && tm->on && a.n;
+    if (timed) cudaEventRecord(tm->next(), st);
+    int rc = launch_gates(a, st);
+    if (rc) return rc;
+    if (timed) {
+      cudaEventRecord(tm->next(), st);
+      tm->launches++;
+      tm->products += a.n;
+    }
+  }
+  if (dp.n_fix) {
+    k_fixup<<<(unsigned)dp.n_fix, 256, 0, st>>>(dp.fix, dp.n_fix, a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "fixup launch");
+  }
+  return SFFT_OK;
+}
+
+int make_device_program(const Program& p, DeviceProgram* dp) {
+  int rc;
+  void* ptr;
+  if ((rc = upload(p.desc.data(), p.desc.size() * sizeof(GateDesc), &ptr))) return rc;
+  dp->desc = (GateDesc*)ptr;
+  if ((rc = upload(p.aux.data(), p.aux.size() * sizeof(GateAux), &ptr))) return rc;
+  dp->aux = (GateAux*)ptr;
+  if ((rc = upload(p.fix.data(), p.fix.size() * sizeof(FixDesc), &ptr))) return rc;
+  dp->fix = (FixDesc*)ptr;
+  dp->n_fix = p.fix.size();
+  dp->level_off = p.level_off;
+  dp->scratch_slots = p.scratch_slots;
+  return SFFT_OK;
+}
+
+void free_device_program(DeviceProgram* dp) {
+  cudaFree(dp->desc);
+  cudaFree(dp->aux);
+  cudaFree(dp->fix);
+  dp->desc = nullptr;
+  dp->aux = nullptr;
+  dp->fix = nullptr;
+}
+
+}  // namespace sfft
+
+struct sfft_plan {
+  sfft::Shape s;
+  sfft::Circuit circuit;
+  sfft::Program prog;
+  sfft::DeviceProgram dev;
+  sfft::Timer timer;
+  uint32_t N1, N2, F, f;
+};
+
+using namespace sfft;
+
+extern "C" {
+
+const char* sfft_version(void) { return "sfft-gb300 0.1 (sm_103a)"; }
+
+uint32_t sfft_min_ell(uint32_t N1, uint32_t N2, uint32_t F, uint32_t f, uint32_t n, uint32_t chi) {
+  Circuit c;
+  if (!build_fft(&c, N1, N2, F, f)) return 0;
+  for (uint32_t ell = 32; ell <= 8192; ell += 32) {
+    sfft_params p{n, ell, (n + 1) * ell, chi};
+    Shape s;
+    if (make_shape(&p, &s, false)) return 0;
+    if (noise_bits(c, s) <= ell - 2) return ell;
+  }
+  return 0;
+}
+
+int sfft_plan_create(const sfft_params* p, uint32_t N1, uint32_t N2, uint32_t F, uint32_t f,
+                     uint32_t flags, sfft_plan** out) {
+  if (!out) return fail(SFFT_EINVAL, "out is NULL");
+  *out = nullptr;
+  std::unique_ptr<sfft_plan> pl(new (std::nothrow) sfft_plan);
+  if (!pl) return fail(SFFT_ENOMEM, "host allocation failed");
+  int rc = make_shape(p, &pl->s, false);
+  if (rc) return rc;
+  if (!build_fft(&pl->circuit, N1, N2, F, f))
+    return fail(SFFT_EINVAL, "N1, N2 must be powers of two, 2 <= F <= 48, f < F");
+  compile(pl->circuit, pl->s, &pl->prog);
+  if (!pl->prog.noise_ok && !(flags & SFFT_PLAN_ALLOW_NOISY))
+    return fail(SFFT_EPARAM, "static noise bound reaches q/4: raise ell (see sfft_min_ell)");
+  if ((rc = make_device_program(pl->prog, &pl->dev))) {
+    free_device_program(&pl->dev);
+    return rc;
+  }
+  pl->N1 = N1;
+  pl->N2 = N2;
+  pl->F = F;
+  pl->f = f;
+  *out = pl.release();
+  return SFFT_OK;
+}
+
+int sfft_plan_info_get(const sfft_plan* pl, sfft_plan_info* info) {
+  if (!pl || !info) return fail(SFFT_EINVAL, "null argument");
+  std::memset(info, 0, sizeof(*info));
+  info->inputs = pl->prog.n_inputs;
+  info->outputs = pl->prog.n_outputs;
+  info->gates_and = pl->circuit.n_and;
+  info->gates_xor = pl->circuit.n_xor;
+  info->gates_or = pl->circuit.n_or;
+  info->gates_not = pl->circuit.n_not;
+  info->products = pl->prog.products;
+  info->levels = pl->prog.level_off.size() - 1;
+  info->max_level_width = pl->prog.max_width;
+  info->scratch_slots = pl->prog.scratch_slots;
+  info->scratch_bytes = pl->prog.scratch_slots * pl->s.ctw * 4;
+  info->ct_words = pl->s.ctw;
+  info->noise_bits = pl->prog.noise_bits;
+  info->noise_ok = pl->prog.noise_ok ? 1 : 0;
+  return SFFT_OK;
+}
+
+void sfft_plan_free(sfft_plan* pl) {
+  if (!pl) return;
+  free_device_program(&pl->dev);
+  delete pl;
+}
+
+int sfft_eval_fft(sfft_plan* pl, const uint32_t* d_in, uint32_t* d_out, uint32_t* d_scratch,
+                  uint64_t scratch_bytes, void* stream) {
+  if (!pl) return fail(SFFT_EINVAL, "plan is NULL");
+  return run_program(pl->s, pl->dev, d_in, d_out, d_scratch, scratch_bytes, (cudaStream_t)stream,
+                     &pl->timer);
+}
+
+int sfft_plan_set_timing(sfft_plan* pl, int on) {
+  if (!pl) return fail(SFFT_EINVAL, "plan is NULL");
+  pl->timer.drain_ms();
+  pl->timer.on = on != 0;
+  pl->timer.launches = pl->timer.products = 0;
+  return SFFT_OK;
+}
+
+int sfft_plan_timing(sfft_plan* pl, double* gate_ms, uint64_t* launches, uint64_t* products) {
+  if (!pl) return fail(SFFT_EINVAL, "plan is NULL");
+  double ms = pl->timer.drain_ms();
+  if (gate_ms) *gate_ms = ms;
+  if (launches) *launches = pl->timer.launches;
+  if (products) *products = pl->timer.products;
+  pl->timer.launches = pl->timer.products = 0;
+  return SFFT_OK;
+}
+
+int sfft_eval_fft_host(sfft_plan* pl, const uint32_t* h_in, uint32_t* h_out, uint32_t* d_in,
+                       uint32_t* d_out, uint32_t* d_scratch, uint64_t scratch_bytes,
+                       void* stream) {
+  if (!pl || !h_in || !h_out) return fail(SFFT_EINVAL, "null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  const uint64_t in_b = pl->prog.n_inputs * pl->s.ctw * 4, out_b = pl->prog.n_outputs * pl->s.ctw * 4;
+  cudaError_t e = cudaMemcpyAsync(d_in, h_in, in_b, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "H2D copy");
+  int rc = run_program(pl->s, pl->dev, d_in, d_out, d_scratch, scratch_bytes, st, &pl->timer);
+  if (rc) return rc;
+  e = cudaMemcpyAsync(h_out, d_out, out_b, cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return cuda_fail(e, "D2H copy");
+  e = cudaStreamSynchronize(st);
+  return e == cudaSuccess ? SFFT_OK : cuda_fail(e, "stream sync");
+}
+
+int sfft_gate_level(const sfft_params* p, const uint32_t* d_a, const uint32_t* d_b,
+                    uint32_t* d_out0, uint32_t* d_out1, const uint16_t* h_code0,
+                    const uint16_t* h_code1, const uint8_t* h_flags, uint64_t n_gates,
+                    void* stream) {
+  Shape s;
+  int rc = make_shape(p, &s, false);
+  if (rc) return rc;
+  if (!d_a || !d_b || !d_out0 || !h_code0 || !h_flags) return fail(SFFT_EINVAL, "null argument");
+  if (n_gates == 0) return SFFT_OK;
+  std::vector<GateDesc> desc(n_gates);
+  std::vector<GateAux> aux(n_gates);
+  for (uint64_t g = 0; g < n_gates; g++) {
+    const bool two = (h_flags[g] & 2) && d_out1;
+    desc[g] = GateDesc{make_ref(REG_SCRATCH, (uint32_t)g), make_ref(REG_IN, (uint32_t)g),
+                       make_ref(REG_OUT, (uint32_t)g), two ? make_ref(REG_GEN, (uint32_t)g) : REF_NONE};
+    aux[g].code = (uint32_t)h_code0[g] | ((uint32_t)(two ? h_code1[g] : 0) << 16);
+    aux[g].flags = h_flags[g] & 1u;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  void *dd = nullptr, *da = nullptr;
+  if ((rc = upload(desc.data(), desc.size() * sizeof(GateDesc), &dd))) return rc;
+  if ((rc = upload(aux.data(), aux.size() * sizeof(GateAux), &da))) {
+    cudaFree(dd);
+    return rc;
+  }
+  KArgs a = make_args(s);
+  a.desc = (const GateDesc*)dd;
+  a.aux = (const GateAux*)da;
+  a.n = n_gates;
+  a.base[REG_SCRATCH] = const_cast<uint32_t*>(d_a);
+  a.base[REG_IN] = const_cast<uint32_t*>(d_b);
+  a.base[REG_OUT] = d_out0;
+  a.base[REG_GEN] = d_out1;  // region 3 is only an output here, never operand A
+  rc = launch_gates(a, st);
+  cudaError_t e = cudaStreamSynchronize(st);
+  cudaFree(dd);
+  cudaFree(da);
+  if (rc) return rc;
+  return e == cudaSuccess ? SFFT_OK : cuda_fail(e, "gate level");
+}
+
+int sfft_encrypt_bits_device(const sfft_params* p, const uint32_t* d_pub, const double* h_re,
+                             const double* h_im, uint64_t count, uint32_t F, uint32_t f,
+                             uint64_t enc_seed, uint32_t* d_ct_out, void* stream) {
+  Shape s;
+  int rc = make_shape(p, &s, true);
+  if (rc) return rc;
+  if (!d_pub || !h_re || !d_ct_out) return fail(SFFT_EINVAL, "null argument");
+  if (F < 2 || F > 48 || f >= F) return fail(SFFT_EPARAM, "need 2 <= F <= 48 and f < F");
+  std::vector<uint8_t> bits;
+  encode_signal(h_re, h_im, count, F, f, &bits);
+  const uint64_t n = bits.size();
+  std::vector<GateDesc> desc(n);
+  std::vector<GateAux> aux(n);
+  for (uint64_t c = 0; c < n; c++) {
+    desc[c] = GateDesc{make_ref(REG_GEN, (uint32_t)c), make_ref(REG_IN, 0),
+                       make_ref(REG_OUT, (uint32_t)c), REF_NONE};
+    aux[c].code = pack_code(bits[c], 0, 0, 1);   // mu P + BitDecomp(R) A
+    aux[c].flags = 0;
+  }
+  void *dd = nullptr, *da = nullptr;
+  if ((rc = upload(desc.data(), n * sizeof(GateDesc), &dd))) return rc;
+  if ((rc = upload(aux.data(), n * sizeof(GateAux), &da))) {
+    cudaFree(dd);
+    return rc;
+  }
+  KArgs a = make_args(s);
+  a.desc = (const GateDesc*)dd;
+  a.aux = (const GateAux*)da;
+  a.n = n;
+  a.base[REG_IN] = const_cast<uint32_t*>(d_pub);
+  a.base[REG_OUT] = d_ct_out;
+  a.gen_state = domain_key(enc_seed, kDomR);
+  cudaStream_t st = (cudaStream_t)stream;
+  rc = launch_gates(a, st);
+  cudaError_t e = cudaStreamSynchronize(st);
+  cudaFree(dd);
+  cudaFree(da);
+  if (rc) return rc;
+  return e == cudaSuccess ? SFFT_OK : cuda_fail(e, "device encryption");
+}
+
+int sfft_gather_dec_rows(const sfft_params* p, const uint32_t* d_ct, uint64_t n_ct,
+                         uint32_t* d_rows, void* stream) {
+  Shape s;
+  int rc = make_shape(p, &s, false);
+  if (rc) return rc;
+  if (!d_ct || !d_rows) return fail(SFFT_EINVAL, "null argument");
+  if (n_ct == 0) return SFFT_OK;
+  const uint64_t t = n_ct * s.W;
+  k_gather_rows<<<(unsigned)((t + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+      d_ct, n_ct, s.ctw, s.W, s.ell - 1, d_rows);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SFFT_OK : cuda_fail(e, "gather rows");
+}
+
+}  // extern "C"

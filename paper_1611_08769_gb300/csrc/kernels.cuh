@@ -1,0 +1,159 @@
+// Device kernels of the level evaluator (integer path).
+//
+// A level is a list of independent ciphertext products (Sec. 7: a NAND in
+// GSW is an N x N matrix product; Sec. 4 composes every other gate from it).
+// Each gate computes, on compressed ciphertexts,
+//     out = c0 P + c1 A + c2 B + c3 BitDecomp(A~) B   (mod 2^ell, per element)
+// with A~ = A or P - A. Row i of BitDecomp(A~) is simply the bit string of
+// row i of A~, so the product is a masked sum of B's rows:
+//     K[i][w] = sum_k bit_k(A~_i) * B[k][w]   (w = word column, no carries yet)
+// accumulated exactly in 64-bit per 32-bit limb, then carried limb by limb
+// inside each Z_q element (the top carry is dropped: mod q = 2^ell).
+#pragma once
+
+#include <cstdint>
+
+#include "common.h"
+#include "rng.h"
+
+namespace sfft {
+
+struct KArgs {
+  const GateDesc* desc;
+  const GateAux* aux;
+  uint64_t n;            // gates in this launch
+  uint32_t* base[4];     // region bases (region 3 = generated R for operand A)
+  uint64_t gen_state;    // domain key of the generated R matrices
+  uint32_t Ng, W, L, ell;
+  uint64_t ctw;
+};
+
+__device__ __forceinline__ uint32_t* resolve(const KArgs& a, uint32_t ref) {
+  return a.base[ref >> 30] + (uint64_t)(ref & SLOT_MASK) * a.ctw;
+}
+
+// Limb `l` of element `j` of row `i` of the gadget matrix P.
+__device__ __forceinline__ uint32_t p_word(uint32_t i, uint32_t j, uint32_t l, uint32_t ell) {
+  return (j == i / ell && l == (i % ell) / 32) ? (1u << (i % 32)) : 0u;
+}
+
+__device__ __forceinline__ int nib(uint32_t code, int k) {
+  return (int)((int32_t)(code << (28 - 4 * k)) >> 28);
+}
+
+// One warp per (gate, 32-row tile); lane = row. CC word columns at a time.
+template <int CC>
+__global__ void __launch_bounds__(256) k_gate_generic(KArgs a) {
+  const uint32_t tiles = a.Ng / 32;
+  const uint64_t task = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (task >= a.n * tiles) return;
+  const uint64_t g = task / tiles;
+  const uint32_t i = (uint32_t)(task % tiles) * 32 + (threadIdx.x & 31);
+  const GateDesc d = a.desc[g];
+  const GateAux x = a.aux[g];
+  const bool gen = (d.a >> 30) == REG_GEN;
+  const uint32_t* A = gen ? nullptr : resolve(a, d.a);
+  const uint64_t gst = gen ? stream_out(a.gen_state, d.a & SLOT_MASK) : 0;
+  const uint32_t* B = resolve(a, d.b);
+  uint32_t* O0 = d.o0 == REF_NONE ? nullptr : resolve(a, d.o0);
+  uint32_t* O1 = d.o1 == REF_NONE ? nullptr : resolve(a, d.o1);
+  const bool comp = (x.flags & 1u) != 0;
+  const uint32_t W = a.W, L = a.L;
+  const uint32_t* Arow = A ? A + (uint64_t)i * W : nullptr;
+  int64_t carry0 = 0, carry1 = 0;
+  for (uint32_t c0 = 0; c0 < W; c0 += CC) {
+    uint64_t acc[CC];
+#pragma unroll
+    for (int c = 0; c < CC; c++) acc[c] = 0;
+    uint32_t borrow = 0;
+    for (uint32_t kw = 0; kw < W; kw++) {
+      uint32_t aw = gen ? r_word(gst, (uint64_t)i * W + kw) : __ldg(Arow + kw);
+      if (comp) {  // (P - A) with a borrow chain inside each element
+        const uint32_t l = kw % L;
+        if (l == 0) borrow = 0;
+        const uint32_t pw = p_word(i, kw / L, l, a.ell);
+        const uint64_t v = (uint64_t)pw - aw - borrow;
+        aw = (uint32_t)v;
+        borrow = (uint32_t)(v >> 63);
+      }
+      const uint32_t* brow = B + (uint64_t)kw * 32 * W + c0;
+#pragma unroll 4
+      for (uint32_t b = 0; b < 32; b++) {
+        const uint32_t m = 0u - ((aw >> b) & 1u);
+        const uint32_t* br = brow + (uint64_t)b * W;
+#pragma unroll
+        for (int c = 0; c < CC; c++)
+          if (c0 + c < W) acc[c] += (uint64_t)(__ldg(br + c) & m);
+      }
+    }
+    // epilogue: linear terms and carries, limb by limb inside each element
+    const uint32_t code0 = x.code & 0xFFFFu, code1 = x.code >> 16;
+#pragma unroll
+    for (int c = 0; c < CC; c++) {
+      const uint32_t w = c0 + c;
+      if (w >= W) break;
+      const uint32_t l = w % L;
+      if (l == 0) carry0 = carry1 = 0;
+      const int64_t aw = A ? (int64_t)__ldg(Arow + w) : 0;
+      const int64_t bw = (int64_t)__ldg(B + (uint64_t)i * W + w);
+      const int64_t pw = (int64_t)p_word(i, w / L, l, a.ell);
+      const int64_t k = (int64_t)acc[c];
+      if (O0) {
+        int64_t v = nib(code0, 3) * k + nib(code0, 1) * aw + nib(code0, 2) * bw +
+                    nib(code0, 0) * pw + carry0;
+        O0[(uint64_t)i * W + w] = (uint32_t)v;
+        carry0 = v >> 32;
+      }
+      if (O1) {
+        int64_t v = nib(code1, 3) * k + nib(code1, 1) * aw + nib(code1, 2) * bw +
+                    nib(code1, 0) * pw + carry1;
+        O1[(uint64_t)i * W + w] = (uint32_t)v;
+        carry1 = v >> 32;
+      }
+    }
+  }
+}
+
+// Output fix-ups: kind 0 copy, 1 P - src, 2 zero, 3 P. One block per fix-up,
+// one thread per (row, element).
+__global__ void k_fixup(const FixDesc* fix, uint64_t n, KArgs a) {
+  const uint64_t f = blockIdx.x;
+  if (f >= n) return;
+  const FixDesc d = fix[f];
+  uint32_t* dst = a.base[REG_OUT] + (uint64_t)d.dst * a.ctw;
+  const uint32_t* src = (d.kind <= 1) ? resolve(a, d.src) : nullptr;
+  const uint32_t NP1 = a.W / a.L;
+  for (uint32_t t = threadIdx.x; t < a.Ng * NP1; t += blockDim.x) {
+    const uint32_t i = t / NP1, j = t % NP1;
+    uint32_t borrow = 0;
+    for (uint32_t l = 0; l < a.L; l++) {
+      const uint64_t off = (uint64_t)i * a.W + j * a.L + l;
+      const uint32_t pw = p_word(i, j, l, a.ell);
+      uint32_t v;
+      if (d.kind == 0) {
+        v = src[off];
+      } else if (d.kind == 1) {
+        const uint64_t r = (uint64_t)pw - src[off] - borrow;
+        v = (uint32_t)r;
+        borrow = (uint32_t)(r >> 63);
+      } else if (d.kind == 2) {
+        v = 0;
+      } else {
+        v = pw;
+      }
+      dst[off] = v;
+    }
+  }
+}
+
+// Row ell-1 of each ciphertext (what decryption reads).
+__global__ void k_gather_rows(const uint32_t* ct, uint64_t n, uint64_t ctw, uint32_t W,
+                              uint32_t row, uint32_t* out) {
+  const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * W) return;
+  const uint64_t c = t / W;
+  const uint32_t w = (uint32_t)(t % W);
+  out[t] = ct[c * ctw + (uint64_t)row * W + w];
+}
+
+}  // namespace sfft

@@ -1,0 +1,516 @@
+// Canonical FFT gate circuit, levelisation, slot allocation, noise bound.
+#include "netlist.h"
+
+#include <algorithm>
+#include <cmath>
+
+namespace sfft {
+
+// ------------------------------------------------------------------ circuit
+
+uint32_t Circuit::new_node(uint32_t d, int32_t prod) {
+  if (depth.empty()) {  // node 0: the constant zero
+    depth.push_back(0);
+    producer.push_back(-1);
+  }
+  depth.push_back(d);
+  producer.push_back(prod);
+  return (uint32_t)depth.size() - 1;
+}
+
+uint32_t Circuit::new_input() {
+  uint32_t n = new_node(0, -1);
+  inputs.push_back(n);
+  return n;
+}
+
+Sig Circuit::NOT(Sig a) {
+  if (sig_node(a) != 0) n_not++;
+  return a ^ SIG_ONE;
+}
+
+void Circuit::HA(Sig a, Sig b, Sig* s, Sig* c) {
+  bool ca = sig_node(a) == 0, cb = sig_node(b) == 0;
+  if (ca && cb) {
+    bool va = sig_neg(a), vb = sig_neg(b);
+    *s = (va != vb) ? SIG_ONE : SIG_ZERO;
+    *c = (va && vb) ? SIG_ONE : SIG_ZERO;
+    return;
+  }
+  if (ca || cb) {  // XOR(x,0)=x, XOR(x,1)=NOT x, AND(x,0)=0, AND(x,1)=x
+    Sig x = ca ? b : a;
+    bool k = sig_neg(ca ? a : b);
+    *s = k ? NOT(x) : x;
+    *c = k ? x : SIG_ZERO;
+    return;
+  }
+  uint32_t d = 1 + std::max(dep(a), dep(b));
+  Product p;
+  if (dep(b) > dep(a)) {
+    p.a = b;
+    p.b = a;
+  } else {
+    p.a = a;
+    p.b = b;
+  }
+  p.is_or = false;
+  const uint64_t key = ((uint64_t)p.a << 32) | p.b;
+  auto hit = memo_ha.find(key);
+  if (hit != memo_ha.end()) {
+    *s = products[hit->second].out_xor;
+    *c = products[hit->second].out_and;
+    return;
+  }
+  int32_t id = (int32_t)products.size();
+  memo_ha[key] = id;
+  products.push_back(p);
+  uint32_t ns = new_node(d, id);
+  uint32_t nc = new_node(d, id);
+  products[id].out_xor = ns;
+  products[id].out_and = nc;
+  n_xor++;
+  n_and++;
+  *s = ns;
+  *c = nc;
+}
+
+Sig Circuit::OR(Sig a, Sig b) {
+  if (a == SIG_ONE || b == SIG_ONE) return SIG_ONE;
+  if (a == SIG_ZERO) return b;
+  if (b == SIG_ZERO) return a;
+  uint32_t d = 1 + std::max(dep(a), dep(b));
+  Product p;
+  if (dep(b) > dep(a)) {
+    p.a = b;
+    p.b = a;
+  } else {
+    p.a = a;
+    p.b = b;
+  }
+  p.is_or = true;
+  p.out_and = 0;
+  const uint64_t key = ((uint64_t)p.a << 32) | p.b;
+  auto hit = memo_or.find(key);
+  if (hit != memo_or.end()) return products[hit->second].out_xor;
+  int32_t id = (int32_t)products.size();
+  memo_or[key] = id;
+  products.push_back(p);
+  uint32_t n = new_node(d, id);
+  products[id].out_xor = n;
+  n_or++;
+  return n;
+}
+
+void Circuit::FA(Sig a, Sig b, Sig c, Sig* s, Sig* co) {
+  Sig s1, c1, c2;
+  HA(a, b, &s1, &c1);
+  HA(s1, c, s, &c2);
+  *co = OR(c1, c2);
+}
+
+std::vector<Sig> Circuit::ADD(const std::vector<Sig>& x, const std::vector<Sig>& y, Sig cin) {
+  size_t F = x.size();
+  std::vector<Sig> out(F);
+  Sig carry;
+  if (cin == SIG_ZERO)
+    HA(x[0], y[0], &out[0], &carry);
+  else
+    FA(x[0], y[0], cin, &out[0], &carry);
+  for (size_t i = 1; i < F; i++) FA(x[i], y[i], carry, &out[i], &carry);
+  return out;  // carry out of the top bit is dropped (wrap mod 2^F)
+}
+
+std::vector<Sig> Circuit::SUB(const std::vector<Sig>& x, const std::vector<Sig>& y) {
+  std::vector<Sig> ny(y.size());
+  for (size_t i = 0; i < y.size(); i++) ny[i] = NOT(y[i]);
+  return ADD(x, ny, SIG_ONE);
+}
+
+std::vector<Sig> Circuit::MUL(const std::vector<Sig>& x, int64_t w, uint32_t f) {
+  const uint32_t F = (uint32_t)x.size();
+  const uint32_t T = f + F;
+  std::vector<Sig> xe(T);
+  for (uint32_t j = 0; j < T; j++) xe[j] = x[std::min(j, F - 1)];
+  const uint64_t wb = (uint64_t)w & (T >= 64 ? ~0ull : ((1ull << T) - 1));
+  std::vector<std::vector<Sig>> col(T);
+  for (uint32_t i = 0; i < T; i++)
+    if ((wb >> i) & 1)
+      for (uint32_t c = i; c < T; c++) col[c].push_back(xe[c - i]);
+  auto tallest = [&]() {
+    size_t h = 0;
+    for (auto& v : col) h = std::max(h, v.size());
+    return h;
+  };
+  while (tallest() > 2) {
+    std::vector<std::vector<Sig>> sums(T), carries(T + 1);
+    std::vector<Sig> pass(T, 0);
+    std::vector<bool> has_pass(T, false);
+    for (uint32_t c = 0; c < T; c++) {
+      const auto& L = col[c];
+      size_t g = 0;
+      while (L.size() - g >= 3) {
+        Sig s, cy;
+        FA(L[g], L[g + 1], L[g + 2], &s, &cy);
+        sums[c].push_back(s);
+        carries[c + 1].push_back(cy);
+        g += 3;
+      }
+      if (L.size() - g == 2) {
+        Sig s, cy;
+        HA(L[g], L[g + 1], &s, &cy);
+        sums[c].push_back(s);
+        carries[c + 1].push_back(cy);
+      } else if (L.size() - g == 1) {
+        pass[c] = L[g];
+        has_pass[c] = true;
+      }
+    }
+    for (uint32_t c = 0; c < T; c++) {
+      std::vector<Sig> nc = sums[c];
+      if (has_pass[c]) nc.push_back(pass[c]);
+      nc.insert(nc.end(), carries[c].begin(), carries[c].end());
+      col[c] = nc;
+    }
+  }
+  std::vector<Sig> r0(T), r1(T);
+  for (uint32_t c = 0; c < T; c++) {
+    r0[c] = col[c].size() >= 1 ? col[c][0] : SIG_ZERO;
+    r1[c] = col[c].size() >= 2 ? col[c][1] : SIG_ZERO;
+  }
+  std::vector<Sig> prod = ADD(r0, r1, SIG_ZERO);
+  return std::vector<Sig>(prod.begin() + f, prod.begin() + f + F);
+}
+
+void twiddles(uint32_t N, uint32_t f, std::vector<int64_t>* wr, std::vector<int64_t>* wi) {
+  wr->clear();
+  wi->clear();
+  const double pi = 3.14159265358979323846;
+  for (uint32_t k = 0; k < N / 2; k++) {
+    double ang = 2.0 * pi * (double)k / (double)N;
+    wr->push_back((int64_t)std::floor(std::cos(ang) * (double)(1ull << f)));
+    wi->push_back((int64_t)std::floor(-std::sin(ang) * (double)(1ull << f)));
+  }
+}
+
+namespace {
+
+using Word = std::vector<Sig>;
+using Cplx = std::pair<Word, Word>;
+
+uint32_t bitrev(uint32_t i, uint32_t bits) {
+  uint32_t r = 0;
+  for (uint32_t b = 0; b < bits; b++) {
+    r = (r << 1) | (i & 1);
+    i >>= 1;
+  }
+  return r;
+}
+
+void butterfly(Circuit* c, Cplx* u, Cplx* x, int64_t wr, int64_t wi, uint32_t f) {
+  Word tr = c->SUB(c->MUL(x->first, wr, f), c->MUL(x->second, wi, f));
+  Word ti = c->ADD(c->MUL(x->second, wr, f), c->MUL(x->first, wi, f), SIG_ZERO);
+  Word top_r = c->ADD(u->first, tr, SIG_ZERO);
+  Word top_i = c->ADD(u->second, ti, SIG_ZERO);
+  Word bot_r = c->SUB(u->first, tr);
+  Word bot_i = c->SUB(u->second, ti);
+  *u = Cplx(top_r, top_i);
+  *x = Cplx(bot_r, bot_i);
+}
+
+std::vector<Cplx> fft(Circuit* c, const std::vector<Cplx>& in, uint32_t f) {
+  const uint32_t N = (uint32_t)in.size();
+  uint32_t logN = 0;
+  while ((1u << logN) < N) logN++;
+  std::vector<int64_t> wr, wi;
+  twiddles(N, f, &wr, &wi);
+  std::vector<Cplx> a(N);
+  for (uint32_t i = 0; i < N; i++) a[i] = in[bitrev(i, logN)];
+  for (uint32_t m = 2; m <= N; m *= 2) {
+    uint32_t h = m / 2;
+    for (uint32_t k = 0; k < N; k += m)
+      for (uint32_t j = 0; j < h; j++) {
+        uint32_t t = j * (N / m);
+        butterfly(c, &a[k + j], &a[k + j + h], wr[t], wi[t], f);
+      }
+  }
+  return a;
+}
+
+bool pow2(uint32_t n) { return n >= 1 && (n & (n - 1)) == 0; }
+
+}  // namespace
+
+bool build_fft(Circuit* c, uint32_t N1, uint32_t N2, uint32_t F, uint32_t f) {
+  if (!pow2(N1) || !pow2(N2) || F < 2 || F > 48 || f >= F) return false;
+  const uint32_t count = N1 * N2;
+  std::vector<Cplx> s(count);
+  for (uint32_t k = 0; k < count; k++) {
+    Word re(F), im(F);
+    for (uint32_t b = 0; b < F; b++) re[b] = c->new_input();
+    for (uint32_t b = 0; b < F; b++) im[b] = c->new_input();
+    s[k] = Cplx(re, im);
+  }
+  std::vector<Cplx> out;
+  if (N2 == 1) {
+    out = N1 > 1 ? fft(c, s, f) : s;
+  } else {
+    std::vector<Cplx> grid(count);
+    for (uint32_t r = 0; r < N1; r++) {
+      std::vector<Cplx> row(s.begin() + r * N2, s.begin() + (r + 1) * N2);
+      std::vector<Cplx> res = fft(c, row, f);
+      for (uint32_t j = 0; j < N2; j++) grid[r * N2 + j] = res[j];
+    }
+    out = grid;
+    if (N1 > 1)
+      for (uint32_t col = 0; col < N2; col++) {
+        std::vector<Cplx> v(N1);
+        for (uint32_t r = 0; r < N1; r++) v[r] = grid[r * N2 + col];
+        std::vector<Cplx> res = fft(c, v, f);
+        for (uint32_t r = 0; r < N1; r++) out[r * N2 + col] = res[r];
+      }
+  }
+  for (auto& z : out) {
+    c->outputs.insert(c->outputs.end(), z.first.begin(), z.first.end());
+    c->outputs.insert(c->outputs.end(), z.second.begin(), z.second.end());
+  }
+  return true;
+}
+
+// ------------------------------------------------------------ noise bound
+
+namespace {
+
+// Minimal non-negative big integer: little-endian base 2^32.
+struct Big {
+  std::vector<uint32_t> d;
+  static Big of(uint64_t v) {
+    Big b;
+    while (v) {
+      b.d.push_back((uint32_t)v);
+      v >>= 32;
+    }
+    return b;
+  }
+  Big mul(uint64_t k) const {  // k < 2^32
+    Big r;
+    uint64_t carry = 0;
+    for (uint32_t x : d) {
+      uint64_t t = (uint64_t)x * k + carry;
+      r.d.push_back((uint32_t)t);
+      carry = t >> 32;
+    }
+    while (carry) {
+      r.d.push_back((uint32_t)carry);
+      carry >>= 32;
+    }
+    r.trim();
+    return r;
+  }
+  Big add(const Big& o) const {
+    Big r;
+    uint64_t carry = 0;
+    size_t n = std::max(d.size(), o.d.size());
+    for (size_t i = 0; i < n; i++) {
+      uint64_t t = carry + (i < d.size() ? d[i] : 0) + (i < o.d.size() ? o.d[i] : 0);
+      r.d.push_back((uint32_t)t);
+      carry = t >> 32;
+    }
+    if (carry) r.d.push_back((uint32_t)carry);
+    r.trim();
+    return r;
+  }
+  void trim() {
+    while (!d.empty() && d.back() == 0) d.pop_back();
+  }
+  uint32_t bits() const {
+    if (d.empty()) return 0;
+    uint32_t top = d.back(), b = 0;
+    while (top) {
+      b++;
+      top >>= 1;
+    }
+    return (uint32_t)(d.size() - 1) * 32 + b;
+  }
+};
+
+struct Code {
+  int c0, c1, c2, c3;
+};
+constexpr Code kXor = {0, 1, 1, -2};
+constexpr Code kAnd = {0, 0, 0, 1};
+constexpr Code kOr = {0, 1, 1, -1};
+
+// Liveness: which products and nodes reach an output.
+void liveness(const Circuit& c, std::vector<char>* live_node, std::vector<char>* live_prod) {
+  live_node->assign(c.depth.size(), 0);
+  live_prod->assign(c.products.size(), 0);
+  for (Sig s : c.outputs) (*live_node)[sig_node(s)] = 1;
+  for (int64_t p = (int64_t)c.products.size() - 1; p >= 0; p--) {
+    const Product& g = c.products[p];
+    bool l = (g.out_xor && (*live_node)[g.out_xor]) || (g.out_and && (*live_node)[g.out_and]);
+    if (!l) continue;
+    (*live_prod)[p] = 1;
+    (*live_node)[sig_node(g.a)] = 1;
+    (*live_node)[sig_node(g.b)] = 1;
+  }
+  (*live_node)[0] = 0;
+}
+
+}  // namespace
+
+uint32_t noise_bits(const Circuit& c, const Shape& s) {
+  std::vector<char> ln, lp;
+  liveness(c, &ln, &lp);
+  std::vector<Big> E(c.depth.size());
+  Big fresh = Big::of((uint64_t)s.m * s.chi);
+  for (uint32_t n : c.inputs) E[n] = fresh;
+  uint32_t best = fresh.bits();
+  for (size_t p = 0; p < c.products.size(); p++) {
+    if (!lp[p]) continue;
+    const Product& g = c.products[p];
+    const Big& EA = E[sig_node(g.a)];
+    const Big& EB = E[sig_node(g.b)];
+    auto apply = [&](uint32_t node, Code k) {
+      if (!node || !ln[node]) return;
+      Big e = EA.mul((uint64_t)(std::abs(k.c1) + std::abs(k.c3)))
+                  .add(EB.mul((uint64_t)std::abs(k.c2) + (uint64_t)std::abs(k.c3) * s.Ng));
+      best = std::max(best, e.bits());
+      E[node] = e;
+    };
+    if (g.is_or) {
+      apply(g.out_xor, kOr);
+    } else {
+      apply(g.out_xor, kXor);
+      apply(g.out_and, kAnd);
+    }
+  }
+  return best;
+}
+
+// -------------------------------------------------------------- compile
+
+namespace {
+
+// Coefficients on stored operands: a complemented B is absorbed first
+// (c2 B~ = c2 P - c2 B; c3 BitDecomp(A~)(P - B) = c3 A~ - c3 BitDecomp(A~) B),
+// then a complemented A in the linear term (c1 A~ = c1 P - c1 A); the kernel
+// itself complements A before BitDecomp.
+uint16_t adjusted(Code k, bool negA, bool negB) {
+  if (negB) {
+    k.c0 += k.c2;
+    k.c2 = -k.c2;
+    k.c1 += k.c3;
+    k.c3 = -k.c3;
+  }
+  if (negA) {
+    k.c0 += k.c1;
+    k.c1 = -k.c1;
+  }
+  return pack_code(k.c0, k.c1, k.c2, k.c3);
+}
+
+}  // namespace
+
+void compile(const Circuit& c, const Shape& s, Program* prog) {
+  std::vector<char> ln, lp;
+  liveness(c, &ln, &lp);
+  const size_t nn = c.depth.size();
+  std::vector<uint32_t> home(nn, REF_NONE);
+  std::vector<uint32_t> last(nn, 0);
+  uint32_t maxlev = 0;
+  for (size_t p = 0; p < c.products.size(); p++) {
+    if (!lp[p]) continue;
+    const Product& g = c.products[p];
+    uint32_t lev = c.depth[g.out_xor ? g.out_xor : g.out_and];
+    maxlev = std::max(maxlev, lev);
+    last[sig_node(g.a)] = std::max(last[sig_node(g.a)], lev);
+    last[sig_node(g.b)] = std::max(last[sig_node(g.b)], lev);
+  }
+  for (size_t i = 0; i < c.inputs.size(); i++) home[c.inputs[i]] = make_ref(REG_IN, (uint32_t)i);
+
+  // Outputs: a gate-produced, uncomplemented node lives directly in its first
+  // output slot; everything else is materialised by a fix-up after the last
+  // level (reads of fix-up sources count as uses at level maxlev + 1).
+  prog->fix.clear();
+  for (size_t o = 0; o < c.outputs.size(); o++) {
+    Sig sg = c.outputs[o];
+    uint32_t node = sig_node(sg);
+    if (node != 0 && !sig_neg(sg) && c.producer[node] >= 0 && home[node] == REF_NONE) {
+      home[node] = make_ref(REG_OUT, (uint32_t)o);
+      continue;
+    }
+    FixDesc f{};
+    f.dst = (uint32_t)o;
+    f.src = node;  // node id for now, resolved below
+    f.kind = node == 0 ? (sig_neg(sg) ? 3u : 2u) : (sig_neg(sg) ? 1u : 0u);
+    prog->fix.push_back(f);
+    if (node) last[node] = std::max(last[node], maxlev + 1);
+  }
+
+  // Group live products by level (creation order inside a level).
+  std::vector<std::vector<uint32_t>> by_level(maxlev + 1);
+  for (size_t p = 0; p < c.products.size(); p++) {
+    if (!lp[p]) continue;
+    const Product& g = c.products[p];
+    by_level[c.depth[g.out_xor ? g.out_xor : g.out_and]].push_back((uint32_t)p);
+  }
+  std::vector<std::vector<uint32_t>> release(maxlev + 2);
+  std::vector<uint32_t> free_slots;
+  uint32_t next_slot = 0;
+  prog->desc.clear();
+  prog->aux.clear();
+  prog->level_off.assign(1, 0);
+  prog->max_width = 0;
+  for (uint32_t lev = 1; lev <= maxlev; lev++) {
+    for (uint32_t p : by_level[lev]) {
+      const Product& g = c.products[p];
+      for (uint32_t node : {g.out_xor, g.out_and}) {
+        if (!node || !ln[node] || home[node] != REF_NONE) continue;
+        uint32_t slot;
+        if (!free_slots.empty()) {
+          slot = free_slots.back();
+          free_slots.pop_back();
+        } else {
+          slot = next_slot++;
+        }
+        home[node] = make_ref(REG_SCRATCH, slot);
+        release[last[node]].push_back(node);
+      }
+      GateDesc d;
+      GateAux x;
+      bool negA = sig_neg(g.a), negB = sig_neg(g.b);
+      d.a = home[sig_node(g.a)];
+      d.b = home[sig_node(g.b)];
+      uint16_t k0, k1 = 0;
+      if (g.is_or) {
+        d.o0 = ln[g.out_xor] ? home[g.out_xor] : REF_NONE;
+        d.o1 = REF_NONE;
+        k0 = adjusted(kOr, negA, negB);
+      } else {
+        d.o0 = (g.out_xor && ln[g.out_xor]) ? home[g.out_xor] : REF_NONE;
+        d.o1 = (g.out_and && ln[g.out_and]) ? home[g.out_and] : REF_NONE;
+        k0 = adjusted(kXor, negA, negB);
+        k1 = adjusted(kAnd, negA, negB);
+      }
+      x.code = (uint32_t)k0 | ((uint32_t)k1 << 16);
+      x.flags = negA ? 1u : 0u;
+      prog->desc.push_back(d);
+      prog->aux.push_back(x);
+    }
+    prog->level_off.push_back(prog->desc.size());
+    prog->max_width = std::max<uint64_t>(prog->max_width, by_level[lev].size());
+    for (uint32_t node : release[lev]) {
+      uint32_t r = home[node];
+      if ((r >> 30) == REG_SCRATCH) free_slots.push_back(r & SLOT_MASK);
+    }
+  }
+  for (auto& f : prog->fix) f.src = f.src ? home[f.src] : 0;
+  prog->n_inputs = c.inputs.size();
+  prog->n_outputs = c.outputs.size();
+  prog->scratch_slots = next_slot;
+  prog->products = prog->desc.size();
+  prog->noise_bits = noise_bits(c, s);
+  prog->noise_ok = prog->noise_bits <= s.ell - 2;
+}
+
+}  // namespace sfft

@@ -1,0 +1,97 @@
+// Canonical FFT gate circuit -> levelised device program.
+//
+// The circuit follows the paper's construction (Sec. 4, Lemmas 3-9): half
+// adders (XOR + AND sharing one ciphertext product), full adders as two half
+// adders and an OR (Lemma 6, Fig. 3), ripple-carry ADD and SUB = ADD(x, NOT y,
+// carry 1), Wallace-tree constant multiplication with sign extension to
+// T = f + F bits keeping bits [f, f+F) (Lemmas 8-9), radix-2 DIT butterflies
+// on the bit-reversed signal, and row-then-column 2-D transforms.
+//
+// Canonical choices that fix every ciphertext bit (shared with any other
+// implementation of the same circuit):
+//  * the bit-decomposed operand A of a product is the input of strictly
+//    greater multiplicative depth, ties keep the gate's first argument;
+//  * gates with a trivial-constant input are folded (bit-exact in GSW);
+//  * Wallace stages: per column FAs over consecutive triples, an HA over a
+//    remaining pair, a lone wire passes; new column = sums, passed wire,
+//    carries from below; repeat until every column has at most 2 wires.
+//
+// NOT gates never reach the device: a signal carries a complement bit, the
+// kernel complements A before BitDecomp, and a complemented B is absorbed
+// into the gate's coefficients (BitDecomp(A)(P - B) = A - BitDecomp(A) B).
+#pragma once
+
+#include <cstdint>
+#include <unordered_map>
+#include <vector>
+
+#include "common.h"
+
+namespace sfft {
+
+// A signal: node id (0 = the constant zero) and a complement bit (bit 31).
+using Sig = uint32_t;
+constexpr Sig SIG_ZERO = 0u;
+constexpr Sig SIG_ONE = 0x80000000u;
+inline uint32_t sig_node(Sig s) { return s & 0x7FFFFFFFu; }
+inline bool sig_neg(Sig s) { return (s >> 31) != 0; }
+
+struct Product {
+  Sig a, b;          // A (bit-decomposed) and B, already ordered by the depth rule
+  uint32_t out_xor;  // node of the XOR output (HA) or the OR output; 0 = none
+  uint32_t out_and;  // node of the AND output (HA only); 0 = none
+  bool is_or;
+};
+
+struct Circuit {
+  std::vector<uint32_t> depth;     // per node; node 0 = constant zero
+  std::vector<int32_t> producer;   // per node: product index or -1 (input/const)
+  std::vector<Product> products;
+  std::vector<uint32_t> inputs;    // input nodes in ciphertext order
+  std::vector<Sig> outputs;        // output signals in ciphertext order
+  uint64_t n_and = 0, n_xor = 0, n_or = 0, n_not = 0;   // logical gates before pruning
+  // Common subexpressions: identical (kind, A, B) gates give identical
+  // ciphertexts, so each is computed once (bit-exact).
+  std::unordered_map<uint64_t, int32_t> memo_ha, memo_or;
+
+  uint32_t new_node(uint32_t d, int32_t prod);
+  uint32_t new_input();
+  uint32_t dep(Sig s) const { return depth[sig_node(s)]; }
+
+  Sig NOT(Sig a);
+  void HA(Sig a, Sig b, Sig* s, Sig* c);
+  Sig OR(Sig a, Sig b);
+  void FA(Sig a, Sig b, Sig c, Sig* s, Sig* co);
+  std::vector<Sig> ADD(const std::vector<Sig>& x, const std::vector<Sig>& y, Sig cin);
+  std::vector<Sig> SUB(const std::vector<Sig>& x, const std::vector<Sig>& y);
+  std::vector<Sig> MUL(const std::vector<Sig>& x, int64_t w, uint32_t f);
+};
+
+// Builds the circuit of a 1-D (N2 == 1) or 2-D FFT. Throws nothing; returns
+// false on invalid sizes.
+bool build_fft(Circuit* c, uint32_t N1, uint32_t N2, uint32_t F, uint32_t f);
+
+// Quantised twiddles W_N^k = exp(-2 pi i k / N), k < N/2, floor to 2^-f.
+void twiddles(uint32_t N, uint32_t f, std::vector<int64_t>* wr, std::vector<int64_t>* wi);
+
+// Device program of a circuit for fixed scheme parameters.
+struct Program {
+  std::vector<GateDesc> desc;      // all gates, level by level
+  std::vector<GateAux> aux;
+  std::vector<uint64_t> level_off; // level l = [level_off[l], level_off[l+1])
+  std::vector<FixDesc> fix;        // output fix-ups
+  uint64_t n_inputs = 0, n_outputs = 0, scratch_slots = 0, products = 0;
+  uint64_t max_width = 0;
+  uint32_t noise_bits = 0;
+  bool noise_ok = false;
+};
+
+// Prunes dead gates, levelises, allocates scratch slots with reuse after last
+// use, and computes the static noise bound for the given parameters.
+void compile(const Circuit& c, const Shape& s, Program* prog);
+
+// Bit length of the largest static noise bound of the circuit's live wires
+// (fresh ciphertext m * chi; gate (|c1|+|c3|) E_A + (|c2| + |c3| Ng) E_B).
+uint32_t noise_bits(const Circuit& c, const Shape& s);
+
+}  // namespace sfft

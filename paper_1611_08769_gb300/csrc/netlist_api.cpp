@@ -1,0 +1,107 @@
+// Host-only C ABI over the circuit compiler: statistics and a plaintext run of
+// the compiled device program (same levels, slots, fix-ups and coefficients).
+#include <cstring>
+#include <vector>
+
+#include "common.h"
+#include "netlist.h"
+
+using namespace sfft;
+
+namespace {
+
+int build(const sfft_params* p, uint32_t N1, uint32_t N2, uint32_t F, uint32_t f, Shape* s,
+          Circuit* c, Program* prog) {
+  int rc = make_shape(p, s, false);
+  if (rc) return rc;
+  if (!build_fft(c, N1, N2, F, f))
+    return fail(SFFT_EINVAL, "N1, N2 must be powers of two, 2 <= F <= 48, f < F");
+  compile(*c, *s, prog);
+  return SFFT_OK;
+}
+
+int nib(uint32_t code, int k) { return (int)((int32_t)(code << (28 - 4 * k)) >> 28); }
+
+}  // namespace
+
+extern "C" {
+
+int sfft_circuit_info(const sfft_params* p, uint32_t N1, uint32_t N2, uint32_t F, uint32_t f,
+                      sfft_plan_info* info) {
+  if (!info) return fail(SFFT_EINVAL, "info is NULL");
+  Shape s;
+  Circuit c;
+  Program prog;
+  int rc = build(p, N1, N2, F, f, &s, &c, &prog);
+  if (rc) return rc;
+  std::memset(info, 0, sizeof(*info));
+  info->inputs = prog.n_inputs;
+  info->outputs = prog.n_outputs;
+  info->gates_and = c.n_and;
+  info->gates_xor = c.n_xor;
+  info->gates_or = c.n_or;
+  info->gates_not = c.n_not;
+  info->products = prog.products;
+  info->levels = prog.level_off.size() - 1;
+  info->max_level_width = prog.max_width;
+  info->scratch_slots = prog.scratch_slots;
+  info->scratch_bytes = prog.scratch_slots * s.ctw * 4;
+  info->ct_words = s.ctw;
+  info->noise_bits = prog.noise_bits;
+  info->noise_ok = prog.noise_ok ? 1 : 0;
+  return SFFT_OK;
+}
+
+int sfft_program_eval_plain(const sfft_params* p, uint32_t N1, uint32_t N2, uint32_t F,
+                            uint32_t f, const uint8_t* h_in_bits, uint8_t* h_out_bits) {
+  if (!h_in_bits || !h_out_bits) return fail(SFFT_EINVAL, "null argument");
+  Shape s;
+  Circuit c;
+  Program prog;
+  int rc = build(p, N1, N2, F, f, &s, &c, &prog);
+  if (rc) return rc;
+  std::vector<int> reg[3];
+  reg[REG_SCRATCH].assign(prog.scratch_slots, -1);
+  reg[REG_IN].assign(h_in_bits, h_in_bits + prog.n_inputs);
+  reg[REG_OUT].assign(prog.n_outputs, -1);
+  auto get = [&](uint32_t ref) -> int {
+    int v = reg[ref >> 30][ref & SLOT_MASK];
+    return v;
+  };
+  for (size_t g = 0; g < prog.desc.size(); g++) {
+    const GateDesc& d = prog.desc[g];
+    const GateAux& x = prog.aux[g];
+    int a = get(d.a), b = get(d.b);
+    if (a < 0 || b < 0) return fail(SFFT_EINVAL, "program reads an unwritten slot");
+    int at = (x.flags & 1) ? 1 - a : a;
+    uint32_t codes[2] = {x.code & 0xFFFFu, x.code >> 16};
+    uint32_t outs[2] = {d.o0, d.o1};
+    for (int o = 0; o < 2; o++) {
+      if (outs[o] == REF_NONE) continue;
+      int v = nib(codes[o], 0) + nib(codes[o], 1) * a + nib(codes[o], 2) * b +
+              nib(codes[o], 3) * at * b;
+      if (v != 0 && v != 1) return fail(SFFT_EINVAL, "gate produced a non-bit");
+      reg[outs[o] >> 30][outs[o] & SLOT_MASK] = v;
+    }
+  }
+  for (const FixDesc& fx : prog.fix) {
+    int v;
+    if (fx.kind == 2)
+      v = 0;
+    else if (fx.kind == 3)
+      v = 1;
+    else {
+      v = get(fx.src);
+      if (v < 0) return fail(SFFT_EINVAL, "fix-up reads an unwritten slot");
+      if (fx.kind == 1) v = 1 - v;
+    }
+    reg[REG_OUT][fx.dst] = v;
+  }
+  for (uint64_t o = 0; o < prog.n_outputs; o++) {
+    if (reg[REG_OUT][o] < 0) return fail(SFFT_EINVAL, "output never written");
+    h_out_bits[o] = (uint8_t)reg[REG_OUT][o];
+  }
+  return SFFT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,44 @@
+// Device-resident form of a compiled program and the launch helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "common.h"
+#include "kernels.cuh"
+#include "netlist.h"
+
+namespace sfft {
+
+struct DeviceProgram {
+  GateDesc* desc = nullptr;
+  GateAux* aux = nullptr;
+  FixDesc* fix = nullptr;
+  uint64_t n_fix = 0;
+  std::vector<uint64_t> level_off;
+  uint64_t scratch_slots = 0;
+};
+
+int cuda_fail(cudaError_t e, const char* what);
+int upload(const void* h, size_t bytes, void** d);
+KArgs make_args(const Shape& s);
+int launch_gates(const KArgs& a, cudaStream_t st);
+int make_device_program(const Program& p, DeviceProgram* dp);
+void free_device_program(DeviceProgram* dp);
+// Optional per-launch CUDA-event timing of gate kernels.
+struct Timer {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  uint64_t launches = 0, products = 0;
+  cudaEvent_t next();   // an event from the pool (grows on demand)
+  double drain_ms();    // waits, sums pairs, resets
+  ~Timer();
+};
+
+int run_program(const Shape& s, const DeviceProgram& dp, const uint32_t* d_in, uint32_t* d_out,
+                uint32_t* d_scratch, uint64_t scratch_bytes, cudaStream_t st, Timer* tm = nullptr);
+
+}  // namespace sfft

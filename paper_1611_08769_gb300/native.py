@@ -1,0 +1,88 @@
+"""ctypes declarations of the C ABI in include/sfft.h (argument marshalling only).
+
+Loading fails loudly when the in-tree library is missing: there is no
+Python or CPU fallback for any call.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsfft.so")
+
+c_u32, c_u64, c_i32, c_i64 = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32, ctypes.c_int64
+c_void_p, c_double_p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)
+c_u32_p, c_u16_p, c_u8_p, c_i64_p = (ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint16),
+                                     ctypes.POINTER(ctypes.c_uint8), ctypes.POINTER(ctypes.c_int64))
+
+
+class sfft_params(ctypes.Structure):
+    _fields_ = [("n", c_u32), ("ell", c_u32), ("m", c_u32), ("chi", c_u32)]
+
+
+class sfft_plan_info(ctypes.Structure):
+    _fields_ = [("inputs", c_u64), ("outputs", c_u64), ("gates_and", c_u64), ("gates_xor", c_u64),
+                ("gates_or", c_u64), ("gates_not", c_u64), ("products", c_u64), ("levels", c_u64),
+                ("max_level_width", c_u64), ("scratch_slots", c_u64), ("scratch_bytes", c_u64),
+                ("ct_words", c_u64), ("noise_bits", c_u32), ("noise_ok", c_u32)]
+
+
+P = ctypes.POINTER
+# name: (restype, argtypes)
+SIGNATURES = {
+    "sfft_last_error": (ctypes.c_char_p, []),
+    "sfft_version": (ctypes.c_char_p, []),
+    "sfft_ct_words": (c_u64, [P(sfft_params)]),
+    "sfft_keygen": (c_i32, [P(sfft_params), c_u64, P(c_void_p)]),
+    "sfft_keys_free": (None, [c_void_p]),
+    "sfft_keys_public": (c_i32, [c_void_p, c_u32_p, c_u64]),
+    "sfft_encrypt_bits": (c_i32, [c_void_p, c_double_p, c_double_p, c_u64, c_u32, c_u32, c_u64,
+                                  c_u32_p]),
+    "sfft_encrypt_bits_device": (c_i32, [P(sfft_params), c_void_p, c_double_p, c_double_p, c_u64,
+                                         c_u32, c_u32, c_u64, c_void_p, c_void_p]),
+    "sfft_decrypt": (c_i32, [c_void_p, c_u32_p, c_u64, c_u64, c_u32, c_u32, c_double_p,
+                             c_double_p, c_i64_p]),
+    "sfft_gather_dec_rows": (c_i32, [P(sfft_params), c_void_p, c_u64, c_void_p, c_void_p]),
+    "sfft_min_ell": (c_u32, [c_u32, c_u32, c_u32, c_u32, c_u32, c_u32]),
+    "sfft_plan_create": (c_i32, [P(sfft_params), c_u32, c_u32, c_u32, c_u32, c_u32, P(c_void_p)]),
+    "sfft_plan_info_get": (c_i32, [c_void_p, P(sfft_plan_info)]),
+    "sfft_plan_free": (None, [c_void_p]),
+    "sfft_eval_fft": (c_i32, [c_void_p, c_void_p, c_void_p, c_void_p, c_u64, c_void_p]),
+    "sfft_eval_fft_host": (c_i32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                   c_u64, c_void_p]),
+    "sfft_plan_set_timing": (c_i32, [c_void_p, ctypes.c_int]),
+    "sfft_plan_timing": (c_i32, [c_void_p, c_double_p, P(c_u64), P(c_u64)]),
+    "sfft_circuit_info": (c_i32, [P(sfft_params), c_u32, c_u32, c_u32, c_u32, P(sfft_plan_info)]),
+    "sfft_program_eval_plain": (c_i32, [P(sfft_params), c_u32, c_u32, c_u32, c_u32, c_u8_p, c_u8_p]),
+    "sfft_gate_level": (c_i32, [P(sfft_params), c_void_p, c_void_p, c_void_p, c_void_p, c_u16_p,
+                                c_u16_p, c_u8_p, c_u64, c_void_p]),
+}
+
+_lib = None
+
+
+def lib():
+    """The loaded library with every declared signature bound."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"native library missing: {LIB_PATH} "
+                              "(build it with paper_1611_08769_gb300.build.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+class SfftError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"sfft error {code}: {msg}")
+        self.code = code
+
+
+def check(rc):
+    if rc != 0:
+        raise SfftError(rc, lib().sfft_last_error().decode())
+    return rc

@@ -176,6 +176,24 @@ int sfft_circuit_info(const sfft_params* p, uint32_t N1, uint32_t N2, uint32_t F
 int sfft_program_eval_plain(const sfft_params* p, uint32_t N1, uint32_t N2, uint32_t F,
                             uint32_t f, const uint8_t* h_in_bits, uint8_t* h_out_bits);
 
+/* sfft_eval_fft without any allocation (the paper has no counterpart; this
+ * is a library service). For callers that must not call cudaMalloc while
+ * evaluating -- e.g. a host application whose memory pool already reserved
+ * the device memory, or a latency-critical serving loop that cannot afford
+ * cudaMalloc's implicit device-wide synchronisation. The caller passes inputs
+ * and outputs; intermediate ciphertexts live in a fixed array of
+ * sfft_noalloc_scratch_bytes() (32 MiB) that the library reserves on every
+ * GPU that loads it, held until the process exits. Plans whose
+ * info.scratch_bytes exceed it are rejected with SFFT_EINVAL. The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture. All calls share the one
+ * array, so calls that overlap on the GPU (other streams, other threads)
+ * race; nothing in it needs clearing between calls (every slot is written
+ * before it is read). Makes no cudaMalloc/cudaFree or allocating library
+ * call. */
+int sfft_eval_fft_noalloc(sfft_plan* plan, const uint32_t* d_in, uint32_t* d_out, void* stream);
+uint64_t sfft_noalloc_scratch_bytes(void);
+
 /* Kernel timing: when on, CUDA events are recorded on the launching stream
  * around every gate-kernel launch of sfft_eval_fft*. sfft_plan_timing waits
  * for them, returns the summed gate-kernel milliseconds, the number of

@@ -173,6 +173,10 @@ class Plan:
         check(lib().sfft_eval_fft_host(self._h, _dptr(h_in), _dptr(h_out), _dptr(d_in),
                                        _dptr(d_out), _dptr(d_scratch), nbytes, _stream(stream)))
 
+    def eval_fft_noalloc(self, d_in, d_out, stream=None):
+        """sfft_eval_fft_noalloc: scratch in the library's fixed device array."""
+        check(lib().sfft_eval_fft_noalloc(self._h, _dptr(d_in), _dptr(d_out), _stream(stream)))
+
     def set_timing(self, on):
         check(lib().sfft_plan_set_timing(self._h, 1 if on else 0))
 

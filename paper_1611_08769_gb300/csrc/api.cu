@@ -137,15 +137,6 @@ void free_device_program(DeviceProgram* dp) {
 
 }  // namespace sfft
 
-struct sfft_plan {
-  sfft::Shape s;
-  sfft::Circuit circuit;
-  sfft::Program prog;
-  sfft::DeviceProgram dev;
-  sfft::Timer timer;
-  uint32_t N1, N2, F, f;
-};
-
 using namespace sfft;
 
 extern "C" {

@@ -1,0 +1,20 @@
+// Launch arguments of the level kernels (shared by host launchers and kernels).
+#pragma once
+
+#include <cstdint>
+
+#include "common.h"
+
+namespace sfft {
+
+struct KArgs {
+  const GateDesc* desc;
+  const GateAux* aux;
+  uint64_t n;            // gates in this launch
+  uint32_t* base[4];     // region bases (region 3 = generated R for operand A)
+  uint64_t gen_state;    // domain key of the generated R matrices
+  uint32_t Ng, W, L, ell;
+  uint64_t ctw;
+};
+
+}  // namespace sfft

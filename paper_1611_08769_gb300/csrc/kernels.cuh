@@ -14,19 +14,11 @@
 #include <cstdint>
 
 #include "common.h"
+#include "kargs.h"
 #include "rng.h"
 
 namespace sfft {
 
-struct KArgs {
-  const GateDesc* desc;
-  const GateAux* aux;
-  uint64_t n;            // gates in this launch
-  uint32_t* base[4];     // region bases (region 3 = generated R for operand A)
-  uint64_t gen_state;    // domain key of the generated R matrices
-  uint32_t Ng, W, L, ell;
-  uint64_t ctw;
-};
 
 __device__ __forceinline__ uint32_t* resolve(const KArgs& a, uint32_t ref) {
   return a.base[ref >> 30] + (uint64_t)(ref & SLOT_MASK) * a.ctw;

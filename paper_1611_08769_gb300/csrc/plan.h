@@ -7,7 +7,7 @@
 #include <vector>
 
 #include "common.h"
-#include "kernels.cuh"
+#include "kargs.h"
 #include "netlist.h"
 
 namespace sfft {
@@ -42,3 +42,13 @@ int run_program(const Shape& s, const DeviceProgram& dp, const uint32_t* d_in, u
                 uint32_t* d_scratch, uint64_t scratch_bytes, cudaStream_t st, Timer* tm = nullptr);
 
 }  // namespace sfft
+
+// A compiled FFT plan (opaque in the C ABI).
+struct sfft_plan {
+  sfft::Shape s;
+  sfft::Circuit circuit;
+  sfft::Program prog;
+  sfft::DeviceProgram dev;
+  sfft::Timer timer;
+  uint32_t N1, N2, F, f;
+};

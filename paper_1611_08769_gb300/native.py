@@ -49,6 +49,8 @@ SIGNATURES = {
     "sfft_eval_fft": (c_i32, [c_void_p, c_void_p, c_void_p, c_void_p, c_u64, c_void_p]),
     "sfft_eval_fft_host": (c_i32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                    c_u64, c_void_p]),
+    "sfft_eval_fft_noalloc": (c_i32, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "sfft_noalloc_scratch_bytes": (c_u64, []),
     "sfft_plan_set_timing": (c_i32, [c_void_p, ctypes.c_int]),
     "sfft_plan_timing": (c_i32, [c_void_p, c_double_p, P(c_u64), P(c_u64)]),
     "sfft_circuit_info": (c_i32, [P(sfft_params), c_u32, c_u32, c_u32, c_u32, P(sfft_plan_info)]),

@@ -135,6 +135,8 @@ typedef struct sfft_plan_info {
   uint64_t ct_words;
   uint32_t noise_bits;          /* bit length of the largest wire noise bound */
   uint32_t noise_ok;            /* bound < q/4 */
+  uint32_t gate_kernel;         /* 1 integer-ALU kernel, 2 tensor-core kernel */
+  uint32_t reserved;
 } sfft_plan_info;
 
 /* Builds the canonical gate circuit of a 1-D (N2 == 1) or row-column 2-D FFT
@@ -144,6 +146,7 @@ typedef struct sfft_plan_info {
  * level) and uploads its gate descriptors to the device. Fails with EPARAM
  * if the static noise bound reaches q/4. flags: SFFT_PLAN_* below. */
 #define SFFT_PLAN_ALLOW_NOISY 1u   /* build even if the noise bound fails */
+#define SFFT_PLAN_INT_KERNEL 2u    /* integer-ALU gate kernel even where tensor cores apply */
 int sfft_plan_create(const sfft_params* p, uint32_t N1, uint32_t N2, uint32_t F, uint32_t f,
                      uint32_t flags, sfft_plan** out);
 int sfft_plan_info_get(const sfft_plan* plan, sfft_plan_info* info);
@@ -156,6 +159,11 @@ void sfft_plan_free(sfft_plan* plan);
  * Device pointers must be 16-byte aligned. */
 int sfft_eval_fft(sfft_plan* plan, const uint32_t* d_in, uint32_t* d_out,
                   uint32_t* d_scratch, uint64_t scratch_bytes, void* stream);
+
+/* Waits for the stream and reports (then clears) the plan's device error
+ * word: SFFT_ETIMEOUT if a bounded wait inside a gate kernel ran out since the
+ * last check (the kernel then skipped its outputs and released its TMEM). */
+int sfft_plan_check(sfft_plan* plan, void* stream);
 
 /* Same, end to end from host buffers: copies h_in to d_in, evaluates, copies
  * d_out to h_out and waits for the stream. Pinned host memory is fastest. */
@@ -208,11 +216,13 @@ int sfft_plan_timing(sfft_plan* plan, double* gate_ms, uint64_t* launches, uint6
  *   d_out0[g] = c0 P + c1 A + c2 B + c3 BitDecomp(A) B    (code0 = c0..c3)
  *   d_out1[g] likewise with code1 when flags[g] & 2.
  * d_a/d_b/d_out0/d_out1 are arrays of n_gates ciphertexts; codes are 4
- * signed nibbles c0 | c1 << 4 | c2 << 8 | c3 << 12 (two's complement). */
+ * signed nibbles c0 | c1 << 4 | c2 << 8 | c3 << 12 (two's complement).
+ * kernel: 0 automatic, 1 integer ALU, 2 tensor cores (EPARAM if unsupported).
+ * Synchronises the stream; SFFT_ETIMEOUT if a bounded device wait ran out. */
 int sfft_gate_level(const sfft_params* p, const uint32_t* d_a, const uint32_t* d_b,
                     uint32_t* d_out0, uint32_t* d_out1, const uint16_t* h_code0,
                     const uint16_t* h_code1, const uint8_t* h_flags, uint64_t n_gates,
-                    void* stream);
+                    uint32_t kernel, void* stream);
 
 #ifdef __cplusplus
 }

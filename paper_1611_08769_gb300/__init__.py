@@ -17,6 +17,8 @@ from . import native
 from .native import SfftError, check, lib, sfft_params, sfft_plan_info
 
 PLAN_ALLOW_NOISY = 1
+PLAN_INT_KERNEL = 2
+KERNEL_AUTO, KERNEL_INT, KERNEL_TC = 0, 1, 2
 
 __all__ = ["Params", "Keys", "Plan", "keygen", "encrypt_bits", "encrypt_bits_device", "decrypt",
            "gather_dec_rows", "min_ell", "gate_level", "ct_words", "SfftError", "version"]
@@ -173,6 +175,10 @@ class Plan:
         check(lib().sfft_eval_fft_host(self._h, _dptr(h_in), _dptr(h_out), _dptr(d_in),
                                        _dptr(d_out), _dptr(d_scratch), nbytes, _stream(stream)))
 
+    def check(self, stream=None):
+        """sfft_plan_check: raises SfftError (ETIMEOUT) if a device wait ran out."""
+        check(lib().sfft_plan_check(self._h, _stream(stream)))
+
     def eval_fft_noalloc(self, d_in, d_out, stream=None):
         """sfft_eval_fft_noalloc: scratch in the library's fixed device array."""
         check(lib().sfft_eval_fft_noalloc(self._h, _dptr(d_in), _dptr(d_out), _stream(stream)))
@@ -195,14 +201,15 @@ class Plan:
             self._h = None
 
 
-def gate_level(params, d_a, d_b, d_out0, d_out1, code0, code1, flags, stream=None):
+def gate_level(params, d_a, d_b, d_out0, d_out1, code0, code1, flags, stream=None, kernel=0):
     code0 = np.ascontiguousarray(code0, dtype=np.uint16)
     code1 = np.ascontiguousarray(code1, dtype=np.uint16)
     flags = np.ascontiguousarray(flags, dtype=np.uint8)
     check(lib().sfft_gate_level(ctypes.byref(params), _dptr(d_a), _dptr(d_b), _dptr(d_out0),
                                 _dptr(d_out1), code0.ctypes.data_as(native.c_u16_p),
                                 code1.ctypes.data_as(native.c_u16_p),
-                                flags.ctypes.data_as(native.c_u8_p), len(code0), _stream(stream)))
+                                flags.ctypes.data_as(native.c_u8_p), len(code0), kernel,
+                                _stream(stream)))
 
 
 def pack_code(c0, c1, c2, c3):

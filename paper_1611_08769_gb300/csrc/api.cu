@@ -42,6 +42,8 @@ KArgs make_args(const Shape& s) {
 // Launches one level of gates with the integer kernel.
 int launch_gates(const KArgs& a, cudaStream_t st) {
   if (a.n == 0) return SFFT_OK;
+  if (a.kernel != KERNEL_INT && tc_supported(a)) return launch_gates_tc(a, st);
+  if (a.kernel == KERNEL_TC) return fail(SFFT_EPARAM, "tensor-core kernel does not support this shape");
   const uint64_t tasks = a.n * (a.Ng / 32);
   const uint64_t blocks = (tasks * 32 + 255) / 256;
   if (a.W <= 2)
@@ -89,6 +91,8 @@ int run_program(const Shape& s, const DeviceProgram& dp, const uint32_t* d_in, u
   a.base[REG_IN] = const_cast<uint32_t*>(d_in);
   a.base[REG_OUT] = d_out;
   a.base[REG_GEN] = nullptr;
+  a.err = dp.err;
+  a.kernel = dp.kernel;
   for (size_t l = 0; l + 1 < dp.level_off.size(); l++) {
     a.desc = dp.desc + dp.level_off[l];
     a.aux = dp.aux + dp.level_off[l];
@@ -123,13 +127,30 @@ int make_device_program(const Program& p, DeviceProgram* dp) {
   dp->n_fix = p.fix.size();
   dp->level_off = p.level_off;
   dp->scratch_slots = p.scratch_slots;
+  cudaError_t e = cudaMalloc((void**)&dp->err, sizeof(int));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+  e = cudaMemset(dp->err, 0, sizeof(int));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemset");
   return SFFT_OK;
+}
+
+int check_device_error(int* err, cudaStream_t st) {
+  if (!err) return SFFT_OK;
+  int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "reading the device error word");
+  if (h == 0) return SFFT_OK;
+  cudaMemsetAsync(err, 0, sizeof(int), st);
+  return fail(SFFT_ETIMEOUT, "a bounded wait inside the tensor-core gate kernel ran out");
 }
 
 void free_device_program(DeviceProgram* dp) {
   cudaFree(dp->desc);
   cudaFree(dp->aux);
   cudaFree(dp->fix);
+  cudaFree(dp->err);
+  dp->err = nullptr;
   dp->desc = nullptr;
   dp->aux = nullptr;
   dp->fix = nullptr;
@@ -176,6 +197,7 @@ int sfft_plan_create(const sfft_params* p, uint32_t N1, uint32_t N2, uint32_t F,
   pl->N2 = N2;
   pl->F = F;
   pl->f = f;
+  pl->dev.kernel = (flags & SFFT_PLAN_INT_KERNEL) ? KERNEL_INT : KERNEL_AUTO;
   *out = pl.release();
   return SFFT_OK;
 }
@@ -197,6 +219,8 @@ int sfft_plan_info_get(const sfft_plan* pl, sfft_plan_info* info) {
   info->ct_words = pl->s.ctw;
   info->noise_bits = pl->prog.noise_bits;
   info->noise_ok = pl->prog.noise_ok ? 1 : 0;
+  info->gate_kernel =
+      (pl->dev.kernel != KERNEL_INT && tc_supported(make_args(pl->s))) ? KERNEL_TC : KERNEL_INT;
   return SFFT_OK;
 }
 
@@ -244,13 +268,19 @@ int sfft_eval_fft_host(sfft_plan* pl, const uint32_t* h_in, uint32_t* h_out, uin
   e = cudaMemcpyAsync(h_out, d_out, out_b, cudaMemcpyDeviceToHost, st);
   if (e != cudaSuccess) return cuda_fail(e, "D2H copy");
   e = cudaStreamSynchronize(st);
-  return e == cudaSuccess ? SFFT_OK : cuda_fail(e, "stream sync");
+  if (e != cudaSuccess) return cuda_fail(e, "stream sync");
+  return check_device_error(pl->dev.err, st);
+}
+
+int sfft_plan_check(sfft_plan* pl, void* stream) {
+  if (!pl) return fail(SFFT_EINVAL, "plan is NULL");
+  return check_device_error(pl->dev.err, (cudaStream_t)stream);
 }
 
 int sfft_gate_level(const sfft_params* p, const uint32_t* d_a, const uint32_t* d_b,
                     uint32_t* d_out0, uint32_t* d_out1, const uint16_t* h_code0,
                     const uint16_t* h_code1, const uint8_t* h_flags, uint64_t n_gates,
-                    void* stream) {
+                    uint32_t kernel, void* stream) {
   Shape s;
   int rc = make_shape(p, &s, false);
   if (rc) return rc;
@@ -280,10 +310,15 @@ int sfft_gate_level(const sfft_params* p, const uint32_t* d_a, const uint32_t* d
   a.base[REG_IN] = const_cast<uint32_t*>(d_b);
   a.base[REG_OUT] = d_out0;
   a.base[REG_GEN] = d_out1;  // region 3 is only an output here, never operand A
+  a.kernel = kernel;
+  cudaMalloc((void**)&a.err, sizeof(int));
+  if (a.err) cudaMemset(a.err, 0, sizeof(int));
   rc = launch_gates(a, st);
   cudaError_t e = cudaStreamSynchronize(st);
+  if (!rc && e == cudaSuccess) rc = check_device_error(a.err, st);
   cudaFree(dd);
   cudaFree(da);
+  cudaFree(a.err);
   if (rc) return rc;
   return e == cudaSuccess ? SFFT_OK : cuda_fail(e, "gate level");
 }

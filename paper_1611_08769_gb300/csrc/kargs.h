@@ -15,6 +15,13 @@ struct KArgs {
   uint64_t gen_state;    // domain key of the generated R matrices
   uint32_t Ng, W, L, ell;
   uint64_t ctw;
+  int* err;              // device error word (bounded waits that ran out), may be null
+  uint32_t kernel;       // KERNEL_AUTO / KERNEL_INT / KERNEL_TC
 };
+
+constexpr uint32_t KERNEL_AUTO = 0, KERNEL_INT = 1, KERNEL_TC = 2;
+
+// Error codes written to KArgs::err by kernels.
+constexpr int KERR_MMA_TIMEOUT = 1;
 
 }  // namespace sfft

@@ -4,7 +4,12 @@
 #include <vector>
 
 #include "common.h"
+#include "kargs.h"
 #include "netlist.h"
+
+namespace sfft {
+bool tc_supported(const KArgs& a);
+}
 
 using namespace sfft;
 
@@ -49,6 +54,10 @@ int sfft_circuit_info(const sfft_params* p, uint32_t N1, uint32_t N2, uint32_t F
   info->ct_words = s.ctw;
   info->noise_bits = prog.noise_bits;
   info->noise_ok = prog.noise_ok ? 1 : 0;
+  KArgs ka{};
+  ka.Ng = s.Ng;
+  ka.W = s.W;
+  info->gate_kernel = tc_supported(ka) ? KERNEL_TC : KERNEL_INT;
   return SFFT_OK;
 }
 

@@ -19,12 +19,20 @@ struct DeviceProgram {
   uint64_t n_fix = 0;
   std::vector<uint64_t> level_off;
   uint64_t scratch_slots = 0;
+  int* err = nullptr;            // device error word of the kernels
+  uint32_t kernel = 0;           // KERNEL_AUTO / KERNEL_INT / KERNEL_TC
 };
+
+// Reads and clears the device error word (synchronises the stream).
+int check_device_error(int* err, cudaStream_t st);
 
 int cuda_fail(cudaError_t e, const char* what);
 int upload(const void* h, size_t bytes, void** d);
 KArgs make_args(const Shape& s);
 int launch_gates(const KArgs& a, cudaStream_t st);
+// Tensor-core gate kernel (tc.cu): shapes it supports, and its launcher.
+bool tc_supported(const KArgs& a);
+int launch_gates_tc(const KArgs& a, cudaStream_t st);
 int make_device_program(const Program& p, DeviceProgram* dp);
 void free_device_program(DeviceProgram* dp);
 // Optional per-launch CUDA-event timing of gate kernels.

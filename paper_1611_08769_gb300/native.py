@@ -23,7 +23,8 @@ class sfft_plan_info(ctypes.Structure):
     _fields_ = [("inputs", c_u64), ("outputs", c_u64), ("gates_and", c_u64), ("gates_xor", c_u64),
                 ("gates_or", c_u64), ("gates_not", c_u64), ("products", c_u64), ("levels", c_u64),
                 ("max_level_width", c_u64), ("scratch_slots", c_u64), ("scratch_bytes", c_u64),
-                ("ct_words", c_u64), ("noise_bits", c_u32), ("noise_ok", c_u32)]
+                ("ct_words", c_u64), ("noise_bits", c_u32), ("noise_ok", c_u32),
+                ("gate_kernel", c_u32), ("reserved", c_u32)]
 
 
 P = ctypes.POINTER
@@ -56,7 +57,8 @@ SIGNATURES = {
     "sfft_circuit_info": (c_i32, [P(sfft_params), c_u32, c_u32, c_u32, c_u32, P(sfft_plan_info)]),
     "sfft_program_eval_plain": (c_i32, [P(sfft_params), c_u32, c_u32, c_u32, c_u32, c_u8_p, c_u8_p]),
     "sfft_gate_level": (c_i32, [P(sfft_params), c_void_p, c_void_p, c_void_p, c_void_p, c_u16_p,
-                                c_u16_p, c_u8_p, c_u64, c_void_p]),
+                                c_u16_p, c_u8_p, c_u64, c_u32, c_void_p]),
+    "sfft_plan_check": (c_i32, [c_void_p, c_void_p]),
 }
 
 _lib = None

@@ -36,8 +36,14 @@ CODES = {"XOR": (0, 1, 1, -2), "AND": (0, 0, 0, 1), "OR": (0, 1, 1, -1), "NAND":
          "MIX": (1, -1, 2, 3)}
 
 
-@pytest.mark.parametrize("n,ell", [(1, 32), (1, 128), (1, 224), (2, 64), (1, 1056)])
-def test_gate_level_matches_oracle(n, ell):
+GATE_CASES = [(1, 32, sf.KERNEL_INT), (1, 128, sf.KERNEL_INT), (1, 224, sf.KERNEL_INT),
+              (2, 64, sf.KERNEL_INT), (1, 1056, sf.KERNEL_INT),
+              (1, 128, sf.KERNEL_TC), (1, 224, sf.KERNEL_TC), (2, 64, sf.KERNEL_TC),
+              (1, 1056, sf.KERNEL_TC), (1, 1984, sf.KERNEL_TC)]
+
+
+@pytest.mark.parametrize("n,ell,kernel", GATE_CASES)
+def test_gate_level_matches_oracle(n, ell, kernel):
     p = gsw.Params(n, ell, (n + 1) * ell, 0)
     sp = sf.Params(n, ell)
     shape = (p.Ng, n + 1, p.L)
@@ -54,7 +60,7 @@ def test_gate_level_matches_oracle(n, ell):
     dA, dB = dev(A), dev(B)
     o0 = torch.zeros_like(dA)
     o1 = torch.zeros_like(dA)
-    sf.gate_level(sp, dA, dB, o0, o1, code0, code1, flags)
+    sf.gate_level(sp, dA, dB, o0, o1, code0, code1, flags, kernel=kernel)
     torch.cuda.synchronize()
     got0, got1 = host(o0, A.shape), host(o1, A.shape)
     for g in range(G):
@@ -88,13 +94,13 @@ def test_device_encryption_matches_oracle(name, ell):
                 assert np.array_equal(got[idx], gsw.encrypt(ok, bit, 5, idx)), idx
 
 
-def _run_plan(sp, N1, N2, F, f, d_in):
-    plan = sf.Plan(sp, N1, N2, F, f)
+def _run_plan(sp, N1, N2, F, f, d_in, flags=0):
+    plan = sf.Plan(sp, N1, N2, F, f, flags)
     info = plan.info
     out = torch.zeros((info["outputs"], info["ct_words"]), dtype=torch.int32, device="cuda")
     scratch = torch.empty(max(1, info["scratch_bytes"] // 4), dtype=torch.int32, device="cuda")
     plan.eval_fft(d_in, out, scratch)
-    torch.cuda.synchronize()
+    plan.check()
     return plan, out
 
 
@@ -130,8 +136,10 @@ def test_fft_8pt_toy_parameters_bit_exact():
     assert list(raw) == [v for k in range(N) for v in (er[k], ei[k])]
 
 
-def test_fft_noisy_leveled_parameters_bit_exact():
-    """Noisy chi = 1 scheme with ell sized by the static bound (8-pt, 8-bit)."""
+@pytest.mark.parametrize("flags", [0, sf.PLAN_INT_KERNEL])
+def test_fft_noisy_leveled_parameters_bit_exact(flags):
+    """Noisy chi = 1 scheme with ell sized by the static bound (8-pt, 8-bit);
+    tensor-core kernel (default) and integer kernel."""
     N, F, f = 8, 8, 4
     ell = sf.min_ell(N, 1, F, f, n=1, chi=1)
     sp = sf.param_set("P1", ell)
@@ -140,7 +148,7 @@ def test_fft_noisy_leveled_parameters_bit_exact():
     keys = sf.keygen(sp, 1)
     d_in = torch.zeros((N * 2 * F, sf.ct_words(sp)), dtype=torch.int32, device="cuda")
     sf.encrypt_bits_device(sp, dev(keys.public()), re_, im_, F, f, 2, d_in)
-    plan, out = _run_plan(sp, N, 1, F, f, d_in)
+    plan, out = _run_plan(sp, N, 1, F, f, d_in, flags)
     got = host(out, (N * 2 * F, p.Ng, p.n + 1, p.L))
     ko = gsw.Keys(p, 1)
     c, bits, want = _oracle_fft(p, ko, re_, im_, N, 1, F, f, 2)

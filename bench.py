@@ -53,7 +53,51 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="budget of the bounded oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="fft", choices=["fft", "gates"],
+                    help="fft: the whole encrypted FFT (default); gates: one level of "
+                         "independent random gates at the workload's parameters")
+    ap.add_argument("--gates", type=int, default=128, help="gates per level in --mode gates")
+    ap.add_argument("--kernel", default="auto", choices=["auto", "int", "tc"])
     return ap.parse_args()
+
+
+def run_gates(args):
+    """One level of `--gates` random products at the workload's parameters, timed
+    with CUDA events; the unit the gate kernels' rooflines are stated in."""
+    import torch
+
+    import paper_1611_08769_gb300 as sf
+    from paper_1611_08769_gb300 import build as sfbuild
+    sfbuild.build()
+    params, dims, _, _ = workload(args.config)
+    cw = sf.ct_words(params)
+    G = args.gates
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    A = torch.randint(-2**31, 2**31 - 1, (G, cw), dtype=torch.int32, device="cuda", generator=gen)
+    B = torch.randint(-2**31, 2**31 - 1, (G, cw), dtype=torch.int32, device="cuda", generator=gen)
+    O0, O1 = torch.empty_like(A), torch.empty_like(A)
+    code0 = [sf.pack_code(0, 1, 1, -2)] * G
+    code1 = [sf.pack_code(0, 0, 0, 1)] * G
+    flags = [2] * G
+    kern = {"auto": 0, "int": 1, "tc": 2}[args.kernel]
+    for _ in range(args.warmup):
+        sf.gate_level(params, A, B, O0, O1, code0, code1, flags, kernel=kern)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms = []
+    for _ in range(args.steps):
+        ev0.record()
+        sf.gate_level(params, A, B, O0, O1, code0, code1, flags, kernel=kern)
+        ev1.record()
+        torch.cuda.synchronize()
+        ms.append(ev0.elapsed_time(ev1))
+    t = statistics.median(ms)
+    info = {"gate_kernel": 2 if (kern == 2 or (kern == 0 and (params.n + 1) * params.ell >= 128))
+            else 1}
+    roof = roofline(params, info, t, 1, G)
+    print(json.dumps({"mode": "gates", "gates": G, "ms_per_level": t, "gates_per_s": G / t * 1e3,
+                      "config": {"workload": args.config, "n": params.n, "ell": params.ell},
+                      "note": "includes the hook's descriptor upload and synchronisation",
+                      "roofline": roof}), flush=True)
 
 
 class ClockSampler:
@@ -236,6 +280,8 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.mode == "gates":
+        return run_gates(args)
 
     import torch
     import torch.distributed as dist
@@ -252,7 +298,7 @@ def main():
     keys = sf.keygen(params, 0)
     cw = sf.ct_words(params)
     pub = torch.from_numpy(keys.public().view(np.int32)).cuda()
-    plan = sf.Plan(params, N1, N2, F, f)
+    plan = sf.Plan(params, N1, N2, F, f, sf.PLAN_INT_KERNEL if args.kernel == "int" else 0)
     info = plan.info
     d_in = torch.empty((info["inputs"], cw), dtype=torch.int32, device="cuda")
     sf.encrypt_bits_device(params, pub, re_, im_, F, f, 0, d_in)

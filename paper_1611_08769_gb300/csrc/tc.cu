@@ -8,18 +8,27 @@
 // so an fp16 x fp16 -> fp32 MMA computes it exactly. Operands are encoded
 // without subnormals: a bit as fp16 1.0, a byte b as fp16 (1024 + b) (bit
 // pattern 0x6400 | b); the 1024 * popcount(A~_i) term is removed in the
-// epilogue. The epilogue then forms K[i][w] = sum_b S[i][4w+b] 2^(8b) and adds
-// the linear terms c0 P + c1 A + c2 B with the limb carries of each element,
+// epilogue. The epilogue forms K[i][w] = sum_b S[i][4w+b] 2^(8b) and adds the
+// linear terms c0 P + c1 A + c2 B with the limb carries of each element,
 // exactly as the integer kernel does.
 //
-// One CTA (4 warps) computes a 128-row tile of one gate's output over all
-// byte columns: A~ tile rows are staged once in shared memory, then for each
-// 64-wide slice of K the threads expand the A bits and the B bytes into
-// 128B-swizzled K-major fp16 tiles (two buffers), one thread issues the
-// tcgen05.mma chain into the TMEM accumulator and commits to an mbarrier, and
-// the next slice is expanded while the tensor core runs. All mbarrier waits
-// are bounded; on timeout the kernel records KERR_MMA_TIMEOUT, waits (bounded)
-// for its own MMAs, frees its TMEM and returns.
+// One CTA (8 warps) computes a 128-row tile of one gate's output over all
+// byte columns:
+//  * the A~ tile (128 rows, contiguous in global memory) arrives by one bulk
+//    copy (cp.async.bulk + mbarrier transaction count) and is complemented in
+//    place when the descriptor asks for P - A;
+//  * B' is consumed in 64-row slices (contiguous); slices are bulk-copied
+//    into a 3-deep shared-memory ring ahead of use;
+//  * per slice, the threads expand A bits and B bytes into 128B-swizzled
+//    K-major fp16 tiles (two buffers) and one thread issues the tcgen05.mma
+//    chain into the TMEM accumulator and commits to an mbarrier; the next
+//    slice is expanded while the tensor core runs;
+//  * the epilogue reads the accumulator with tcgen05.ld, takes A~ and the
+//    tile's B' rows (bulk-copied) from shared memory, builds the two output
+//    tiles in shared memory and writes each back with one bulk store.
+// Every mbarrier wait is bounded (~2 s); on timeout the kernel records
+// KERR_MMA_TIMEOUT, waits (bounded) for its own MMAs, frees its TMEM and
+// returns.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -33,11 +42,12 @@ namespace sfft {
 
 namespace {
 
-constexpr int kThreads = 128;
+constexpr int kThreads = 256;
 constexpr int kTileM = 128;
-constexpr int kBK = 64;                  // K elements per slice (128 bytes of fp16)
+constexpr int kBK = 64;                        // K elements per slice (128 bytes of fp16)
 constexpr uint32_t kSpinLimit = 1u << 26;
-constexpr uint64_t kWaitNs = 2000000000ull;   // bound of any single mbarrier wait
+constexpr uint64_t kWaitNs = 2000000000ull;    // bound of any single mbarrier wait
+constexpr uint32_t kMaxSmem = 232448;          // 227 KB opt-in per CTA
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -73,6 +83,27 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     if ((it & 255u) == 255u && global_ns() - t0 > kWaitNs) return false;
   }
   return false;
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+// Bulk copy global -> shared, completing `bytes` transactions on `bar`.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Bulk copy shared -> global (bulk-group completion).
+__device__ __forceinline__ void bulk_s2g(void* dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
+               "r"(smem_u32(src)), "r"(bytes)
+               : "memory");
 }
 
 __device__ __forceinline__ void fence_proxy_async_smem() {
@@ -164,96 +195,129 @@ __device__ __forceinline__ uint32_t bits2h(uint32_t x) {
 }  // namespace
 
 struct TcShape {
-  uint32_t nd, ndpad, tmem_cols, mtiles, kblocks;
+  uint32_t nd, ndpad, tmem_cols, mtiles, kblocks, nstages;
   uint32_t n0_len, n1_len;   // MMA N of the two column chunks (n1_len 0 if one chunk)
-  uint32_t smem_bytes;
+  uint32_t stage_bytes, ring_bytes, smem_bytes;
 };
+
+namespace {
+
+// Shared-memory layout for W words per row and ring depth ns.
+__host__ __device__ inline void tc_layout(uint32_t W, uint32_t ndpad, uint32_t ns, uint32_t* stage,
+                                          uint32_t* ring, uint32_t* total) {
+  *stage = 16384u + ndpad * 128u;                      // expanded A tile + expanded B tile
+  *ring = (uint32_t)kBK * W * 4u;                      // one raw 64-row slice of B'
+  const uint32_t tileA = (uint32_t)kTileM * W * 4u;
+  uint32_t ring_total = ns * *ring;
+  if (ring_total < tileA) ring_total = tileA;          // the ring also holds the epilogue's B rows
+  *total = 1024u + 2u * *stage + ring_total + tileA + kTileM * 4u + 128u;
+}
+
+}  // namespace
 
 __global__ void __launch_bounds__(kThreads, 1) k_gate_tc(KArgs a, TcShape t) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  const uint32_t W = a.W, L = a.L;
-  const uint32_t btile = t.ndpad * 128u;
-  const uint32_t stage_bytes = 16384u + btile;
+  const uint32_t W = a.W, L = a.L, NP1 = W / L;
   uint8_t* stage0 = smem;
-  uint32_t* sbits = (uint32_t*)(smem + 2 * stage_bytes);            // kTileM x W packed A~ rows
-  uint32_t* spop = sbits + kTileM * W;                               // popcount per row
-  uint64_t* bars = (uint64_t*)(spop + kTileM);                       // 2 mbarriers
-  uint32_t* tslot = (uint32_t*)(bars + 2);
+  uint8_t* ring = smem + 2 * t.stage_bytes;
+  uint32_t ring_total = t.nstages * t.ring_bytes;
+  if (ring_total < (uint32_t)kTileM * W * 4u) ring_total = kTileM * W * 4u;
+  uint32_t* tileA = (uint32_t*)(ring + ring_total);                // A~ rows of the tile
+  uint32_t* spop = tileA + kTileM * W;                              // popcount per row
+  uint64_t* bars = (uint64_t*)(spop + kTileM);
+  uint64_t* full = bars;                                            // [nstages] ring slots
+  uint64_t* mmab = bars + 4;                                        // [2] MMA commits
+  uint64_t* abar = bars + 6;                                        // A tile arrived
+  uint64_t* ebar = bars + 7;                                        // epilogue B rows arrived
+  uint32_t* tslot = (uint32_t*)(bars + 8);
 
   const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint64_t g = blockIdx.x / t.mtiles;
   const uint32_t row0 = (blockIdx.x % t.mtiles) * kTileM;
   if (g >= a.n) return;
+  const uint32_t rows = (a.Ng - row0) < (uint32_t)kTileM ? (a.Ng - row0) : (uint32_t)kTileM;
   const GateDesc d = a.desc[g];
   const GateAux x = a.aux[g];
   const bool gen = (d.a >> 30) == REG_GEN;
   const uint32_t* A = gen ? nullptr : a.base[d.a >> 30] + (uint64_t)(d.a & SLOT_MASK) * a.ctw;
   const uint64_t gst = gen ? stream_out(a.gen_state, d.a & SLOT_MASK) : 0;
   const uint32_t* B = a.base[d.b >> 30] + (uint64_t)(d.b & SLOT_MASK) * a.ctw;
+  const bool comp = (x.flags & 1u) != 0;
 
   if (tid == 0) {
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
+    for (int b = 0; b < 8; b++) mbar_init(&bars[b], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) tmem_alloc(tslot, t.tmem_cols);
-
-  // Stage the A~ rows of this tile (coalesced), zero the padded B rows.
-  for (uint32_t e = tid; e < kTileM * W; e += kThreads) {
-    const uint32_t r = e / W, w = e % W, i = row0 + r;
-    uint32_t v = 0;
-    if (i < a.Ng) v = gen ? r_word(gst, (uint64_t)i * W + w) : __ldg(A + (uint64_t)i * W + w);
-    sbits[e] = v;
+  __syncthreads();
+  if (tid == 0) {
+    if (!gen) {
+      mbar_expect_tx(abar, rows * W * 4u);
+      bulk_g2s(tileA, A + (uint64_t)row0 * W, rows * W * 4u, abar);
+    }
+    for (uint32_t s = 0; s < t.nstages && s < t.kblocks; s++) {
+      const uint32_t krows = (a.Ng - s * kBK) < (uint32_t)kBK ? (a.Ng - s * kBK) : (uint32_t)kBK;
+      mbar_expect_tx(&full[s], krows * W * 4u);
+      bulk_g2s(ring + s * t.ring_bytes, B + (uint64_t)s * kBK * W, krows * W * 4u, &full[s]);
+    }
   }
+  // zero the padded byte-column rows of both expanded B tiles (never rewritten)
   for (uint32_t e = tid; e < (t.ndpad - t.nd) * 32u; e += kThreads) {
     const uint32_t r = t.nd + e / 32, c = e % 32;
     ((uint32_t*)(stage0 + 16384u + r * 128u))[c] = 0;
-    ((uint32_t*)(stage0 + stage_bytes + 16384u + r * 128u))[c] = 0;
+    ((uint32_t*)(stage0 + t.stage_bytes + 16384u + r * 128u))[c] = 0;
+  }
+  bool timed_out = false;
+  if (gen) {
+    for (uint32_t e = tid; e < kTileM * W; e += kThreads) {
+      const uint32_t r = e / W, w = e % W;
+      tileA[e] = r < rows ? r_word(gst, (uint64_t)(row0 + r) * W + w) : 0u;
+    }
+  } else {
+    timed_out = !mbar_wait_bounded(abar, 0);
+    for (uint32_t e = rows * W + tid; e < kTileM * W; e += kThreads) tileA[e] = 0;
   }
   __syncthreads();
   // Complement (P - A) row by row with the borrow chain of each element; popcount.
-  {
+  if (tid < kTileM) {
     const uint32_t r = tid, i = row0 + r;
     uint32_t pc = 0, borrow = 0;
-    const bool comp = (x.flags & 1u) != 0;
     for (uint32_t w = 0; w < W; w++) {
-      uint32_t v = sbits[r * W + w];
-      if (comp && i < a.Ng) {
+      uint32_t v = tileA[r * W + w];
+      if (comp && r < rows) {
         const uint32_t l = w % L;
         if (l == 0) borrow = 0;
         const uint64_t dv = (uint64_t)p_word(i, w / L, l, a.ell) - v - borrow;
         v = (uint32_t)dv;
         borrow = (uint32_t)(dv >> 63);
-        sbits[r * W + w] = v;
+        tileA[r * W + w] = v;
       }
       pc += __popc(v);
     }
     spop[r] = pc;
   }
   tc_fence_before();
-  __syncthreads();
+  bool ok = !__syncthreads_or(timed_out);
   tc_fence_after();
   const uint32_t tmem = *tslot;
 
-  bool ok = true;
   const uint32_t idesc0 = idesc_f16(kTileM, t.n0_len), idesc1 = idesc_f16(kTileM, t.n1_len);
-  for (uint32_t kb = 0; kb < t.kblocks; kb++) {
-    const uint32_t s = kb & 1;
-    uint8_t* sA = stage0 + s * stage_bytes;
+  for (uint32_t kb = 0; ok && kb < t.kblocks; kb++) {
+    const uint32_t s = kb & 1, slot = kb % t.nstages;
+    uint8_t* sA = stage0 + s * t.stage_bytes;
     uint8_t* sB = sA + 16384u;
-    // the MMAs of slice kb-2 read this buffer: wait for their commit (block-uniform outcome)
-    const bool waited = kb < 2 || mbar_wait_bounded(&bars[s], ((kb - 2) >> 1) & 1);
-    if (__syncthreads_or(!waited)) {
-      ok = false;
-      break;
-    }
-    // A~ slice: 128 rows x 64 bits -> fp16 {0,1}; thread handles (row, 16-byte chunk).
+    const uint32_t* raw = (const uint32_t*)(ring + slot * t.ring_bytes);
+    // the MMAs of slice kb-2 read this stage; slice kb's raw rows must have landed
+    bool w_ok = kb < 2 || mbar_wait_bounded(&mmab[s], ((kb - 2) >> 1) & 1);
+    w_ok = w_ok && mbar_wait_bounded(&full[slot], (kb / t.nstages) & 1);
+    const uint32_t krows = (a.Ng - kb * kBK) < (uint32_t)kBK ? (a.Ng - kb * kBK) : (uint32_t)kBK;
+    // A~ slice: 128 rows x 64 bits -> fp16 {0,1}; task = (row, 16-byte chunk)
     for (uint32_t e = tid; e < kTileM * 8u; e += kThreads) {
       const uint32_t r = e >> 3, c = e & 7;
-      const uint32_t kbit = kb * kBK + c * 8;        // first K index of the chunk
+      const uint32_t kbit = kb * kBK + c * 8;
       const uint32_t wi = kbit >> 5;
-      const uint32_t byte = wi < W ? (sbits[r * W + wi] >> (kbit & 31)) & 0xFFu : 0u;
+      const uint32_t byte = wi < W ? (tileA[r * W + wi] >> (kbit & 31)) & 0xFFu : 0u;
       uint4 v;
       v.x = bits2h(byte);
       v.y = bits2h(byte >> 2);
@@ -261,14 +325,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_gate_tc(KArgs a, TcShape t) {
       v.w = bits2h(byte >> 6);
       *(uint4*)(sA + sw128_off(r, c)) = v;
     }
-    // B slice: rows k of B' (64 of them) -> byte columns n = 4w + b as fp16 1024 + byte.
+    // B slice: raw rows k (64) -> byte columns n = 4w + b as fp16 (1024 + byte)
     for (uint32_t e = tid; e < 8u * W; e += kThreads) {
       const uint32_t c = e & 7, w = e >> 3;
       uint32_t xw[8];
 #pragma unroll
       for (int q = 0; q < 8; q++) {
-        const uint32_t k = kb * kBK + c * 8 + q;
-        xw[q] = k < a.Ng ? __ldg(B + (uint64_t)k * W + w) : 0u;
+        const uint32_t k = c * 8 + q;
+        xw[q] = k < krows ? raw[k * W + w] : 0u;
       }
 #pragma unroll
       for (int b = 0; b < 4; b++) {
@@ -280,13 +344,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_gate_tc(KArgs a, TcShape t) {
         v.y = (__byte_perm(xw[2], xw[3], sel) & 0x00FF00FFu) | 0x64006400u;
         v.z = (__byte_perm(xw[4], xw[5], sel) & 0x00FF00FFu) | 0x64006400u;
         v.w = (__byte_perm(xw[6], xw[7], sel) & 0x00FF00FFu) | 0x64006400u;
-        const uint32_t n = 4 * w + b;
-        *(uint4*)(sB + sw128_off(n, c)) = v;
+        *(uint4*)(sB + sw128_off(4 * w + b, c)) = v;
       }
     }
     fence_proxy_async_smem();
-    __syncthreads();
+    if (__syncthreads_or(!w_ok)) {
+      ok = false;
+      break;
+    }
     if (tid == 0) {
+      // refill the ring slot just consumed
+      const uint32_t nk = kb + t.nstages;
+      if (nk < t.kblocks) {
+        const uint32_t nrows = (a.Ng - nk * kBK) < (uint32_t)kBK ? (a.Ng - nk * kBK) : (uint32_t)kBK;
+        mbar_expect_tx(&full[slot], nrows * W * 4u);
+        bulk_g2s(ring + slot * t.ring_bytes, B + (uint64_t)nk * kBK * W, nrows * W * 4u, &full[slot]);
+      }
       tc_fence_after();
       const uint32_t a_base = smem_u32(sA), b_base = smem_u32(sB);
 #pragma unroll
@@ -297,61 +370,89 @@ __global__ void __launch_bounds__(kThreads, 1) k_gate_tc(KArgs a, TcShape t) {
           mma_f16(tmem + t.n0_len, ad, sw128_desc(b_base + t.n0_len * 128u + ks * 32), idesc1,
                   (kb | ks) != 0);
       }
-      mma_commit(&bars[s]);
+      mma_commit(&mmab[s]);
     }
   }
+  // B rows of this tile (linear term c2 B) into the ring, which is free now
+  if (ok && tid == 0) {
+    mbar_expect_tx(ebar, rows * W * 4u);
+    bulk_g2s(ring, B + (uint64_t)row0 * W, rows * W * 4u, ebar);
+  }
+  const uint32_t last = t.kblocks - 1;
   if (ok) {
-    const uint32_t last = t.kblocks - 1;
-    ok = !__syncthreads_or(!mbar_wait_bounded(&bars[last & 1], (last >> 1) & 1));
+    bool w_ok = mbar_wait_bounded(&mmab[last & 1], (last >> 1) & 1);
+    w_ok = w_ok && mbar_wait_bounded(ebar, 0);
+    ok = !__syncthreads_or(!w_ok);
   }
   if (!ok) {
     if (tid == 0 && a.err) atomicExch(a.err, KERR_MMA_TIMEOUT);
-    // give in-flight MMAs a bounded chance to finish before TMEM is released
-    const uint32_t last = t.kblocks - 1;
-    mbar_wait_bounded(&bars[last & 1], (last >> 1) & 1);
+    mbar_wait_bounded(&mmab[last & 1], (last >> 1) & 1);   // bounded: let own MMAs drain
   }
   tc_fence_after();
 
   if (ok) {
-    // Epilogue: warp w owns TMEM lanes 32w .. 32w+31 = tile rows; thread = row.
-    const uint32_t r = warp * 32 + lane, i = row0 + r;
-    const bool live = i < a.Ng;
+    // Epilogue: warp w reads TMEM lanes 32 (w % 4) ..; warps 0-3 and 4-7 take
+    // alternate elements of the row. Outputs go to row-major tiles in the
+    // (now idle) expanded stages.
+    const uint32_t r = (warp & 3) * 32 + lane, i = row0 + r;
+    const bool live = r < rows;
     const int64_t bias = 1024 * (int64_t)spop[r];
-    uint32_t* O0 = d.o0 == REF_NONE ? nullptr : a.base[d.o0 >> 30] + (uint64_t)(d.o0 & SLOT_MASK) * a.ctw;
-    uint32_t* O1 = d.o1 == REF_NONE ? nullptr : a.base[d.o1 >> 30] + (uint64_t)(d.o1 & SLOT_MASK) * a.ctw;
-    const uint32_t code0 = x.code & 0xFFFFu, code1 = x.code >> 16;
-    int64_t carry0 = 0, carry1 = 0;
-    for (uint32_t n0 = 0; n0 < t.nd; n0 += 16) {
-      uint32_t v[16];
-      tmem_ld16(tmem + ((warp * 32u) << 16) + n0, v);
+    const uint32_t* Bt = (const uint32_t*)ring;
+    uint32_t* T0 = (uint32_t*)stage0;
+    uint32_t* T1 = (uint32_t*)(stage0 + t.stage_bytes);
+    uint32_t code0 = x.code & 0xFFFFu, code1 = x.code >> 16;
+    int c00 = nib(code0, 0), c01 = nib(code0, 1), c02 = nib(code0, 2), c03 = nib(code0, 3);
+    int c10 = nib(code1, 0), c11 = nib(code1, 1), c12 = nib(code1, 2), c13 = nib(code1, 3);
+    if (comp) {  // the stored A is P - A~: c1 A = c1 P - c1 A~
+      c00 += c01;
+      c01 = -c01;
+      c10 += c11;
+      c11 = -c11;
+    }
+    const bool has0 = d.o0 != REF_NONE, has1 = d.o1 != REF_NONE;
+    for (uint32_t j = warp >> 2; j < NP1; j += 2) {
+      int64_t carry0 = 0, carry1 = 0;
+      const uint32_t wbeg = j * L, wend = wbeg + L;
+      for (uint32_t n0 = (4 * wbeg) & ~15u; n0 < 4 * wend; n0 += 16) {
+        uint32_t v[16];
+        tmem_ld16(tmem + (((warp & 3) * 32u) << 16) + n0, v);
 #pragma unroll
-      for (int q = 0; q < 4; q++) {
-        const uint32_t w = n0 / 4 + q;
-        if (w >= W || !live) continue;
-        int64_t k = 0;
+        for (int q = 0; q < 4; q++) {
+          const uint32_t w = n0 / 4 + q;
+          if (w < wbeg || w >= wend || !live) continue;
+          int64_t k = 0;
 #pragma unroll
-        for (int b = 0; b < 4; b++) {
-          const int64_t sv = (int64_t)__float2int_rn(__uint_as_float(v[4 * q + b])) - bias;
-          k += sv << (8 * b);
-        }
-        const uint32_t l = w % L;
-        if (l == 0) carry0 = carry1 = 0;
-        const int64_t aw = A ? (int64_t)__ldg(A + (uint64_t)i * W + w) : 0;
-        const int64_t bw = (int64_t)__ldg(B + (uint64_t)i * W + w);
-        const int64_t pw = (int64_t)p_word(i, w / L, l, a.ell);
-        if (O0) {
-          const int64_t o = nib(code0, 3) * k + nib(code0, 1) * aw + nib(code0, 2) * bw +
-                            nib(code0, 0) * pw + carry0;
-          O0[(uint64_t)i * W + w] = (uint32_t)o;
-          carry0 = o >> 32;
-        }
-        if (O1) {
-          const int64_t o = nib(code1, 3) * k + nib(code1, 1) * aw + nib(code1, 2) * bw +
-                            nib(code1, 0) * pw + carry1;
-          O1[(uint64_t)i * W + w] = (uint32_t)o;
-          carry1 = o >> 32;
+          for (int b = 0; b < 4; b++) {
+            const int64_t sv = (int64_t)__float2int_rn(__uint_as_float(v[4 * q + b])) - bias;
+            k += sv << (8 * b);
+          }
+          const int64_t aw = (int64_t)tileA[r * W + w];
+          const int64_t bw = (int64_t)Bt[r * W + w];
+          const int64_t pw = (int64_t)p_word(i, j, w - wbeg, a.ell);
+          if (has0) {
+            const int64_t o = c03 * k + c01 * aw + c02 * bw + c00 * pw + carry0;
+            T0[r * W + w] = (uint32_t)o;
+            carry0 = o >> 32;
+          }
+          if (has1) {
+            const int64_t o = c13 * k + c11 * aw + c12 * bw + c10 * pw + carry1;
+            T1[r * W + w] = (uint32_t)o;
+            carry1 = o >> 32;
+          }
         }
       }
+    }
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      if (has0)
+        bulk_s2g(a.base[d.o0 >> 30] + (uint64_t)(d.o0 & SLOT_MASK) * a.ctw + (uint64_t)row0 * W, T0,
+                 rows * W * 4u);
+      if (has1)
+        bulk_s2g(a.base[d.o1 >> 30] + (uint64_t)(d.o1 & SLOT_MASK) * a.ctw + (uint64_t)row0 * W, T1,
+                 rows * W * 4u);
+      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+      asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
     }
   }
   tc_fence_before();
@@ -362,27 +463,46 @@ __global__ void __launch_bounds__(kThreads, 1) k_gate_tc(KArgs a, TcShape t) {
   }
 }
 
-bool tc_supported(const KArgs& a) { return a.Ng >= 128 && a.W * 4 <= 512 - 16; }
+namespace {
+
+bool make_tc_shape(const KArgs& a, TcShape* t) {
+  if (a.Ng < 128) return false;
+  t->nd = a.W * 4;
+  t->ndpad = (t->nd + 15) / 16 * 16;
+  if (t->ndpad > 512) return false;
+  t->n0_len = t->ndpad < 256 ? t->ndpad : 256;
+  t->n1_len = t->ndpad - t->n0_len;
+  t->tmem_cols = 32;
+  while (t->tmem_cols < t->ndpad) t->tmem_cols *= 2;
+  t->mtiles = (a.Ng + kTileM - 1) / kTileM;
+  t->kblocks = (a.Ng + kBK - 1) / kBK;
+  for (uint32_t ns = 3; ns >= 2; ns--) {
+    tc_layout(a.W, t->ndpad, ns, &t->stage_bytes, &t->ring_bytes, &t->smem_bytes);
+    if (t->smem_bytes <= kMaxSmem) {
+      t->nstages = ns;
+      return true;
+    }
+  }
+  return false;
+}
+
+}  // namespace
+
+bool tc_supported(const KArgs& a) {
+  TcShape t;
+  return make_tc_shape(a, &t);
+}
 
 int launch_gates_tc(const KArgs& a, cudaStream_t st) {
   if (a.n == 0) return SFFT_OK;
   TcShape t{};
-  t.nd = a.W * 4;
-  t.ndpad = (t.nd + 15) / 16 * 16;
-  t.n0_len = t.ndpad < 256 ? t.ndpad : 256;
-  t.n1_len = t.ndpad - t.n0_len;
-  t.tmem_cols = 32;
-  while (t.tmem_cols < t.ndpad) t.tmem_cols *= 2;
-  t.mtiles = (a.Ng + kTileM - 1) / kTileM;
-  t.kblocks = (a.Ng + kBK - 1) / kBK;
-  const uint32_t stage_bytes = 16384u + t.ndpad * 128u;
-  t.smem_bytes = 1024 + 2 * stage_bytes + kTileM * a.W * 4 + kTileM * 4 + 64;
+  if (!make_tc_shape(a, &t)) return fail(SFFT_EPARAM, "tensor-core kernel does not support this shape");
   static uint32_t configured = 0;
   if (t.smem_bytes > configured) {
     cudaError_t e = cudaFuncSetAttribute(k_gate_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)t.smem_bytes);
+                                         (int)kMaxSmem);
     if (e != cudaSuccess) return cuda_fail(e, "tc smem attribute");
-    configured = t.smem_bytes;
+    configured = kMaxSmem;
   }
   const uint64_t blocks = a.n * t.mtiles;
   k_gate_tc<<<(unsigned)blocks, kThreads, t.smem_bytes, st>>>(a, t);

@@ -39,7 +39,14 @@ KArgs make_args(const Shape& s) {
   return a;
 }
 
-// Launches one level of gates with the integer kernel.
+uint64_t scratch_layout(const Shape& s, uint64_t slots, uint64_t max_width, bool tc, uint64_t* bx_off) {
+  const uint64_t wires = slots * s.ctw * 4;
+  *bx_off = (wires + 255) & ~255ull;
+  if (!tc) return wires;
+  return *bx_off + tc_bx_bytes(make_args(s), max_width);
+}
+
+// Launches one level of gates (tensor-core kernel where it applies).
 int launch_gates(const KArgs& a, cudaStream_t st) {
   if (a.n == 0) return SFFT_OK;
   if (a.kernel != KERNEL_INT && tc_supported(a)) return launch_gates_tc(a, st);
@@ -84,10 +91,11 @@ Timer::~Timer() {
 int run_program(const Shape& s, const DeviceProgram& dp, const uint32_t* d_in, uint32_t* d_out,
                 uint32_t* d_scratch, uint64_t scratch_bytes, cudaStream_t st, Timer* tm) {
   if (!d_in || !d_out) return fail(SFFT_EINVAL, "null buffer");
-  if (scratch_bytes < dp.scratch_slots * s.ctw * 4 || (dp.scratch_slots && !d_scratch))
+  if (scratch_bytes < dp.scratch_bytes || (dp.scratch_bytes && !d_scratch))
     return fail(SFFT_EINVAL, "scratch buffer too small");
   KArgs a = make_args(s);
   a.base[REG_SCRATCH] = d_scratch;
+  a.bx = dp.tc ? (uint8_t*)d_scratch + dp.bx_off : nullptr;
   a.base[REG_IN] = const_cast<uint32_t*>(d_in);
   a.base[REG_OUT] = d_out;
   a.base[REG_GEN] = nullptr;
@@ -198,6 +206,10 @@ int sfft_plan_create(const sfft_params* p, uint32_t N1, uint32_t N2, uint32_t F,
   pl->F = F;
   pl->f = f;
   pl->dev.kernel = (flags & SFFT_PLAN_INT_KERNEL) ? KERNEL_INT : KERNEL_AUTO;
+  pl->dev.max_width = pl->prog.max_width;
+  pl->dev.tc = pl->dev.kernel != KERNEL_INT && tc_supported(make_args(pl->s));
+  pl->dev.scratch_bytes = scratch_layout(pl->s, pl->prog.scratch_slots, pl->prog.max_width,
+                                         pl->dev.tc, &pl->dev.bx_off);
   *out = pl.release();
   return SFFT_OK;
 }
@@ -215,7 +227,7 @@ int sfft_plan_info_get(const sfft_plan* pl, sfft_plan_info* info) {
   info->levels = pl->prog.level_off.size() - 1;
   info->max_level_width = pl->prog.max_width;
   info->scratch_slots = pl->prog.scratch_slots;
-  info->scratch_bytes = pl->prog.scratch_slots * pl->s.ctw * 4;
+  info->scratch_bytes = pl->dev.scratch_bytes;
   info->ct_words = pl->s.ctw;
   info->noise_bits = pl->prog.noise_bits;
   info->noise_ok = pl->prog.noise_ok ? 1 : 0;
@@ -313,12 +325,22 @@ int sfft_gate_level(const sfft_params* p, const uint32_t* d_a, const uint32_t* d
   a.kernel = kernel;
   cudaMalloc((void**)&a.err, sizeof(int));
   if (a.err) cudaMemset(a.err, 0, sizeof(int));
+  if (kernel != KERNEL_INT && tc_supported(a)) {
+    cudaError_t me = cudaMalloc((void**)&a.bx, tc_bx_bytes(a, n_gates));
+    if (me != cudaSuccess) {
+      cudaFree(dd);
+      cudaFree(da);
+      cudaFree(a.err);
+      return cuda_fail(me, "cudaMalloc");
+    }
+  }
   rc = launch_gates(a, st);
   cudaError_t e = cudaStreamSynchronize(st);
   if (!rc && e == cudaSuccess) rc = check_device_error(a.err, st);
   cudaFree(dd);
   cudaFree(da);
   cudaFree(a.err);
+  cudaFree(a.bx);
   if (rc) return rc;
   return e == cudaSuccess ? SFFT_OK : cuda_fail(e, "gate level");
 }
@@ -356,10 +378,20 @@ int sfft_encrypt_bits_device(const sfft_params* p, const uint32_t* d_pub, const 
   a.base[REG_OUT] = d_ct_out;
   a.gen_state = domain_key(enc_seed, kDomR);
   cudaStream_t st = (cudaStream_t)stream;
+  if (tc_supported(a)) {  // every gate multiplies by the same public matrix: expand it once
+    a.bx_shared = 1;
+    cudaError_t me = cudaMalloc((void**)&a.bx, tc_bx_bytes_per_gate(a));
+    if (me != cudaSuccess) {
+      cudaFree(dd);
+      cudaFree(da);
+      return cuda_fail(me, "cudaMalloc");
+    }
+  }
   rc = launch_gates(a, st);
   cudaError_t e = cudaStreamSynchronize(st);
   cudaFree(dd);
   cudaFree(da);
+  cudaFree(a.bx);
   if (rc) return rc;
   return e == cudaSuccess ? SFFT_OK : cuda_fail(e, "device encryption");
 }

@@ -17,6 +17,8 @@ struct KArgs {
   uint64_t ctw;
   int* err;              // device error word (bounded waits that ran out), may be null
   uint32_t kernel;       // KERNEL_AUTO / KERNEL_INT / KERNEL_TC
+  uint8_t* bx;           // tensor-core kernel: expanded B operands (scratch)
+  uint32_t bx_shared;    // 1: every gate has the same B operand (expanded once)
 };
 
 constexpr uint32_t KERNEL_AUTO = 0, KERNEL_INT = 1, KERNEL_TC = 2;

@@ -9,6 +9,7 @@
 
 namespace sfft {
 bool tc_supported(const KArgs& a);
+uint64_t tc_bx_bytes(const KArgs& a, uint64_t gates);
 }
 
 using namespace sfft;
@@ -50,7 +51,16 @@ int sfft_circuit_info(const sfft_params* p, uint32_t N1, uint32_t N2, uint32_t F
   info->levels = prog.level_off.size() - 1;
   info->max_level_width = prog.max_width;
   info->scratch_slots = prog.scratch_slots;
-  info->scratch_bytes = prog.scratch_slots * s.ctw * 4;
+  {
+    KArgs k{};
+    k.Ng = s.Ng;
+    k.W = s.W;
+    uint64_t bx_off = 0;
+    const bool tc = tc_supported(k);
+    const uint64_t wires = prog.scratch_slots * s.ctw * 4;
+    bx_off = (wires + 255) & ~255ull;
+    info->scratch_bytes = tc ? bx_off + tc_bx_bytes(k, prog.max_width) : wires;
+  }
   info->ct_words = s.ctw;
   info->noise_bits = prog.noise_bits;
   info->noise_ok = prog.noise_ok ? 1 : 0;

@@ -54,7 +54,7 @@ int scratch_on_current_device(uint32_t** out) {
 extern "C" int sfft_eval_fft_noalloc(sfft_plan* pl, const uint32_t* d_in, uint32_t* d_out,
                                      void* stream) {
   if (!pl) return sfft::fail(SFFT_EINVAL, "plan is NULL");
-  const uint64_t need = pl->prog.scratch_slots * pl->s.ctw * 4;
+  const uint64_t need = pl->dev.scratch_bytes;
   if (need > kNoAllocScratchBytes)
     return sfft::fail(SFFT_EINVAL, "plan needs " + std::to_string(need) +
                                        " bytes of scratch; sfft_eval_fft_noalloc holds at most " +

@@ -21,6 +21,10 @@ struct DeviceProgram {
   uint64_t scratch_slots = 0;
   int* err = nullptr;            // device error word of the kernels
   uint32_t kernel = 0;           // KERNEL_AUTO / KERNEL_INT / KERNEL_TC
+  uint64_t max_width = 0;        // products in the widest level
+  bool tc = false;               // levels run on the tensor-core kernel
+  uint64_t scratch_bytes = 0;    // wire slots + expanded B operands
+  uint64_t bx_off = 0;           // offset of the expanded B operands in scratch
 };
 
 // Reads and clears the device error word (synchronises the stream).
@@ -33,6 +37,14 @@ int launch_gates(const KArgs& a, cudaStream_t st);
 // Tensor-core gate kernel (tc.cu): shapes it supports, and its launcher.
 bool tc_supported(const KArgs& a);
 int launch_gates_tc(const KArgs& a, cudaStream_t st);
+// Bytes of the expanded B operand of one gate (0 if the shape is unsupported),
+// and of the expansion buffer a launch of `gates` gates needs (levels run in
+// L2-sized chunks of gates that share one buffer).
+uint64_t tc_bx_bytes_per_gate(const KArgs& a);
+uint64_t tc_bx_bytes(const KArgs& a, uint64_t gates);
+// Scratch layout of a program: wire slots first, then (tensor-core kernel) the
+// expanded B operands of the widest level, 256-byte aligned.
+uint64_t scratch_layout(const Shape& s, uint64_t slots, uint64_t max_width, bool tc, uint64_t* bx_off);
 int make_device_program(const Program& p, DeviceProgram* dp);
 void free_device_program(DeviceProgram* dp);
 // Optional per-launch CUDA-event timing of gate kernels.

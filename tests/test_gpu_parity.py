@@ -39,7 +39,7 @@ CODES = {"XOR": (0, 1, 1, -2), "AND": (0, 0, 0, 1), "OR": (0, 1, 1, -1), "NAND":
 GATE_CASES = [(1, 32, sf.KERNEL_INT), (1, 128, sf.KERNEL_INT), (1, 224, sf.KERNEL_INT),
               (2, 64, sf.KERNEL_INT), (1, 1056, sf.KERNEL_INT),
               (1, 128, sf.KERNEL_TC), (1, 224, sf.KERNEL_TC), (2, 64, sf.KERNEL_TC),
-              (1, 1056, sf.KERNEL_TC), (1, 1344, sf.KERNEL_TC), (1, 1984, sf.KERNEL_AUTO)]
+              (1, 1056, sf.KERNEL_TC), (1, 1216, sf.KERNEL_TC), (1, 1984, sf.KERNEL_AUTO)]
 
 
 @pytest.mark.parametrize("n,ell,kernel", GATE_CASES)

@@ -64,6 +64,9 @@ typedef struct sfft_server sfft_server;
 
 const char* sfft_last_error(void);
 const char* sfft_version(void);
+/* Running count of kernel launches this library has issued in the process
+ * (graph replays excluded: they re-run launches counted at capture). */
+uint64_t sfft_launch_count(void);
 
 /* Words (uint32) of one compressed ciphertext: Ng * (n+1) * ell/32. */
 uint64_t sfft_ct_words(const sfft_params* p);
@@ -209,6 +212,42 @@ uint64_t sfft_noalloc_scratch_bytes(void);
  * then resets. */
 int sfft_plan_set_timing(sfft_plan* plan, int on);
 int sfft_plan_timing(sfft_plan* plan, double* gate_ms, uint64_t* launches, uint64_t* products);
+
+/* ------------------------------------------------------------- batches */
+
+/* One encrypted-FFT request: 1-D (N2 == 1) or N1 x N2 2-D, F-bit words with
+ * f fraction bits. */
+typedef struct sfft_request {
+  uint32_t N1, N2, F, f;
+} sfft_request;
+
+/* Batched form of step 4: the circuits of `count` requests are built and
+ * their levels merged (level l of the batch = every request's products of
+ * multiplicative depth l, evaluated by the same launches), so many requests
+ * share each launch. GSW leveled evaluation has no evaluation key, so the
+ * requests may come from different client key sets (same n, ell). Inputs and
+ * outputs are the requests' ciphertexts concatenated in request order
+ * (sfft_batch_offsets gives each request's first ciphertext). Unless
+ * SFFT_BATCH_NO_GRAPH, sfft_batch_eval captures the whole launch sequence as
+ * a CUDA graph on first use and replays it (re-captured when a pointer or
+ * the stream changes; needs a non-default stream). flags: SFFT_PLAN_* too. */
+#define SFFT_BATCH_NO_GRAPH 4u
+int sfft_batch_create(const sfft_params* p, const sfft_request* reqs, uint32_t count,
+                      uint32_t flags, sfft_batch** out);
+int sfft_batch_info_get(const sfft_batch* b, sfft_plan_info* info);
+int sfft_batch_offsets(const sfft_batch* b, uint64_t* h_in_off, uint64_t* h_out_off);
+int sfft_batch_eval(sfft_batch* b, const uint32_t* d_in, uint32_t* d_out, uint32_t* d_scratch,
+                    uint64_t scratch_bytes, void* stream);
+/* End to end from host buffers: H2D of all inputs, evaluation, D2H of all
+ * outputs, then waits for the stream. */
+int sfft_batch_eval_host(sfft_batch* b, const uint32_t* h_in, uint32_t* h_out, uint32_t* d_in,
+                         uint32_t* d_out, uint32_t* d_scratch, uint64_t scratch_bytes,
+                         void* stream);
+int sfft_batch_check(sfft_batch* b, void* stream);
+/* Per-launch event timing (graph replay is bypassed while timing is on). */
+int sfft_batch_set_timing(sfft_batch* b, int on);
+int sfft_batch_timing(sfft_batch* b, double* gate_ms, uint64_t* launches, uint64_t* products);
+void sfft_batch_free(sfft_batch* b);
 
 /* Evaluates a single level of gates given explicitly (test hook): gate g
  * computes, with A = d_a[g] (complemented to P - A first when

@@ -201,6 +201,59 @@ class Plan:
             self._h = None
 
 
+BATCH_NO_GRAPH = 4
+
+
+class Batch:
+    """Many FFT requests evaluated level-merged (sfft_batch_create), graph-replayed."""
+
+    def __init__(self, params, requests, flags=0):
+        self.params = params
+        self.requests = [tuple(r) for r in requests]
+        arr = (native.sfft_request * len(self.requests))(*[native.sfft_request(*r) for r in self.requests])
+        h = ctypes.c_void_p()
+        check(lib().sfft_batch_create(ctypes.byref(params), arr, len(self.requests), flags,
+                                      ctypes.byref(h)))
+        self._h = h
+        info = sfft_plan_info()
+        check(lib().sfft_batch_info_get(h, ctypes.byref(info)))
+        self.info = {k: getattr(info, k) for k, _ in sfft_plan_info._fields_}
+        n = len(self.requests)
+        i_off = (ctypes.c_uint64 * n)()
+        o_off = (ctypes.c_uint64 * n)()
+        check(lib().sfft_batch_offsets(h, i_off, o_off))
+        self.in_off, self.out_off = list(i_off), list(o_off)
+
+    def eval(self, d_in, d_out, d_scratch, stream=None):
+        nbytes = 0 if d_scratch is None else d_scratch.numel() * d_scratch.element_size()
+        check(lib().sfft_batch_eval(self._h, _dptr(d_in), _dptr(d_out), _dptr(d_scratch), nbytes,
+                                    _stream(stream)))
+
+    def eval_host(self, h_in, h_out, d_in, d_out, d_scratch, stream=None):
+        nbytes = 0 if d_scratch is None else d_scratch.numel() * d_scratch.element_size()
+        check(lib().sfft_batch_eval_host(self._h, _dptr(h_in), _dptr(h_out), _dptr(d_in),
+                                         _dptr(d_out), _dptr(d_scratch), nbytes, _stream(stream)))
+
+    def check(self, stream=None):
+        check(lib().sfft_batch_check(self._h, _stream(stream)))
+
+    def set_timing(self, on):
+        check(lib().sfft_batch_set_timing(self._h, 1 if on else 0))
+
+    def timing(self):
+        ms = ctypes.c_double()
+        n = ctypes.c_uint64()
+        g = ctypes.c_uint64()
+        check(lib().sfft_batch_timing(self._h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(g)))
+        return ms.value, n.value, g.value
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            lib().sfft_batch_free(h)
+            self._h = None
+
+
 def gate_level(params, d_a, d_b, d_out0, d_out1, code0, code1, flags, stream=None, kernel=0):
     code0 = np.ascontiguousarray(code0, dtype=np.uint16)
     code1 = np.ascontiguousarray(code1, dtype=np.uint16)

@@ -2,6 +2,7 @@
 // the single-level gate hook and decryption-row gathering.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstring>
 #include <memory>
 #include <string>
@@ -39,6 +40,9 @@ KArgs make_args(const Shape& s) {
   return a;
 }
 
+static std::atomic<uint64_t> g_launches{0};
+void count_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
 uint64_t scratch_layout(const Shape& s, uint64_t slots, uint64_t max_width, bool tc, uint64_t* bx_off) {
   const uint64_t wires = slots * s.ctw * 4;
   *bx_off = (wires + 255) & ~255ull;
@@ -59,6 +63,7 @@ int launch_gates(const KArgs& a, cudaStream_t st) {
     k_gate_generic<4><<<(unsigned)blocks, 256, 0, st>>>(a);
   else
     k_gate_generic<8><<<(unsigned)blocks, 256, 0, st>>>(a);
+  count_launches(1);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? SFFT_OK : cuda_fail(e, "gate kernel launch");
 }
@@ -117,6 +122,7 @@ int run_program(const Shape& s, const DeviceProgram& dp, const uint32_t* d_in, u
   }
   if (dp.n_fix) {
     k_fixup<<<(unsigned)dp.n_fix, 256, 0, st>>>(dp.fix, dp.n_fix, a);
+    count_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "fixup launch");
   }
@@ -171,6 +177,8 @@ using namespace sfft;
 extern "C" {
 
 const char* sfft_version(void) { return "sfft-gb300 0.1 (sm_103a)"; }
+
+uint64_t sfft_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 uint32_t sfft_min_ell(uint32_t N1, uint32_t N2, uint32_t F, uint32_t f, uint32_t n, uint32_t chi) {
   Circuit c;

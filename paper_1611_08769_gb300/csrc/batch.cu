@@ -1,0 +1,267 @@
+// Batched evaluation: many FFT requests' circuit levels merged into one
+// program, optionally replayed as a CUDA graph.
+//
+// Level l of the merged program holds every request's products of
+// multiplicative depth l (all independent), so one launch covers them all;
+// wire references are shifted into per-request ranges of one input buffer,
+// one output buffer and one scratch pool. GSW leveled evaluation needs no
+// evaluation key, so requests encrypted under different client keys batch
+// freely as long as (n, ell) agree. The captured graph holds the whole
+// sequence of level launches (gate-kernel pairs in L2-sized chunks, then the
+// output fix-ups) for fixed buffer pointers and stream; it is re-captured
+// when any of them changes.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "common.h"
+#include "netlist.h"
+#include "plan.h"
+
+namespace sfft {
+
+namespace {
+
+uint32_t shift_ref(uint32_t ref, const uint64_t off[4]) {
+  if (ref == REF_NONE) return ref;
+  const uint32_t region = ref >> 30;
+  return make_ref(region, (uint32_t)((ref & SLOT_MASK) + off[region]));
+}
+
+}  // namespace
+
+// Merges per-request programs level by level. off[r][region] is the first
+// slot of request r in each region (scratch / input / output).
+void merge_programs(const std::vector<Program>& parts, const std::vector<std::array<uint64_t, 4>>& off,
+                    Program* out) {
+  size_t levels = 0;
+  for (const Program& p : parts) levels = std::max(levels, p.level_off.size() - 1);
+  out->desc.clear();
+  out->aux.clear();
+  out->fix.clear();
+  out->level_off.assign(1, 0);
+  out->max_width = 0;
+  out->products = 0;
+  out->noise_ok = true;
+  out->noise_bits = 0;
+  for (size_t l = 0; l < levels; l++) {
+    const uint64_t before = out->desc.size();
+    for (size_t r = 0; r < parts.size(); r++) {
+      const Program& p = parts[r];
+      if (l + 1 >= p.level_off.size()) continue;
+      for (uint64_t g = p.level_off[l]; g < p.level_off[l + 1]; g++) {
+        GateDesc d = p.desc[g];
+        d.a = shift_ref(d.a, off[r].data());
+        d.b = shift_ref(d.b, off[r].data());
+        d.o0 = shift_ref(d.o0, off[r].data());
+        d.o1 = shift_ref(d.o1, off[r].data());
+        out->desc.push_back(d);
+        out->aux.push_back(p.aux[g]);
+      }
+    }
+    out->level_off.push_back(out->desc.size());
+    out->max_width = std::max<uint64_t>(out->max_width, out->desc.size() - before);
+  }
+  for (size_t r = 0; r < parts.size(); r++) {
+    for (FixDesc f : parts[r].fix) {
+      f.dst = (uint32_t)(f.dst + off[r][REG_OUT]);
+      if (f.kind <= 1) f.src = shift_ref(f.src, off[r].data());
+      out->fix.push_back(f);
+    }
+    out->noise_ok = out->noise_ok && parts[r].noise_ok;
+    out->noise_bits = std::max(out->noise_bits, parts[r].noise_bits);
+  }
+  out->products = out->desc.size();
+}
+
+// Graph replay of run_program for fixed pointers and stream.
+struct GraphCache {
+  cudaGraphExec_t exec = nullptr;
+  const void* key[4] = {nullptr, nullptr, nullptr, nullptr};
+  uint64_t bytes = 0;
+  ~GraphCache() {
+    if (exec) cudaGraphExecDestroy(exec);
+  }
+};
+
+int run_graph(GraphCache* gc, const Shape& s, const DeviceProgram& dp, const uint32_t* d_in,
+              uint32_t* d_out, uint32_t* d_scratch, uint64_t scratch_bytes, cudaStream_t st) {
+  if (!st) return fail(SFFT_EINVAL, "graph replay needs a non-default stream");
+  const void* key[4] = {d_in, d_out, d_scratch, st};
+  const bool hit = gc->exec && std::memcmp(key, gc->key, sizeof(key)) == 0 && gc->bytes == scratch_bytes;
+  if (!hit) {
+    if (gc->exec) {
+      cudaGraphExecDestroy(gc->exec);
+      gc->exec = nullptr;
+    }
+    // kernel attributes are set outside the capture by a zero-gate launch
+    KArgs warm = make_args(s);
+    warm.n = 0;
+    launch_gates(warm, st);
+    cudaGraph_t graph;
+    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+    int rc = run_program(s, dp, d_in, d_out, d_scratch, scratch_bytes, st, nullptr);
+    e = cudaStreamEndCapture(st, &graph);
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&gc->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    std::memcpy(gc->key, key, sizeof(key));
+    gc->bytes = scratch_bytes;
+  }
+  cudaError_t e = cudaGraphLaunch(gc->exec, st);
+  return e == cudaSuccess ? SFFT_OK : cuda_fail(e, "cudaGraphLaunch");
+}
+
+}  // namespace sfft
+
+struct sfft_batch {
+  sfft::Shape s;
+  std::vector<sfft::Program> parts;
+  std::vector<std::array<uint64_t, 4>> off;
+  sfft::Program merged;
+  sfft::DeviceProgram dev;
+  sfft::GraphCache graph;
+  sfft::Timer timer;
+  bool use_graph = true;
+  uint64_t fft_products = 0;
+};
+
+using namespace sfft;
+
+extern "C" {
+
+int sfft_batch_create(const sfft_params* p, const sfft_request* reqs, uint32_t count, uint32_t flags,
+                      sfft_batch** out) {
+  if (!out || (!reqs && count)) return fail(SFFT_EINVAL, "null argument");
+  *out = nullptr;
+  if (count == 0) return fail(SFFT_EINVAL, "empty batch");
+  std::unique_ptr<sfft_batch> b(new (std::nothrow) sfft_batch);
+  if (!b) return fail(SFFT_ENOMEM, "host allocation failed");
+  int rc = make_shape(p, &b->s, false);
+  if (rc) return rc;
+  uint64_t in = 0, outp = 0, scr = 0;
+  for (uint32_t r = 0; r < count; r++) {
+    Circuit c;
+    if (!build_fft(&c, reqs[r].N1, reqs[r].N2, reqs[r].F, reqs[r].f))
+      return fail(SFFT_EINVAL, "request " + std::to_string(r) + ": invalid FFT shape");
+    Program prog;
+    compile(c, b->s, &prog);
+    if (!prog.noise_ok && !(flags & SFFT_PLAN_ALLOW_NOISY))
+      return fail(SFFT_EPARAM, "request " + std::to_string(r) + ": static noise bound reaches q/4");
+    std::array<uint64_t, 4> o = {scr, in, outp, 0};
+    b->off.push_back(o);
+    scr += prog.scratch_slots;
+    in += prog.n_inputs;
+    outp += prog.n_outputs;
+    b->fft_products += prog.products;
+    b->parts.push_back(std::move(prog));
+  }
+  if (scr > SLOT_MASK || in > SLOT_MASK || outp > SLOT_MASK)
+    return fail(SFFT_EINVAL, "batch too large for 30-bit slot numbers");
+  merge_programs(b->parts, b->off, &b->merged);
+  b->merged.n_inputs = in;
+  b->merged.n_outputs = outp;
+  b->merged.scratch_slots = scr;
+  if ((rc = make_device_program(b->merged, &b->dev))) {
+    free_device_program(&b->dev);
+    return rc;
+  }
+  b->dev.kernel = (flags & SFFT_PLAN_INT_KERNEL) ? KERNEL_INT : KERNEL_AUTO;
+  b->dev.max_width = b->merged.max_width;
+  b->dev.tc = b->dev.kernel != KERNEL_INT && tc_supported(make_args(b->s));
+  b->dev.scratch_bytes =
+      scratch_layout(b->s, scr, b->merged.max_width, b->dev.tc, &b->dev.bx_off);
+  b->use_graph = !(flags & SFFT_BATCH_NO_GRAPH);
+  *out = b.release();
+  return SFFT_OK;
+}
+
+int sfft_batch_info_get(const sfft_batch* b, sfft_plan_info* info) {
+  if (!b || !info) return fail(SFFT_EINVAL, "null argument");
+  std::memset(info, 0, sizeof(*info));
+  info->inputs = b->merged.n_inputs;
+  info->outputs = b->merged.n_outputs;
+  info->products = b->merged.products;
+  info->levels = b->merged.level_off.size() - 1;
+  info->max_level_width = b->merged.max_width;
+  info->scratch_slots = b->merged.scratch_slots;
+  info->scratch_bytes = b->dev.scratch_bytes;
+  info->ct_words = b->s.ctw;
+  info->noise_bits = b->merged.noise_bits;
+  info->noise_ok = b->merged.noise_ok ? 1 : 0;
+  info->gate_kernel = b->dev.tc ? KERNEL_TC : KERNEL_INT;
+  return SFFT_OK;
+}
+
+int sfft_batch_offsets(const sfft_batch* b, uint64_t* in_off, uint64_t* out_off) {
+  if (!b) return fail(SFFT_EINVAL, "batch is NULL");
+  for (size_t r = 0; r < b->off.size(); r++) {
+    if (in_off) in_off[r] = b->off[r][REG_IN];
+    if (out_off) out_off[r] = b->off[r][REG_OUT];
+  }
+  return SFFT_OK;
+}
+
+int sfft_batch_eval(sfft_batch* b, const uint32_t* d_in, uint32_t* d_out, uint32_t* d_scratch,
+                    uint64_t scratch_bytes, void* stream) {
+  if (!b) return fail(SFFT_EINVAL, "batch is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (b->use_graph && !b->timer.on)
+    return run_graph(&b->graph, b->s, b->dev, d_in, d_out, d_scratch, scratch_bytes, st);
+  return run_program(b->s, b->dev, d_in, d_out, d_scratch, scratch_bytes, st, &b->timer);
+}
+
+int sfft_batch_eval_host(sfft_batch* b, const uint32_t* h_in, uint32_t* h_out, uint32_t* d_in,
+                         uint32_t* d_out, uint32_t* d_scratch, uint64_t scratch_bytes, void* stream) {
+  if (!b || !h_in || !h_out) return fail(SFFT_EINVAL, "null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  const uint64_t in_b = b->merged.n_inputs * b->s.ctw * 4, out_b = b->merged.n_outputs * b->s.ctw * 4;
+  cudaError_t e = cudaMemcpyAsync(d_in, h_in, in_b, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "H2D copy");
+  int rc = sfft_batch_eval(b, d_in, d_out, d_scratch, scratch_bytes, stream);
+  if (rc) return rc;
+  e = cudaMemcpyAsync(h_out, d_out, out_b, cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return cuda_fail(e, "D2H copy");
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "stream sync");
+  return check_device_error(b->dev.err, st);
+}
+
+int sfft_batch_check(sfft_batch* b, void* stream) {
+  if (!b) return fail(SFFT_EINVAL, "batch is NULL");
+  return check_device_error(b->dev.err, (cudaStream_t)stream);
+}
+
+int sfft_batch_set_timing(sfft_batch* b, int on) {
+  if (!b) return fail(SFFT_EINVAL, "batch is NULL");
+  b->timer.drain_ms();
+  b->timer.on = on != 0;
+  b->timer.launches = b->timer.products = 0;
+  return SFFT_OK;
+}
+
+int sfft_batch_timing(sfft_batch* b, double* gate_ms, uint64_t* launches, uint64_t* products) {
+  if (!b) return fail(SFFT_EINVAL, "batch is NULL");
+  const double ms = b->timer.drain_ms();
+  if (gate_ms) *gate_ms = ms;
+  if (launches) *launches = b->timer.launches;
+  if (products) *products = b->timer.products;
+  b->timer.launches = b->timer.products = 0;
+  return SFFT_OK;
+}
+
+void sfft_batch_free(sfft_batch* b) {
+  if (!b) return;
+  free_device_program(&b->dev);
+  delete b;
+}
+
+}  // extern "C"

@@ -181,10 +181,6 @@ __device__ __forceinline__ uint32_t sw128_off(uint32_t r, uint32_t c) {
   return r * 128u + ((c ^ (r & 7u)) << 4);
 }
 
-__device__ __forceinline__ uint32_t p_word(uint32_t i, uint32_t j, uint32_t l, uint32_t ell) {
-  return (j == i / ell && l == (i % ell) / 32) ? (1u << (i % 32)) : 0u;
-}
-
 __device__ __forceinline__ int nib(uint32_t code, int k) {
   return (int)((int32_t)(code << (28 - 4 * k)) >> 28);
 }
@@ -613,6 +609,7 @@ int launch_gates_tc(const KArgs& a, cudaStream_t st) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "B expansion launch");
     k_gate_tc<<<(unsigned)(ca.n * t.mtiles), kThreads, t.smem_bytes, st>>>(ca, t);
+    count_launches(2);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "tc gate kernel launch");
   }

@@ -32,6 +32,7 @@ P = ctypes.POINTER
 SIGNATURES = {
     "sfft_last_error": (ctypes.c_char_p, []),
     "sfft_version": (ctypes.c_char_p, []),
+    "sfft_launch_count": (c_u64, []),
     "sfft_ct_words": (c_u64, [P(sfft_params)]),
     "sfft_keygen": (c_i32, [P(sfft_params), c_u64, P(c_void_p)]),
     "sfft_keys_free": (None, [c_void_p]),
@@ -59,7 +60,21 @@ SIGNATURES = {
     "sfft_gate_level": (c_i32, [P(sfft_params), c_void_p, c_void_p, c_void_p, c_void_p, c_u16_p,
                                 c_u16_p, c_u8_p, c_u64, c_u32, c_void_p]),
     "sfft_plan_check": (c_i32, [c_void_p, c_void_p]),
+    "sfft_batch_create": (c_i32, [P(sfft_params), c_void_p, c_u32, c_u32, P(c_void_p)]),
+    "sfft_batch_info_get": (c_i32, [c_void_p, P(sfft_plan_info)]),
+    "sfft_batch_offsets": (c_i32, [c_void_p, P(c_u64), P(c_u64)]),
+    "sfft_batch_eval": (c_i32, [c_void_p, c_void_p, c_void_p, c_void_p, c_u64, c_void_p]),
+    "sfft_batch_check": (c_i32, [c_void_p, c_void_p]),
+    "sfft_batch_eval_host": (c_i32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                    c_u64, c_void_p]),
+    "sfft_batch_set_timing": (c_i32, [c_void_p, ctypes.c_int]),
+    "sfft_batch_timing": (c_i32, [c_void_p, c_double_p, P(c_u64), P(c_u64)]),
+    "sfft_batch_free": (None, [c_void_p]),
 }
+
+
+class sfft_request(ctypes.Structure):
+    _fields_ = [("N1", c_u32), ("N2", c_u32), ("F", c_u32), ("f", c_u32)]
 
 _lib = None
 

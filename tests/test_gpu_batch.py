@@ -1,0 +1,120 @@
+"""Batched (level-merged, graph-replayed) evaluation: bit-exact against the
+per-request plain evaluator and the oracle, with requests from several
+client key sets in one batch."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1611_08769_gb300 as sf  # noqa: E402
+from oracle import circuit, evaluate, fixedpoint as fx, gsw  # noqa: E402
+from paper_1611_08769_gb300 import build as sfbuild  # noqa: E402
+from synthetic import image_2d, signal_1d  # noqa: E402
+
+REQS = [(8, 1, 8, 4), (4, 1, 6, 2), (2, 4, 8, 3), (16, 1, 8, 4), (4, 1, 6, 2)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    sfbuild.build()
+
+
+def _inputs(sp, reqs):
+    """Per-request signals, key sets (request index mod 3) and device ciphertexts."""
+    cw = sf.ct_words(sp)
+    keys = {ks: sf.keygen(sp, 100 + ks) for ks in range(3)}
+    pubs = {ks: torch.from_numpy(k.public().view(np.int32)).cuda() for ks, k in keys.items()}
+    cts, sigs = [], []
+    for r, (N1, N2, F, f) in enumerate(reqs):
+        re_, im_ = signal_1d(N1 * N2, -1, 1, r) if N2 == 1 else image_2d(N1, N2, r)
+        d = torch.empty((N1 * N2 * 2 * F, cw), dtype=torch.int32, device="cuda")
+        sf.encrypt_bits_device(sp, pubs[r % 3], re_, im_, F, f, 7 + r, d)
+        cts.append(d)
+        sigs.append((re_, im_))
+    return keys, cts, sigs
+
+
+def _single(sp, req, d_in, flags=0):
+    plan = sf.Plan(sp, *req, flags=flags)
+    out = torch.empty((plan.info["outputs"], plan.info["ct_words"]), dtype=torch.int32, device="cuda")
+    scr = torch.empty(max(1, plan.info["scratch_bytes"] // 4), dtype=torch.int32, device="cuda")
+    plan.eval_fft(d_in, out, scr)
+    plan.check()
+    return out
+
+
+@pytest.mark.parametrize("pset,flags", [("P0", 0), ("P2", 0), ("P2", sf.PLAN_INT_KERNEL)])
+def test_batch_equals_per_request_plans(pset, flags):
+    sp = sf.param_set(pset)
+    keys, cts, _ = _inputs(sp, REQS)
+    batch = sf.Batch(sp, REQS, flags)
+    info = batch.info
+    assert info["inputs"] == sum(len(c) for c in cts)
+    d_in = torch.cat(cts)
+    out = torch.empty((info["outputs"], info["ct_words"]), dtype=torch.int32, device="cuda")
+    scr = torch.empty(max(1, info["scratch_bytes"] // 4), dtype=torch.int32, device="cuda")
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        for _ in range(2):                       # capture, then replay
+            out.fill_(-1)
+            batch.eval(d_in, out, scr, stream)
+            batch.check(stream)
+            for r, req in enumerate(REQS):
+                want = _single(sp, req, cts[r], flags)
+                got = out[batch.out_off[r]:batch.out_off[r] + len(want)]
+                assert torch.equal(got, want), (r, req)
+
+
+def test_batch_graph_replay_equals_plain_launches():
+    sp = sf.param_set("P2")
+    _, cts, _ = _inputs(sp, REQS[:3])
+    d_in = torch.cat(cts)
+    res = []
+    stream = torch.cuda.Stream()
+    for flags in (0, sf.BATCH_NO_GRAPH):
+        b = sf.Batch(sp, REQS[:3], flags)
+        out = torch.zeros((b.info["outputs"], b.info["ct_words"]), dtype=torch.int32, device="cuda")
+        scr = torch.empty(max(1, b.info["scratch_bytes"] // 4), dtype=torch.int32, device="cuda")
+        with torch.cuda.stream(stream):
+            b.eval(d_in, out, scr, stream)
+            b.check(stream)
+        res.append(out)
+    assert torch.equal(res[0], res[1])
+
+
+def test_batch_request_matches_oracle_and_decrypts():
+    """One request of a mixed-key batch against the oracle's ciphertexts."""
+    sp = sf.param_set("P2")
+    p = gsw.Params(sp.n, sp.ell, sp.m, sp.chi)
+    reqs = [(4, 1, 6, 2), (8, 1, 8, 4)]
+    keys, cts, sigs = _inputs(sp, reqs)
+    b = sf.Batch(sp, reqs)
+    d_in = torch.cat(cts)
+    out = torch.empty((b.info["outputs"], b.info["ct_words"]), dtype=torch.int32, device="cuda")
+    scr = torch.empty(max(1, b.info["scratch_bytes"] // 4), dtype=torch.int32, device="cuda")
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        b.eval(d_in, out, scr, stream)
+        b.check(stream)
+    r = 1
+    N, _, F, f = reqs[r]
+    re_, im_ = sigs[r]
+    ko = gsw.Keys(p, 100 + r % 3)
+    c = circuit.fft_circuit(N, 1, F, f)
+    ins = []
+    for k in range(N):
+        for part, x in enumerate((re_[k], im_[k])):
+            for bit_i, bit in enumerate(fx.to_bits(fx.quantize(x, F, f), F)):
+                ins.append(gsw.encrypt(ko, bit, 7 + r, (2 * k + part) * F + bit_i))
+    want = evaluate.eval_encrypted(c, p, ins)
+    got = out[b.out_off[r]:b.out_off[r] + len(want)].cpu().numpy().view(np.uint32)
+    assert np.array_equal(got.reshape(want.shape), want)
+    W = (p.n + 1) * p.L
+    rows = got.reshape(len(want), -1)[:, (p.ell - 1) * W:p.ell * W]
+    _, _, raw = sf.decrypt(keys[r % 3], rows, W, N, F, f)
+    q = [fx.quantize(x, F, f) for x in re_]
+    er, ei = fx.fft_int(q, [0] * N, F, f)
+    assert list(raw) == [v for k in range(N) for v in (er[k], ei[k])]

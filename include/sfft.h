@@ -249,6 +249,38 @@ int sfft_batch_set_timing(sfft_batch* b, int on);
 int sfft_batch_timing(sfft_batch* b, double* gate_ms, uint64_t* launches, uint64_t* products);
 void sfft_batch_free(sfft_batch* b);
 
+/* ------------------------------------------------------------- serving */
+
+/* Continuous-batching server (north side of Fig. 1's step 4 under load).
+ * A worker thread owns a stream and repeats a tick: admit queued requests
+ * (FIFO) while the HBM budget has room for all their ciphertexts (scratch
+ * wires, inputs, outputs) and fewer than max_active run, copying their input
+ * ciphertexts in; then launch the next level of every active request
+ * together; finished requests get their fix-ups and are copied out to the
+ * client's h_out, and their memory is released once the copy completed. A
+ * request arriving while others run joins at the next tick. hbm_budget_bytes
+ * is allocated at creation (one arena) plus descriptor pools. All requests
+ * share (n, ell); their client keys may differ. */
+typedef struct sfft_server_stats {
+  uint64_t completed, queued, active, ticks, tick_gates, peak_active;
+  double p50_ms, p99_ms, max_ms;   /* submit-to-completion latency of completed requests */
+} sfft_server_stats;
+
+int sfft_server_create(const sfft_params* p, uint64_t hbm_budget_bytes, uint32_t max_active,
+                       sfft_server** out);
+/* Queues one request. h_in: its input ciphertexts (layout of sfft_eval_fft's
+ * d_in), h_out: room for its output ciphertexts; both caller-owned and valid
+ * until sfft_server_wait returned for the ticket. ENOMEM if the request alone
+ * exceeds the budget. */
+int sfft_server_submit(sfft_server* sv, const sfft_request* req, const uint32_t* h_in,
+                       uint32_t* h_out, uint64_t* ticket);
+/* Waits up to timeout_ms for the request (ETIMEOUT otherwise), reports its
+ * submit-to-completion latency, and forgets the ticket. */
+int sfft_server_wait(sfft_server* sv, uint64_t ticket, uint32_t timeout_ms, double* latency_ms);
+int sfft_server_get_stats(sfft_server* sv, sfft_server_stats* st);
+/* Stops the worker (queued requests are dropped, running ones finish). */
+void sfft_server_free(sfft_server* sv);
+
 /* Evaluates a single level of gates given explicitly (test hook): gate g
  * computes, with A = d_a[g] (complemented to P - A first when
  * (flags[g] & 1)) and B = d_b[g],

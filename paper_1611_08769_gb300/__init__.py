@@ -254,6 +254,55 @@ class Batch:
             self._h = None
 
 
+def _hptr(a):
+    """Host pointer of a numpy array or a CPU torch tensor."""
+    if isinstance(a, np.ndarray):
+        return ctypes.c_void_p(a.ctypes.data)
+    return ctypes.c_void_p(int(a.data_ptr()))
+
+
+class Server:
+    """Continuous-batching encrypted-FFT server (sfft_server_create)."""
+
+    def __init__(self, params, hbm_budget_bytes, max_active=64):
+        self.params = params
+        h = ctypes.c_void_p()
+        check(lib().sfft_server_create(ctypes.byref(params), int(hbm_budget_bytes), max_active,
+                                       ctypes.byref(h)))
+        self._h = h
+        self._held = {}
+
+    def submit(self, request, h_in, h_out):
+        """Queue one request; h_in / h_out stay referenced until wait()."""
+        t = ctypes.c_uint64()
+        req = native.sfft_request(*request)
+        check(lib().sfft_server_submit(self._h, ctypes.byref(req), _hptr(h_in), _hptr(h_out),
+                                       ctypes.byref(t)))
+        self._held[t.value] = (h_in, h_out)
+        return t.value
+
+    def wait(self, ticket, timeout_ms=600000):
+        lat = ctypes.c_double()
+        check(lib().sfft_server_wait(self._h, ticket, timeout_ms, ctypes.byref(lat)))
+        self._held.pop(ticket, None)
+        return lat.value
+
+    def stats(self):
+        st = native.sfft_server_stats()
+        check(lib().sfft_server_get_stats(self._h, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in native.sfft_server_stats._fields_}
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            lib().sfft_server_free(h)
+            self._h = None
+        self._held.clear()
+
+    def __del__(self):
+        self.close()
+
+
 def gate_level(params, d_a, d_b, d_out0, d_out1, code0, code1, flags, stream=None, kernel=0):
     code0 = np.ascontiguousarray(code0, dtype=np.uint16)
     code1 = np.ascontiguousarray(code1, dtype=np.uint16)

@@ -120,13 +120,15 @@ int run_program(const Shape& s, const DeviceProgram& dp, const uint32_t* d_in, u
       tm->products += a.n;
     }
   }
-  if (dp.n_fix) {
-    k_fixup<<<(unsigned)dp.n_fix, 256, 0, st>>>(dp.fix, dp.n_fix, a);
-    count_launches(1);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "fixup launch");
-  }
-  return SFFT_OK;
+  return launch_fixups(dp.fix, dp.n_fix, a, st);
+}
+
+int launch_fixups(const FixDesc* d_fix, uint64_t n, const KArgs& a, cudaStream_t st) {
+  if (n == 0) return SFFT_OK;
+  k_fixup<<<(unsigned)n, 256, 0, st>>>(d_fix, n, a);
+  count_launches(1);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SFFT_OK : cuda_fail(e, "fixup launch");
 }
 
 int make_device_program(const Program& p, DeviceProgram* dp) {

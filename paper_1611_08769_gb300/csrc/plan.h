@@ -34,6 +34,8 @@ int cuda_fail(cudaError_t e, const char* what);
 int upload(const void* h, size_t bytes, void** d);
 KArgs make_args(const Shape& s);
 int launch_gates(const KArgs& a, cudaStream_t st);
+// Output fix-ups (copies, complements, constants) of n entries.
+int launch_fixups(const FixDesc* d_fix, uint64_t n, const KArgs& a, cudaStream_t st);
 // Process-wide count of this library's kernel launches (sfft_launch_count).
 void count_launches(uint64_t n);
 // Tensor-core gate kernel (tc.cu): shapes it supports, and its launcher.

@@ -32,6 +32,7 @@
 // returns.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "common.h"
@@ -567,14 +568,15 @@ uint64_t tc_bx_bytes_per_gate(const KArgs& a) {
   return (uint64_t)t.kblocks * t.btile;
 }
 
-// A level runs in chunks of gates whose expanded B operands fit well inside
-// L2 (expand a chunk, then multiply it), so the GEMM's slice copies hit L2.
-constexpr uint64_t kBxL2Budget = 48ull << 20;
+// A level runs in chunks of gates (expand a chunk's B operands, then multiply
+// it) so that the expansion buffer stays bounded; the chunk is large enough
+// that each GEMM launch spans many waves of CTAs.
+constexpr uint64_t kBxL2Budget = 512ull << 20;
 
 uint64_t tc_chunk_gates(const KArgs& a) {
   const uint64_t per = tc_bx_bytes_per_gate(a);
   if (per == 0) return 0;
-  const uint64_t c = kBxL2Budget / per;
+  const uint64_t c = std::min<uint64_t>(kBxL2Budget / per, 4096);
   return c ? c : 1;
 }
 

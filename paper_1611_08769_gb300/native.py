@@ -76,6 +76,21 @@ SIGNATURES = {
 class sfft_request(ctypes.Structure):
     _fields_ = [("N1", c_u32), ("N2", c_u32), ("F", c_u32), ("f", c_u32)]
 
+
+class sfft_server_stats(ctypes.Structure):
+    _fields_ = [("completed", c_u64), ("queued", c_u64), ("active", c_u64), ("ticks", c_u64),
+                ("tick_gates", c_u64), ("peak_active", c_u64), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double)]
+
+
+SIGNATURES.update({
+    "sfft_server_create": (c_i32, [P(sfft_params), c_u64, c_u32, P(c_void_p)]),
+    "sfft_server_submit": (c_i32, [c_void_p, P(sfft_request), c_void_p, c_void_p, P(c_u64)]),
+    "sfft_server_wait": (c_i32, [c_void_p, c_u64, c_u32, c_double_p]),
+    "sfft_server_get_stats": (c_i32, [c_void_p, P(sfft_server_stats)]),
+    "sfft_server_free": (None, [c_void_p]),
+})
+
 _lib = None
 
 

@@ -50,6 +50,7 @@ CONFIGS = {
     "fft16x16_image_noisy": dict(kind="fft", N1=16, N2=16, F=16, f=6, lo=None, hi=None, pset="P1"),
     "fft64_16bit_p2": dict(kind="fft", N1=64, N2=1, F=16, f=8, lo=-8.0, hi=8.0, pset="P2"),
     "batch256_p2": dict(kind="batch", count=256, pset="P2", key_sets=4),
+    "serve_p2": dict(kind="serve", pset="P2", key_sets=8, requests=400, calib=48),
 }
 
 
@@ -69,6 +70,8 @@ def parse():
                          "gates at the workload's parameters")
     ap.add_argument("--gates", type=int, default=128, help="gates per level in --mode gates")
     ap.add_argument("--kernel", default="auto", choices=["auto", "int", "tc"])
+    ap.add_argument("--budget-gb", type=float, default=150.0, help="serving HBM admission budget")
+    ap.add_argument("--requests", type=int, default=0, help="serving: requests in the trace")
     return ap.parse_args()
 
 
@@ -188,8 +191,23 @@ def batch_workload(cfg):
     return params, [((r.N1, r.N2, r.F, r.f), r.re, r.im, r.key_set, i) for i, r in enumerate(reqs)]
 
 
+def serve_workload(cfg):
+    """A sample of the serving trace's requests (used by the oracle arm)."""
+    import paper_1611_08769_gb300 as sf
+    from synthetic import serving_trace
+    c = CONFIGS[cfg]
+    trace = serving_trace(16, 1.0, seed=6, key_sets=c["key_sets"])
+    return sf.param_set(c["pset"]), [((r.N1, r.N2, r.F, r.f), r.re, r.im, r.key_set, r.seed)
+                                     for r in trace]
+
+
 def workload(cfg):
-    return batch_workload(cfg) if CONFIGS[cfg]["kind"] == "batch" else fft_workload(cfg)
+    kind = CONFIGS[cfg]["kind"]
+    if kind == "batch":
+        return batch_workload(cfg)
+    if kind == "serve":
+        return serve_workload(cfg)
+    return fft_workload(cfg)
 
 
 def cpu_oracle_sample(params, items, budget_s):
@@ -310,6 +328,91 @@ def run_gates(args):
                       "roofline": roofline(params, gk, t, 1, G)}), flush=True)
 
 
+def run_serve(args):
+    """Poisson arrivals into the continuous-batching server (rank 0 only)."""
+    import torch
+
+    import paper_1611_08769_gb300 as sf
+    from paper_1611_08769_gb300 import build as sfbuild
+    from synthetic import serving_trace
+    sfbuild.build()
+    c = CONFIGS[args.config]
+    params = sf.param_set(c["pset"])
+    cw = sf.ct_words(params)
+    count = args.requests or c["requests"]
+    # one encrypted input per distinct (shape, key set); outputs rotate per shape
+    probe = serving_trace(count + c["calib"], 1.0, seed=5, key_sets=c["key_sets"])
+    keys = {ks: sf.keygen(params, 2000 + ks) for ks in range(c["key_sets"])}
+    pubs = {ks: torch.from_numpy(k.public().view(np.int32)).cuda() for ks, k in keys.items()}
+    inputs, outputs = {}, {}
+    for r in probe:
+        shape = (r.N1, r.N2, r.F, r.f)
+        if (shape, r.key_set) not in inputs:
+            n = r.N1 * r.N2 * 2 * r.F
+            d = torch.empty((n, cw), dtype=torch.int32, device="cuda")
+            sf.encrypt_bits_device(params, pubs[r.key_set], r.re, r.im, r.F, r.f, r.seed, d)
+            inputs[(shape, r.key_set)] = d.cpu().pin_memory()
+            del d
+        if shape not in outputs:
+            outputs[shape] = [torch.empty((r.N1 * r.N2 * 2 * r.F, cw), dtype=torch.int32).pin_memory()
+                              for _ in range(4)]
+    products = {s: sf.circuit_info(params, *s)["products"] for s in outputs}
+    srv = sf.Server(params, int(args.budget_gb * (1 << 30)), max_active=64)
+    rot = {}
+
+    def submit(r):
+        shape = (r.N1, r.N2, r.F, r.f)
+        k = rot.get(shape, 0)
+        rot[shape] = k + 1
+        return srv.submit(shape, inputs[(shape, r.key_set)], outputs[shape][k % 4])
+
+    # capacity: a closed burst of the same mix
+    burst = probe[:c["calib"]]
+    t0 = time.perf_counter()
+    tickets = [submit(r) for r in burst]
+    for t in tickets:
+        srv.wait(t)
+    cap = len(burst) / (time.perf_counter() - t0)
+    rate = 0.8 * cap
+    trace = serving_trace(count, rate, seed=6, key_sets=c["key_sets"])
+    srv.close()
+    srv = sf.Server(params, int(args.budget_gb * (1 << 30)), max_active=64)
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        t0 = time.perf_counter()
+        tickets = []
+        for r in trace:
+            now = time.perf_counter() - t0
+            if r.arrival_s > now:
+                time.sleep(r.arrival_s - now)
+            tickets.append(submit(r))
+        lat = [srv.wait(t) for t in tickets]
+        wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    served_prod = sum(products[(r.N1, r.N2, r.F, r.f)] for r in trace)
+    line = {
+        "metric": "encrypted FFTs/s served", "value": len(trace) / wall, "unit": "FFT/s",
+        "n_gpus": 1, "steps": len(trace), "warmup": len(burst), "ms_per_step": wall * 1000 / len(trace),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": args.config, "n": params.n, "ell": params.ell, "chi": params.chi,
+                   "requests": len(trace), "key_sets": c["key_sets"],
+                   "arrival_rate_per_s": rate, "capacity_closed_burst_per_s": cap,
+                   "hbm_budget_gb": args.budget_gb, "max_active": 64,
+                   "mix": "75% 1-D N in {8..256} 8.8, 25% 2-D 8x8/16x16/32x32 at log2(pixels)+2 "
+                          "integer bits, F = 16"},
+        "latency_ms": {"p50": st["p50_ms"], "p99": st["p99_ms"], "max": st["max_ms"],
+                       "client_p50": float(np.percentile(lat, 50)),
+                       "client_p99": float(np.percentile(lat, 99))},
+        "gates_per_s": served_prod / wall,
+        "server": {k: st[k] for k in ("ticks", "tick_gates", "peak_active")},
+        "e2e": {"value": len(trace) / wall, "unit": "FFT/s",
+                "note": "served end to end: host ciphertexts in, host ciphertexts out"},
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -319,6 +422,8 @@ def main():
         return run_reference(args, rank, world)
     if args.mode == "gates":
         return run_gates(args)
+    if CONFIGS[args.config]["kind"] == "serve":
+        return run_serve(args) if rank == 0 else None
 
     import torch
     import torch.distributed as dist

@@ -345,7 +345,8 @@ def run_serve(args):
     keys = {ks: sf.keygen(params, 2000 + ks) for ks in range(c["key_sets"])}
     pubs = {ks: torch.from_numpy(k.public().view(np.int32)).cuda() for ks, k in keys.items()}
     inputs, outputs = {}, {}
-    for r in probe:
+    # shapes and key sets of a trace do not depend on its rate
+    for r in probe + serving_trace(count, 1.0, seed=6, key_sets=c["key_sets"]):
         shape = (r.N1, r.N2, r.F, r.f)
         if (shape, r.key_set) not in inputs:
             n = r.N1 * r.N2 * 2 * r.F

@@ -131,14 +131,15 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "of fallback"
 
 
-def roofline(params, gate_kernel, gate_ms, launches, gates_timed):
+def roofline(params, gate_kernel, gate_ms, launches, gates_timed, tc_columns=0):
     """Roofline of the dominant kernel (the gate product) from CUDA-event times.
 
     Integer kernel: unit = one product = Ng^2 (n+1) L 32-bit limb additions,
     against the derived INT32 ALU peak. Tensor-core kernel: unit = one product
-    = the dense contraction 2 Ng Ng (4 W) flops (bits x byte digits, W words
-    per row), against the measured dense bf16 rate (kind::f16 runs fp16 at the
-    bf16 rate); the sustained figure, since the kernel runs inside a long step.
+    = the dense contraction 2 Ng Ng C flops (bits x 11-bit digits, C = (n+1)
+    ceil(ell / 11) digit columns per row), against the measured dense bf16
+    rate (kind::f16 runs fp16 at the bf16 rate); the sustained figure, since
+    the kernel runs inside a long step.
     """
     Ng, L = (params.n + 1) * params.ell, params.ell // 32
     W = (params.n + 1) * L
@@ -146,12 +147,13 @@ def roofline(params, gate_kernel, gate_ms, launches, gates_timed):
     sec = gate_ms / 1000.0 if gate_ms > 0 else float("inf")
     if gate_kernel == 2:
         peaks, src = measured_peaks()
-        flops = 2.0 * Ng * Ng * 4 * W * gates_timed
+        cols = tc_columns or (params.n + 1) * -(-params.ell // 11)
+        flops = 2.0 * Ng * Ng * cols * gates_timed
         achieved = flops / sec / 1e12
         peak = float(peaks["bf16_tflops_sustained"])
         return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None, "kernel": "k_gate_tc (+k_expand_b)",
-                "avg_launch_ms": avg_launch_ms, "flops_per_product": 2.0 * Ng * Ng * 4 * W,
+                "avg_launch_ms": avg_launch_ms, "flops_per_product": 2.0 * Ng * Ng * cols,
                 "peak_source": f"bf16_tflops_sustained {src}"}
     ops = float(Ng) * Ng * (params.n + 1) * L * gates_timed
     achieved = ops / sec
@@ -325,7 +327,7 @@ def run_gates(args):
     print(json.dumps({"mode": "gates", "gates": G, "ms_per_level": t, "gates_per_s": G / t * 1e3,
                       "config": {"workload": args.config, "n": params.n, "ell": params.ell},
                       "note": "includes the test hook's descriptor upload, allocation and sync",
-                      "roofline": roofline(params, gk, t, 1, G)}), flush=True)
+                      "roofline": roofline(params, gk, t, 1, G, info["tc_columns"])}), flush=True)
 
 
 def run_serve(args):
@@ -551,7 +553,8 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic", "config": cfg,
             "gates_per_s": world * info["products"] * 1000.0 / ms,
-            "roofline": roofline(params, info["gate_kernel"], gate_ms, launches, gates_timed),
+            "roofline": roofline(params, info["gate_kernel"], gate_ms, launches, gates_timed,
+                                 info["tc_columns"]),
             "plain": plain,
             "cpu_baseline": cpu,
             "e2e": {"value": world * len(items) * 1000.0 / e2e_ms, "unit": "FFT/s",

@@ -139,7 +139,8 @@ typedef struct sfft_plan_info {
   uint32_t noise_bits;          /* bit length of the largest wire noise bound */
   uint32_t noise_ok;            /* bound < q/4 */
   uint32_t gate_kernel;         /* 1 integer-ALU kernel, 2 tensor-core kernel */
-  uint32_t reserved;
+  uint32_t tc_columns;          /* tensor-core kernel: digit columns of a product row
+                                   ((n+1) ceil(ell / dw), dw = 11 bits); 0 otherwise */
 } sfft_plan_info;
 
 /* Builds the canonical gate circuit of a 1-D (N2 == 1) or row-column 2-D FFT

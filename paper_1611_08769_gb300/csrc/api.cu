@@ -243,6 +243,7 @@ int sfft_plan_info_get(const sfft_plan* pl, sfft_plan_info* info) {
   info->noise_ok = pl->prog.noise_ok ? 1 : 0;
   info->gate_kernel =
       (pl->dev.kernel != KERNEL_INT && tc_supported(make_args(pl->s))) ? KERNEL_TC : KERNEL_INT;
+  info->tc_columns = info->gate_kernel == KERNEL_TC ? tc_digit_columns(make_args(pl->s)) : 0;
   return SFFT_OK;
 }
 

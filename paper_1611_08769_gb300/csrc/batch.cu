@@ -198,6 +198,7 @@ int sfft_batch_info_get(const sfft_batch* b, sfft_plan_info* info) {
   info->noise_bits = b->merged.noise_bits;
   info->noise_ok = b->merged.noise_ok ? 1 : 0;
   info->gate_kernel = b->dev.tc ? KERNEL_TC : KERNEL_INT;
+  info->tc_columns = b->dev.tc ? tc_digit_columns(make_args(b->s)) : 0;
   return SFFT_OK;
 }
 

@@ -10,6 +10,7 @@
 namespace sfft {
 bool tc_supported(const KArgs& a);
 uint64_t tc_bx_bytes(const KArgs& a, uint64_t gates);
+uint32_t tc_digit_columns(const KArgs& a);
 }
 
 using namespace sfft;
@@ -55,6 +56,8 @@ int sfft_circuit_info(const sfft_params* p, uint32_t N1, uint32_t N2, uint32_t F
     KArgs k{};
     k.Ng = s.Ng;
     k.W = s.W;
+    k.L = s.L;
+    k.ell = s.ell;
     uint64_t bx_off = 0;
     const bool tc = tc_supported(k);
     const uint64_t wires = prog.scratch_slots * s.ctw * 4;
@@ -67,7 +70,10 @@ int sfft_circuit_info(const sfft_params* p, uint32_t N1, uint32_t N2, uint32_t F
   KArgs ka{};
   ka.Ng = s.Ng;
   ka.W = s.W;
+  ka.L = s.L;
+  ka.ell = s.ell;
   info->gate_kernel = tc_supported(ka) ? KERNEL_TC : KERNEL_INT;
+  info->tc_columns = tc_digit_columns(ka);
   return SFFT_OK;
 }
 

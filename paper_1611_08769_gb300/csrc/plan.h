@@ -46,6 +46,9 @@ int launch_gates_tc(const KArgs& a, cudaStream_t st);
 // L2-sized chunks of gates that share one buffer).
 uint64_t tc_bx_bytes_per_gate(const KArgs& a);
 uint64_t tc_bx_bytes(const KArgs& a, uint64_t gates);
+// Digit columns of one row of the tensor-core product (elements x digits per
+// element), 0 if the tensor-core kernel does not support the shape.
+uint32_t tc_digit_columns(const KArgs& a);
 // Scratch layout of a program: wire slots first, then (tensor-core kernel) the
 // expanded B operands of the widest level, 256-byte aligned.
 uint64_t scratch_layout(const Shape& s, uint64_t slots, uint64_t max_width, bool tc, uint64_t* bx_off);

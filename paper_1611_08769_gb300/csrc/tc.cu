@@ -1,35 +1,38 @@
 // Gate product on the 5th-generation tensor cores (tcgen05, sm_103a).
 //
 // The GSW product K = BitDecomp(A~) B' (Sec. 7: an N x N matrix product per
-// gate) is a dense contraction of a {0,1} matrix with B''s digits. Splitting
-// every 32-bit limb of B' into its four bytes gives, per output row i and
-// byte column n (byte n%4 of word n/4),
-//     S[i][n] = sum_k bit_k(A~_i) * byte_n(B'_k)  <  255 Ng  < 2^24,
-// so an fp16 x fp16 -> fp32 MMA computes it exactly. Operands are encoded
-// without subnormals: a bit as fp16 1.0, a byte b as fp16 (1024 + b) (bit
-// pattern 0x6400 | b); the 1024 * popcount(A~_i) term is removed in the
-// epilogue. The epilogue forms K[i][w] = sum_b S[i][4w+b] 2^(8b) and adds the
-// linear terms c0 P + c1 A + c2 B with the limb carries of each element,
-// exactly as the integer kernel does.
+// gate) is a dense contraction of a {0,1} matrix with the entries of B'.
+// Every ell-bit entry of B' is cut into D = ceil(ell / dw) digits of dw bits
+// (dw = 11, or fewer if Ng (2^dw - 1) would reach 2^24), so that per output
+// row i and digit column (element e, digit d)
+//     S[i][e,d] = sum_k bit_k(A~_i) * digit_d(B'_k[e])  <=  Ng (2^dw - 1)  <  2^24.
+// Digits up to 2047 are exact fp16 values and every partial sum is an
+// integer below 2^24, so an fp16 x fp16 -> fp32 MMA computes S exactly. The
+// epilogue forms K[i][e] = sum_d S[i][e,d] 2^(dw d) (mod 2^ell) word by word
+// and adds the linear terms c0 P + c1 A + c2 B with the limb carries of the
+// element, exactly as the integer kernel does.
 //
 // Two kernels per level:
 //  * k_expand_b writes, once per gate, the B operand in its tensor-core form:
 //    for every 64-row slice of B' the exact shared-memory image of the
-//    128B-swizzled K-major fp16 tile (ndpad byte columns x 64 K values);
-//  * k_gate_tc, one CTA (16 warps) per 128-row tile of a gate's output: the
-//    A~ tile arrives by one bulk copy (cp.async.bulk + mbarrier transaction
-//    count) and is complemented in place when the descriptor asks for P - A;
-//    the B slices stream through a shared-memory ring by 1-D bulk copies
-//    (already swizzled, no instructions spent on them); per slice the
-//    threads expand the A bits into a swizzled fp16 tile (two buffers) and
-//    one thread issues the tcgen05.mma chain into the TMEM accumulator and
-//    commits to mbarriers that free the A buffer and the ring slot; the
-//    epilogue reads the accumulator with tcgen05.ld, takes A~ and the tile's
-//    B' rows from shared memory, builds both output tiles in shared memory
-//    and writes each back with one bulk store.
+//    128B-swizzled K-major fp16 tile (digit columns x 64 K values);
+//  * k_gate_tc, one CTA (16 warps) per group of J work items (an item is a
+//    128-row tile of one gate's output; J > 1 for small ciphertexts so the
+//    CTA's fixed costs are shared): the A~ tiles arrive by bulk copies
+//    (cp.async.bulk + mbarrier transaction count) and are complemented in
+//    place when the descriptor asks for P - A; the B slices stream through a
+//    shared-memory ring by 1-D bulk copies (already swizzled); per (item,
+//    slice) step 14 warps expand the A bits into a swizzled fp16 tile and one
+//    warp issues the step's tcgen05.mma instructions (one elected lane, the
+//    MMAs and their commits in one instruction group) into the item's TMEM
+//    accumulator; the commits free the A buffer and the ring slot. The
+//    epilogue reads each accumulator with tcgen05.ld (all 16 warps turn digit
+//    sums into int64 word sums), then one thread per (row, element) runs the
+//    element's carry chain, and both output tiles go back by bulk stores.
 // Every mbarrier wait is bounded (~2 s); on timeout the kernel records
 // KERR_MMA_TIMEOUT, waits (bounded) for its own MMAs, frees its TMEM and
 // returns.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -51,6 +54,7 @@ constexpr uint32_t kSpinLimit = 1u << 26;
 constexpr uint64_t kWaitNs = 2000000000ull;    // bound of any single mbarrier wait
 constexpr uint32_t kMaxSmem = 232448;          // 227 KB opt-in per CTA
 constexpr int kExpandThreads = 256;
+constexpr uint32_t kMaxDigitBits = 11;         // fp16 holds the integers 0 .. 2048 exactly
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -78,12 +82,26 @@ __device__ __forceinline__ uint64_t global_ns() {
 }
 
 // Waits for the phase with the given parity, giving up after ~2 s (or an
-// iteration cap, whichever comes first).
+// iteration cap, whichever comes first). The timer is read only once the
+// first probe finds the phase still open.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_ns();
   for (uint32_t it = 0; it < kSpinLimit; it++) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((it & 255u) == 255u && global_ns() - t0 > kWaitNs) return false;
+  }
+  return false;
+}
+
+// As mbar_wait_bounded, and also gives up once `flag` is set (another role
+// stopped); the flag is read only on the slow path.
+__device__ __forceinline__ bool mbar_wait_flag(uint64_t* bar, uint32_t parity, volatile int* flag) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 0; it < kSpinLimit; it++) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255u) == 255u && (*flag || global_ns() - t0 > kWaitNs)) return false;
   }
   return false;
 }
@@ -132,20 +150,54 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
   asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
 
-// D[tmem] (+)= A[smem] * B[smem]^T, fp16 inputs, fp32 accumulate.
-__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                        uint32_t accumulate) {
+// One 64-wide K slice of one item, issued by one elected lane of the calling
+// warp (every lane executes the statement; the MMAs and the commits that
+// track them sit under the same elect.sync predicate, so one thread issues
+// all of them):
+//   D[d0] (+)= A * B0^T over four K=16 steps, the same into D[d1] with B1 when
+//   `two` is set; then commit -> fb, and -> fd if `last` (one commit per slice:
+//   a second one per slice costs the tensor pipe measurably).
+// A sits in tensor memory at column `at` (row i in lane i, two fp16 K values
+// per 32-bit column: a K=16 step is 8 columns); B0, B1 are 128B-swizzled
+// K-major shared-memory tiles (a descriptor advances 32 bytes = 2 units per
+// step). `acc` = 0 starts the accumulator (first slice of the item).
+__device__ __forceinline__ void mma_slice(uint32_t d0, uint32_t d1, uint32_t at, uint64_t b0,
+                                          uint64_t b1, uint32_t id0, uint32_t id1, uint32_t acc,
+                                          uint32_t two, uint64_t* fb, uint64_t* fd, uint32_t last) {
   asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      "{\n .reg .pred e, e2, e3, p, t;\n .reg .b32 a1, a2, a3;\n .reg .b64 x1, x2, x3, y1, y2, y3;\n"
+      " elect.sync _|e, 0xffffffff;\n"
+      " setp.ne.b32 p, %8, 0;\n"
+      " setp.eq.b32 t, %8, %8;\n"
+      " setp.ne.and.b32 e2, %9, 0, e;\n"
+      " setp.ne.and.b32 e3, %12, 0, e;\n"
+      " add.u32 a1, %3, 8;\n add.u32 a2, %3, 16;\n add.u32 a3, %3, 24;\n"
+      " add.u64 x1, %4, 2;\n add.u64 x2, %4, 4;\n add.u64 x3, %4, 6;\n"
+      " add.u64 y1, %5, 2;\n add.u64 y2, %5, 4;\n add.u64 y3, %5, 6;\n"
+      " @e tcgen05.mma.cta_group::1.kind::f16 [%1], [%3], %4, %6, p;\n"
+      " @e tcgen05.mma.cta_group::1.kind::f16 [%1], [a1], x1, %6, t;\n"
+      " @e tcgen05.mma.cta_group::1.kind::f16 [%1], [a2], x2, %6, t;\n"
+      " @e tcgen05.mma.cta_group::1.kind::f16 [%1], [a3], x3, %6, t;\n"
+      " @e2 tcgen05.mma.cta_group::1.kind::f16 [%2], [%3], %5, %7, p;\n"
+      " @e2 tcgen05.mma.cta_group::1.kind::f16 [%2], [a1], y1, %7, t;\n"
+      " @e2 tcgen05.mma.cta_group::1.kind::f16 [%2], [a2], y2, %7, t;\n"
+      " @e2 tcgen05.mma.cta_group::1.kind::f16 [%2], [a3], y3, %7, t;\n"
+      " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%10];\n"
+      " @e3 tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%11];\n}\n" ::"r"(0u),
+      "r"(d0), "r"(d1), "r"(at), "l"(b0), "l"(b1), "r"(id0), "r"(id1), "r"(acc), "r"(two),
+      "r"(smem_u32(fb)), "r"(smem_u32(fd)), "r"(last)
       : "memory");
 }
 
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                   smem_u32(bar))
-               : "memory");
+// Commit -> bar from the elected lane of the calling warp (the lane that
+// issued the warp's MMAs: with every lane active, elect.sync picks the same
+// leader each time).
+__device__ __forceinline__ void mma_commit_elected(uint64_t* bar) {
+  asm volatile(
+      "{\n .reg .pred e;\n elect.sync _|e, 0xffffffff;\n"
+      " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}\n" ::"r"(
+          smem_u32(bar))
+      : "memory");
 }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
@@ -157,6 +209,19 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
         "=r"(r[15])
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Each thread stores 32 consecutive 32-bit columns of its own lane.
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]),
+      "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]),
+      "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]),
+      "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
+      : "memory");
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
 // Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
@@ -171,15 +236,8 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   return d;
 }
 
-// Instruction descriptor of kind::f16: F16 x F16 -> F32, both K-major.
 __host__ __device__ constexpr uint32_t idesc_f16(uint32_t M, uint32_t N) {
   return (1u << 4) | ((N >> 3) << 17) | ((M >> 4) << 24);
-}
-
-// Byte offset of 16-byte chunk `c` (K elements 8c .. 8c+7) of row `r` in a
-// 128B-swizzled K-major tile.
-__device__ __forceinline__ uint32_t sw128_off(uint32_t r, uint32_t c) {
-  return r * 128u + ((c ^ (r & 7u)) << 4);
 }
 
 __device__ __forceinline__ int nib(uint32_t code, int k) {
@@ -207,9 +265,13 @@ __device__ __forceinline__ const uint32_t* ct_ptr(const KArgs& a, uint32_t ref) 
 }  // namespace
 
 struct TcShape {
-  uint32_t nd, ndpad, tmem_cols, mtiles, kblocks, nstages;
+  uint32_t dw;               // digit width in bits
+  uint32_t D, dpad;          // digits per element, digit columns per element (multiple of 16)
+  uint32_t ndpad;            // digit columns of a row (elements x dpad)
+  uint32_t tmem_cols, mtiles, kblocks, nstages;
   uint32_t n0_len, n1_len;   // MMA N of the two column chunks (n1_len 0 if one chunk)
   uint32_t btile;            // bytes of one expanded B slice (ndpad x 128)
+  uint32_t items;            // work items (gate x 128-row tile) per CTA
   uint32_t smem_bytes;
 };
 
@@ -220,7 +282,7 @@ struct TcShape {
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kExpandThreads) k_expand_b(KArgs a, TcShape t) {
   extern __shared__ uint32_t raw[];   // 64 rows x W words
-  const uint32_t W = a.W;
+  const uint32_t W = a.W, L = a.L;
   const uint64_t job = blockIdx.x / t.kblocks;
   const uint32_t kb = blockIdx.x % t.kblocks;
   if (job >= a.n) return;
@@ -232,125 +294,201 @@ __global__ void __launch_bounds__(kExpandThreads) k_expand_b(KArgs a, TcShape t)
     raw[e] = e < krows * W ? __ldg(src + e) : 0u;
   __syncthreads();
   uint4* dst = (uint4*)(a.bx + (job * t.kblocks + kb) * (uint64_t)t.btile);
+  const uint32_t mask = (1u << t.dw) - 1u;
   // 16-byte unit u of the tile image: row n = u / 8, stored position p = u % 8
-  // holds K chunk c = p ^ (n & 7); digit n = byte (n % 4) of word (n / 4).
+  // holds K chunk c = p ^ (n & 7); row n is digit d = n % dpad of element
+  // e = n / dpad: bits dw d .. dw d + dw - 1 of the element (zero past ell).
   for (uint32_t u = threadIdx.x; u < t.ndpad * 8u; u += kExpandThreads) {
     const uint32_t n = u >> 3, c = (u & 7u) ^ (n & 7u);
+    const uint32_t e = n / t.dpad, d = n - e * t.dpad;
     uint4 v = make_uint4(0, 0, 0, 0);
-    if (n < t.nd) {
-      const uint32_t w = n >> 2, b = n & 3u;
-      const uint32_t* rp = raw + c * 8u * W + w;
-      const uint32_t sel = b | ((b + 4) << 8);
-      v.x = (__byte_perm(rp[0], rp[W], sel) & 0x00FF00FFu) | 0x64006400u;
-      v.y = (__byte_perm(rp[2 * W], rp[3 * W], sel) & 0x00FF00FFu) | 0x64006400u;
-      v.z = (__byte_perm(rp[4 * W], rp[5 * W], sel) & 0x00FF00FFu) | 0x64006400u;
-      v.w = (__byte_perm(rp[6 * W], rp[7 * W], sel) & 0x00FF00FFu) | 0x64006400u;
+    if (d < t.D) {
+      const uint32_t bit = d * t.dw, wl = bit >> 5, sh = bit & 31u;
+      const bool hi = wl + 1 < L;   // the digit may continue in the element's next limb
+      const uint32_t* rp = raw + c * 8u * W + e * L + wl;
+      uint32_t h[8];
+#pragma unroll
+      for (int q = 0; q < 8; q++) {
+        const uint32_t dig = __funnelshift_r(rp[q * W], hi ? rp[q * W + 1] : 0u, sh) & mask;
+        h[q] = __half_as_ushort(__uint2half_rn(dig));
+      }
+      v.x = h[0] | (h[1] << 16);
+      v.y = h[2] | (h[3] << 16);
+      v.z = h[4] | (h[5] << 16);
+      v.w = h[6] | (h[7] << 16);
     }
     dst[u] = v;
   }
 }
 
+
 // ---------------------------------------------------------------------------
-// Shared-memory layout of k_gate_tc (offsets from a 1024-aligned base):
-//   ring    nstages x btile     expanded B slices (bulk copies)
-//   stageA  kAStages x 16 KB    expanded A slices
-//   tileA   128 x W words       A~ rows
-//   spop    128 words, then 24 mbarriers, the TMEM address slot, a flag
-// The epilogue reuses ring slot 0 for the tile's B' rows and slots 1, 2 for
-// the two output tiles (each slot >= 128 W words since ndpad >= 4 W).
+// Shared-memory layout of k_gate_tc (offsets from a 1024-aligned base), for J
+// work items per CTA (an item = one gate's 128-row output tile):
+//   ring    nstages x btile       expanded B slices (bulk copies)
+//   tileA   J x 128 x W words     A~ rows of every item
+//   brows   J x 128 x W words     B' rows of every item (epilogue)
+//   then 27 mbarriers, the TMEM address slot, a flag, and from the 32nd
+//   8-byte word on 4 words per item (gate, row0, rows, K rotation)
+// Tensor memory (512 columns): item j's accumulator at columns j ndpad ..
+// (j+1) ndpad - 1; the kAStages expanded A slices (32 columns each: 64 fp16
+// K values per lane = row) in the last 32 kAStages columns.
+// Epilogue (after the main loop): the ring holds the int64 word sums of the
+// current item (1024 (W | 1) bytes); output tiles 0 and 1 overwrite the
+// item's A~ and B' rows in place.
 //
-// Warp roles in the main loop (no CTA-wide barrier inside it):
-//   warp 0, lane 0   MMA issuer: waits "A stage full" and "B slot full",
-//                    issues the MMA chain, commits "A stage free" and
-//                    "B slot free"
-//   warp 1, lane 0   producer: refills each B slot once its MMAs are done
-//   warps 2 .. 15    expand A slices; each warp arrives on "A stage full"
+// Warp roles in the main loop (no CTA-wide barrier inside it); the loop runs
+// over steps = (item, 64-wide K slice), J x kblocks of them. Step st uses B
+// slot st % nstages and A stage st % kAStages; one pair of barriers per slot:
+// full[slot] completes when the slice's B bytes landed (transaction count of
+// the producer's arrival) and the four expander warps of the step arrived;
+// bfree[slot] when the step's MMAs are done (their single commit).
+//   warp 0           MMA issuer (one elected lane issues, the warp runs the
+//                    loop): waits full, issues the slice's MMAs into the
+//                    item's TMEM columns, commits -> bfree
+//   warp 1, lane 0   producer: refills a B slot once the MMAs of its
+//                    previous step are done
+//   warps 4 .. 11    expanders, two groups of four warps (one warp per TMEM
+//                    lane quarter) taking alternate steps: once the MMAs of
+//                    step st - kAStages (the stage's last readers) are done,
+//                    each thread turns its row's 64 bits of the slice into 64
+//                    fp16 values and stores them to its lane of the stage's
+//                    columns; each warp arrives on full. (nstages >= kAStages
+//                    keeps these waits unambiguous: the next phase of the
+//                    slot needs this step's MMAs first.)
 // ---------------------------------------------------------------------------
 constexpr uint32_t kAStages = 4;
-constexpr uint32_t kExpandWarps = kThreads / 32 - 2;
+constexpr uint32_t kExpandGroups = 2;
+constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kAColumns = 32 * kAStages;   // tensor-memory columns of the A stages
+
+// Position of a main-loop step: B slot and the parity of its phase, item and
+// K slice. Advanced incrementally, so the per-step paths divide nothing.
+struct StepPos {
+  uint32_t slot, phase, j, kb;
+  __device__ __forceinline__ void start(uint32_t st, const TcShape& t) {
+    slot = st % t.nstages;
+    phase = (st / t.nstages) & 1u;
+    j = st / t.kblocks;
+    kb = st % t.kblocks;
+  }
+  __device__ __forceinline__ void next(const TcShape& t) {
+    if (++slot == t.nstages) {
+      slot = 0;
+      phase ^= 1u;
+    }
+    if (++kb == t.kblocks) {
+      kb = 0;
+      j++;
+    }
+  }
+};
 
 __global__ void __launch_bounds__(kThreads, 1) k_gate_tc(KArgs a, TcShape t) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  const uint32_t W = a.W, L = a.L, NP1 = W / L;
+  const uint32_t W = a.W, L = a.L, NP1 = W / L, J = t.items;
   uint8_t* ring = smem;
-  uint8_t* stageA = ring + t.nstages * t.btile;
-  uint32_t* tileA = (uint32_t*)(stageA + kAStages * 16384u);
-  uint32_t* spop = tileA + kTileM * W;
-  uint64_t* bars = (uint64_t*)(spop + kTileM);
-  uint64_t* full = bars;          // [4] B slice landed
-  uint64_t* bfree = bars + 4;     // [4] MMAs reading the B slot finished
-  uint64_t* afull = bars + 8;     // [4] A stage expanded (one arrival per expander warp)
-  uint64_t* afree = bars + 12;    // [4] MMAs reading the A stage finished
-  uint64_t* abar = bars + 16;     // A tile landed
-  uint64_t* ebar = bars + 17;     // epilogue B rows landed
-  uint64_t* done = bars + 18;     // all MMAs finished
-  uint32_t* tslot = (uint32_t*)(bars + 24);
+  uint32_t* tileA = (uint32_t*)(ring + t.nstages * t.btile);
+  uint32_t* brows = tileA + J * kTileM * W;
+  uint64_t* bars = (uint64_t*)(brows + J * kTileM * W);
+  uint64_t* full = bars;          // [8] B slice landed and A stage expanded
+  uint64_t* bfree = bars + 8;     // [8] MMAs of the slot's step finished
+  uint64_t* abar = bars + 24;     // A tiles landed
+  uint64_t* ebar = bars + 25;     // epilogue B rows landed
+  uint64_t* done = bars + 26;     // all MMAs finished
+  uint32_t* tslot = (uint32_t*)(bars + 28);
   volatile int* sflag = (volatile int*)(tslot + 1);   // a bounded wait ran out
 
   const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const uint64_t g = blockIdx.x / t.mtiles;
-  const uint32_t row0 = (blockIdx.x % t.mtiles) * kTileM;
-  if (g >= a.n) return;
-  const uint32_t rows = (a.Ng - row0) < (uint32_t)kTileM ? (a.Ng - row0) : (uint32_t)kTileM;
-  const GateDesc d = a.desc[g];
-  const GateAux x = a.aux[g];
-  const bool gen = (d.a >> 30) == REG_GEN;
-  const uint32_t* A = gen ? nullptr : ct_ptr(a, d.a);
-  const uint64_t gst = gen ? stream_out(a.gen_state, d.a & SLOT_MASK) : 0;
-  const uint32_t* B = ct_ptr(a, d.b);
-  const uint8_t* bx = a.bx + (a.bx_shared ? 0 : g) * t.kblocks * (uint64_t)t.btile;
-  const bool comp = (x.flags & 1u) != 0;
+  const uint64_t n_items = a.n * t.mtiles;
+  const uint64_t item0 = (uint64_t)blockIdx.x * J;
+  if (item0 >= n_items) return;
+  const uint32_t nj = (uint32_t)((n_items - item0) < J ? (n_items - item0) : J);  // live items
+  const uint32_t steps = nj * t.kblocks;
+  // item j: gate, first row, live rows (computed once, kept in shared memory)
+  // The K slices of an item run in rotated order (tile m starts at slice
+  // m kblocks / mtiles; the exact integer sums do not depend on the order), so
+  // the tiles of one gate stream different B slices at any moment.
+  uint32_t* iinfo = (uint32_t*)(bars + 32);   // [J][4]: gate, row0, rows, rotation
+  if (tid < nj) {
+    const uint64_t it = item0 + tid;
+    const uint32_t m = (uint32_t)(it % t.mtiles), r0 = m * kTileM;
+    iinfo[4 * tid] = (uint32_t)(it / t.mtiles);
+    iinfo[4 * tid + 1] = r0;
+    iinfo[4 * tid + 2] = (a.Ng - r0) < (uint32_t)kTileM ? (a.Ng - r0) : (uint32_t)kTileM;
+    iinfo[4 * tid + 3] = m * t.kblocks / t.mtiles;
+  }
+  auto item_gate = [&](uint32_t j) { return (uint64_t)iinfo[4 * j]; };
+  auto item_row0 = [&](uint32_t j) { return iinfo[4 * j + 1]; };
+  auto item_rows = [&](uint32_t j) { return iinfo[4 * j + 2]; };
+  // slice of K consumed by step st (item st / kblocks)
+  auto step_kb = [&](uint32_t st) {
+    const uint32_t kb = st % t.kblocks + iinfo[4 * (st / t.kblocks) + 3];
+    return kb < t.kblocks ? kb : kb - t.kblocks;
+  };
+  auto item_bx = [&](uint32_t j) {
+    return a.bx + (a.bx_shared ? 0 : item_gate(j)) * t.kblocks * (uint64_t)t.btile;
+  };
 
   if (tid == 0) {
-    for (int b = 0; b < 19; b++) mbar_init(&bars[b], (b >= 8 && b < 12) ? kExpandWarps : 1u);
+    for (int b = 0; b < 27; b++) mbar_init(&bars[b], b < 8 ? 5u : 1u);   // full: producer + 4 warps
     *sflag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) tmem_alloc(tslot, t.tmem_cols);
+  if (warp == 0) tmem_alloc(tslot, kTmemCols);
   __syncthreads();
+  const bool gen = (a.desc[item_gate(0)].a >> 30) == REG_GEN;   // encryption: every item generated
   if (tid == 0) {
+    uint32_t bytes = 0;
+    for (uint32_t j = 0; j < nj; j++) bytes += item_rows(j) * W * 4u;
     if (!gen) {
-      mbar_expect_tx(abar, rows * W * 4u);
-      bulk_g2s(tileA, A + (uint64_t)row0 * W, rows * W * 4u, abar);
+      mbar_expect_tx(abar, bytes);
+      for (uint32_t j = 0; j < nj; j++) {
+        const uint32_t* A = ct_ptr(a, a.desc[item_gate(j)].a);
+        bulk_g2s(tileA + j * kTileM * W, A + (uint64_t)item_row0(j) * W, item_rows(j) * W * 4u, abar);
+      }
     }
-    for (uint32_t s = 0; s < t.nstages && s < t.kblocks; s++) {
+    // the epilogue's B' rows (for c2 B) arrive during the main loop
+    mbar_expect_tx(ebar, bytes);
+    for (uint32_t j = 0; j < nj; j++)
+      bulk_g2s(brows + j * kTileM * W, ct_ptr(a, a.desc[item_gate(j)].b) + (uint64_t)item_row0(j) * W,
+               item_rows(j) * W * 4u, ebar);
+    for (uint32_t s = 0; s < t.nstages && s < steps; s++) {
       mbar_expect_tx(&full[s], t.btile);
-      bulk_g2s(ring + s * t.btile, bx + (uint64_t)s * t.btile, t.btile, &full[s]);
+      bulk_g2s(ring + s * t.btile, item_bx(s / t.kblocks) + (uint64_t)step_kb(s) * t.btile,
+               t.btile, &full[s]);
     }
   }
   bool timed_out = false;
   if (gen) {
-    for (uint32_t e = tid; e < kTileM * W; e += kThreads) {
-      const uint32_t r = e / W, w = e % W;
-      tileA[e] = r < rows ? r_word(gst, (uint64_t)(row0 + r) * W + w) : 0u;
+    for (uint32_t e = tid; e < nj * kTileM * W; e += kThreads) {
+      const uint32_t j = e / (kTileM * W), r = (e / W) % kTileM, w = e % W;
+      const uint64_t gst = stream_out(a.gen_state, a.desc[item_gate(j)].a & SLOT_MASK);
+      tileA[e] = r < item_rows(j) ? r_word(gst, (uint64_t)(item_row0(j) + r) * W + w) : 0u;
     }
   } else {
     timed_out = !mbar_wait_bounded(abar, 0);
-    for (uint32_t e = rows * W + tid; e < kTileM * W; e += kThreads) tileA[e] = 0;
+    for (uint32_t j = 0; j < nj; j++)   // rows past the last ciphertext row of a partial tile
+      for (uint32_t e = item_rows(j) * W + tid; e < kTileM * W; e += kThreads)
+        tileA[j * kTileM * W + e] = 0;
   }
   __syncthreads();
-  // Complement (P - A) row by row with the borrow chain of each element; popcount.
+  // Complement (P - A) row by row with the borrow chain of each element.
   // Row i of P has one nonzero word: 2^(i % 32) at word (i / ell) L + (i % ell) / 32.
-  if (tid < kTileM) {
-    const uint32_t r = tid, i = row0 + r;
+  for (uint32_t task = tid; task < nj * kTileM; task += kThreads) {
+    const uint32_t j = task / kTileM, r = task % kTileM, i = item_row0(j) + r;
+    if (!(a.aux[item_gate(j)].flags & 1u) || r >= item_rows(j)) continue;
+    uint32_t* row = tileA + (j * kTileM + r) * W;
     const uint32_t pidx = (i / a.ell) * L + (i % a.ell) / 32, pval = 1u << (i % 32);
-    uint32_t pc = 0;
-    if (comp && r < rows) {
-      uint32_t borrow = 0, l = 0;
-      for (uint32_t w = 0; w < W; w++) {
-        if (l == 0) borrow = 0;
-        const uint64_t dv = (uint64_t)(w == pidx ? pval : 0u) - tileA[r * W + w] - borrow;
-        const uint32_t v = (uint32_t)dv;
-        borrow = (uint32_t)(dv >> 63);
-        tileA[r * W + w] = v;
-        pc += __popc(v);
-        if (++l == L) l = 0;
-      }
-    } else {
-      for (uint32_t w = 0; w < W; w++) pc += __popc(tileA[r * W + w]);
+    uint32_t borrow = 0, l = 0;
+    for (uint32_t w = 0; w < W; w++) {
+      if (l == 0) borrow = 0;
+      const uint64_t dv = (uint64_t)(w == pidx ? pval : 0u) - row[w] - borrow;
+      row[w] = (uint32_t)dv;
+      borrow = (uint32_t)(dv >> 63);
+      if (++l == L) l = 0;
     }
-    spop[r] = pc;
   }
   tc_fence_before();
   bool ok = !__syncthreads_or(timed_out);
@@ -360,199 +498,263 @@ __global__ void __launch_bounds__(kThreads, 1) k_gate_tc(KArgs a, TcShape t) {
   if (ok) {
     if (warp == 0) {
       // ---------------------------------------------------------- MMA issuer
-      if (lane == 0) {
-        const uint32_t idesc0 = idesc_f16(kTileM, t.n0_len), idesc1 = idesc_f16(kTileM, t.n1_len);
-        for (uint32_t kb = 0; kb < t.kblocks; kb++) {
-          const uint32_t s = kb % kAStages, slot = kb % t.nstages;
-          if (*sflag || !mbar_wait_bounded(&afull[s], (kb / kAStages) & 1) ||
-              !mbar_wait_bounded(&full[slot], (kb / t.nstages) & 1)) {
-            *sflag = 1;
-            break;
-          }
-          tc_fence_after();
-          const uint32_t a_base = smem_u32(stageA + s * 16384u), b_base = smem_u32(ring + slot * t.btile);
-#pragma unroll
-          for (uint32_t ks = 0; ks < kBK / 16; ks++) {
-            const uint64_t ad = sw128_desc(a_base + ks * 32);
-            mma_f16(tmem, ad, sw128_desc(b_base + ks * 32), idesc0, (kb | ks) != 0);
-            if (t.n1_len)
-              mma_f16(tmem + t.n0_len, ad, sw128_desc(b_base + t.n0_len * 128u + ks * 32), idesc1,
-                      (kb | ks) != 0);
-          }
-          mma_commit(&afree[s]);
-          mma_commit(&bfree[slot]);
+      const uint32_t idesc0 = idesc_f16(kTileM, t.n0_len), idesc1 = idesc_f16(kTileM, t.n1_len);
+      const uint32_t two = t.n1_len != 0, ring_s = smem_u32(ring);
+      const uint32_t acol = tmem + (kTmemCols - kAColumns);
+      bool issued_all = true;
+      StepPos p;
+      p.start(0, t);
+      for (uint32_t st = 0; st < steps; st++) {
+        if (!__all_sync(0xFFFFFFFFu, mbar_wait_flag(&full[p.slot], p.phase, sflag))) {
+          if (lane == 0) *sflag = 1;
+          issued_all = false;
+          break;
         }
-        mma_commit(done);   // tracks every MMA issued above
+        tc_fence_after();
+        const uint32_t b_base = ring_s + p.slot * t.btile;
+        const uint32_t d = tmem + p.j * t.ndpad;
+        mma_slice(d, d + t.n0_len, acol + 32u * (st & (kAStages - 1)), sw128_desc(b_base),
+                  sw128_desc(b_base + t.n0_len * 128u), idesc0, idesc1, p.kb != 0, two, &bfree[p.slot],
+                  done, st + 1 == steps);
+        p.next(t);
       }
+      // after a failed wait, `done` still has to track the MMAs issued so far
+      if (!issued_all) mma_commit_elected(done);
     } else if (warp == 1) {
       // ------------------------------------------------------------ producer
-      if (lane == 0) {
-        for (uint32_t kb = t.nstages; kb < t.kblocks; kb++) {
-          const uint32_t slot = kb % t.nstages, prev = kb - t.nstages;
-          if (*sflag || !mbar_wait_bounded(&bfree[slot], (prev / t.nstages) & 1)) {
+      if (lane == 0 && steps > t.nstages) {
+        StepPos p;
+        p.start(t.nstages, t);
+        uint32_t rot = iinfo[4 * p.j + 3];
+        const uint8_t* bx = item_bx(p.j);
+        for (uint32_t st = t.nstages; st < steps; st++) {
+          // the slot's previous step (st - nstages) ran in the other phase
+          if (!mbar_wait_flag(&bfree[p.slot], p.phase ^ 1u, sflag)) {
             *sflag = 1;
             break;
           }
-          mbar_expect_tx(&full[slot], t.btile);
-          bulk_g2s(ring + slot * t.btile, bx + (uint64_t)kb * t.btile, t.btile, &full[slot]);
+          uint32_t kbr = p.kb + rot;
+          if (kbr >= t.kblocks) kbr -= t.kblocks;
+          mbar_expect_tx(&full[p.slot], t.btile);
+          bulk_g2s(ring + p.slot * t.btile, bx + (uint64_t)kbr * t.btile, t.btile, &full[p.slot]);
+          const uint32_t oj = p.j;
+          p.next(t);
+          if (p.j != oj && p.j < nj) {
+            rot = iinfo[4 * p.j + 3];
+            bx = item_bx(p.j);
+          }
         }
       }
-    } else {
+    } else if (warp >= 4 && warp < 4 + 4 * kExpandGroups) {
       // ----------------------------------------------------------- expanders
-      const uint32_t et = tid - 64;   // 0 .. 32 kExpandWarps - 1
-      for (uint32_t kb = 0; kb < t.kblocks; kb++) {
-        const uint32_t s = kb % kAStages;
-        // lane 0 decides for the whole warp: stop if another role gave up, or
-        // once the MMAs of slice kb - kAStages (last readers of this stage) are done
+      const uint32_t grp = (warp - 4) / 4, q = warp & 3, r = q * 32 + lane;
+      const uint32_t acol = tmem + ((q * 32u) << 16) + (kTmemCols - kAColumns);
+      StepPos p;
+      p.start(grp, t);
+      uint32_t rot = p.j < nj ? iinfo[4 * p.j + 3] : 0u;
+      for (uint32_t st = grp; st < steps; st += kExpandGroups) {
+        // lane 0 decides for the whole warp: go on once the MMAs of step
+        // st - kAStages (the stage's last readers) are done; that step used
+        // slot - kAStages, in the previous phase if the slot index wrapped
         int stop = 0;
-        if (lane == 0) {
-          stop = *sflag;
-          if (!stop && kb >= kAStages &&
-              !mbar_wait_bounded(&afree[s], ((kb - kAStages) / kAStages) & 1)) {
+        if (lane == 0 && st >= kAStages) {
+          const bool wrap = p.slot < kAStages;
+          const uint32_t ps = wrap ? p.slot + t.nstages - kAStages : p.slot - kAStages;
+          if (!mbar_wait_flag(&bfree[ps], wrap ? p.phase ^ 1u : p.phase, sflag)) {
             *sflag = 1;
             stop = 1;
           }
         }
         if (__shfl_sync(0xFFFFFFFFu, stop, 0)) break;
-        uint8_t* sA = stageA + s * 16384u;
-        for (uint32_t e = et; e < kTileM * 8u; e += 32u * kExpandWarps) {
-          const uint32_t r = e >> 3, c = e & 7;
-          const uint32_t kbit = kb * kBK + c * 8;
-          const uint32_t wi = kbit >> 5;
-          const uint32_t byte = wi < W ? (tileA[r * W + wi] >> (kbit & 31)) & 0xFFu : 0u;
-          *(uint4*)(sA + sw128_off(r, c)) = byte_to_h8(byte);
+        tc_fence_after();
+        uint32_t kb = p.kb + rot;
+        if (kb >= t.kblocks) kb -= t.kblocks;
+        // row r's bits 64 kb .. 64 kb + 63 (words 2 kb, 2 kb + 1; zero past the
+        // row) -> 64 fp16 values, K value k in half k % 2 of column k / 2
+        const uint32_t* row = tileA + (p.j * kTileM + r) * W;
+        const uint32_t w0 = 2u * kb < W ? row[2u * kb] : 0u;
+        const uint32_t w1 = 2u * kb + 1u < W ? row[2u * kb + 1u] : 0u;
+        uint32_t v[32];
+#pragma unroll
+        for (uint32_t b = 0; b < 8; b++) {
+          const uint4 h = byte_to_h8(((b < 4 ? w0 : w1) >> (8u * (b & 3u))) & 0xFFu);
+          v[4 * b] = h.x;
+          v[4 * b + 1] = h.y;
+          v[4 * b + 2] = h.z;
+          v[4 * b + 3] = h.w;
         }
-        fence_proxy_async_smem();
+        tmem_st32(acol + 32u * (st & (kAStages - 1)), v);
+        tc_fence_before();
         __syncwarp();
-        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&afull[s])) : "memory");
+        if (lane == 0)
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full[p.slot])) : "memory");
+        const uint32_t oj = p.j;
+        for (uint32_t k = 0; k < kExpandGroups; k++) p.next(t);
+        if (p.j != oj && p.j < nj) rot = iinfo[4 * p.j + 3];
       }
     }
   }
   __syncthreads();
   if (ok && *sflag) ok = false;
   if (ok) {
-    // every MMA finished -> the ring is free: fetch the tile's B' rows (for c2 B)
-    bool w_ok = mbar_wait_bounded(done, 0);
-    if (w_ok && tid == 0) {
-      mbar_expect_tx(ebar, rows * W * 4u);
-      bulk_g2s(ring, B + (uint64_t)row0 * W, rows * W * 4u, ebar);
-    }
-    w_ok = w_ok && mbar_wait_bounded(ebar, 0);
+    // every MMA finished and the B' rows landed
+    const bool w_ok = mbar_wait_bounded(done, 0) && mbar_wait_bounded(ebar, 0);
     ok = !__syncthreads_or(!w_ok);
   }
   if (!ok) {
     if (tid == 0 && a.err) atomicExch(a.err, KERR_MMA_TIMEOUT);
     mbar_wait_bounded(done, 0);   // bounded: let own MMAs drain before TMEM is freed
+    mbar_wait_bounded(ebar, 0);   // and the bulk copies into shared memory
   }
   tc_fence_after();
 
-  if (ok) {
-    // Epilogue, phase 1 (all warps): warp w reads TMEM lanes 32 (w % 4) ..
-    // (its rows) and every fourth 16-column chunk starting at chunk w / 4;
-    // each word's product part K[r][w] = sum_b S[r][4w+b] 2^(8b) goes to
-    // shared memory as int64 (ring slots 1-2, free now).
-    int64_t* Kv = (int64_t*)(ring + t.btile);
+  // Epilogue. Phase 1 (all warps): warp w reads TMEM lanes 32 (w % 4) .. +31
+  // (its rows) over the digit columns of the row's words [w/4 W/4, (w/4+1) W/4);
+  // digit d of element e adds S << (dw d mod 32) to word (dw d) / 32 of the
+  // element (every word gets at least two digits, in column order) and the
+  // int64 word sums go to Kv (row stride KS = W | 1 words of 8 bytes, odd, so
+  // a warp's rows fall in distinct bank pairs). Phase 2: one thread per (row,
+  // element) runs the element's carry chain with the linear terms; output
+  // tile 0 overwrites the item's A~ rows and tile 1 its B' rows in place.
+  int64_t* Kv = (int64_t*)ring;
+  const uint32_t KS = W | 1u;
+  for (uint32_t j = 0; ok && j < nj; j++) {
+    const uint64_t g = item_gate(j);
+    const uint32_t row0 = item_row0(j), rows = item_rows(j);
+    const GateDesc gd = a.desc[g];
+    const GateAux x = a.aux[g];
+    uint32_t* At = tileA + j * kTileM * W;               // A~ rows, then output tile 0
+    uint32_t* Bt = brows + j * kTileM * W;               // B' rows, then output tile 1
     {
-      const uint32_t r = (warp & 3) * 32 + lane;
-      const bool live = r < rows;
-      const int64_t bias = 1024 * (int64_t)spop[r];
-      for (uint32_t n0 = (warp >> 2) * 16u; n0 < t.nd; n0 += 64u) {
-        uint32_t v[16];
-        tmem_ld16(tmem + (((warp & 3) * 32u) << 16) + n0, v);
+      const uint32_t q = warp & 3, cg = warp >> 2, r = q * 32 + lane;
+      const uint32_t gw0 = cg * W / 4, gw1 = (cg + 1) * W / 4;
+      // first digit column of global word gw (element gw / L, local word gw % L)
+      auto first_col = [&](uint32_t gw) {
+        const uint32_t e = gw / L, wl = gw - e * L;
+        return e * t.dpad + (32u * wl + t.dw - 1) / t.dw;
+      };
+      if (gw0 < gw1) {
+        const uint32_t n0 = first_col(gw0), n1 = first_col(gw1);
+        const uint32_t taddr = tmem + ((q * 32u) << 16) + j * t.ndpad;
+        int64_t acc = 0;
+        uint32_t cur = gw0;
+        for (uint32_t c0 = n0 & ~15u; c0 < n1; c0 += 16) {
+          uint32_t v[16];
+          tmem_ld16(taddr + c0, v);
+          const uint32_t e = c0 / t.dpad, dbase = c0 - e * t.dpad;   // a chunk lies in one element
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
-          const uint32_t w = n0 / 4 + q;
-          if (w >= W || !live) continue;
-          int64_t k = 0;
-#pragma unroll
-          for (int b = 0; b < 4; b++) {
-            const int64_t sv = (int64_t)__float2int_rn(__uint_as_float(v[4 * q + b])) - bias;
-            k += sv << (8 * b);
+          for (uint32_t k = 0; k < 16; k++) {
+            const uint32_t n = c0 + k, d = dbase + k;
+            if (n >= n0 && n < n1 && d < t.D) {
+              const uint32_t bit = d * t.dw, gw = e * L + (bit >> 5);
+              if (gw != cur) {
+                Kv[r * KS + cur] = acc;
+                acc = 0;
+                cur = gw;
+              }
+              acc += (int64_t)__float2int_rn(__uint_as_float(v[k])) << (bit & 31u);
+            }
           }
-          Kv[r * W + w] = k;
+        }
+        Kv[r * KS + cur] = acc;   // word gw1 - 1
+      }
+    }
+    __syncthreads();
+    {
+      const uint32_t code0 = x.code & 0xFFFFu, code1 = x.code >> 16;
+      int c00 = nib(code0, 0), c01 = nib(code0, 1), c02 = nib(code0, 2), c03 = nib(code0, 3);
+      int c10 = nib(code1, 0), c11 = nib(code1, 1), c12 = nib(code1, 2), c13 = nib(code1, 3);
+      if (x.flags & 1u) {  // the stored A is P - A~: c1 A = c1 P - c1 A~
+        c00 += c01;
+        c01 = -c01;
+        c10 += c11;
+        c11 = -c11;
+      }
+      for (uint32_t task = tid; task < kTileM * NP1; task += kThreads) {
+        const uint32_t r = task % kTileM, e = task / kTileM, i = row0 + r;
+        if (r >= rows) continue;
+        // row i of P: 2^(i % 32) at word (i / ell) L + (i % ell) / 32
+        const uint32_t pw_at = (i / a.ell) * L + (i % a.ell) / 32;
+        const int64_t pval = (int64_t)1 << (i % 32);
+        uint32_t* Ar = At + r * W;
+        uint32_t* Br = Bt + r * W;
+        const int64_t* Kr = Kv + r * KS;
+        int64_t carry0 = 0, carry1 = 0;
+        for (uint32_t w = e * L; w < (e + 1) * L; w++) {
+          const int64_t k = Kr[w], aw = Ar[w], bw = Br[w], pw = w == pw_at ? pval : 0;
+          const int64_t o0 = c03 * k + c01 * aw + c02 * bw + c00 * pw + carry0;
+          const int64_t o1 = c13 * k + c11 * aw + c12 * bw + c10 * pw + carry1;
+          carry0 = o0 >> 32;
+          carry1 = o1 >> 32;
+          Ar[w] = (uint32_t)o0;
+          Br[w] = (uint32_t)o1;
         }
       }
     }
-    __syncthreads();
-    // Phase 2: one thread per (row, element): linear terms and the limb
-    // carries of the element; output tile 0 -> stage A area, output tile 1
-    // overwrites the tile's B' rows (each word read before it is replaced).
-    const uint32_t* Bt = (const uint32_t*)ring;
-    uint32_t* T0 = (uint32_t*)stageA;
-    uint32_t* T1 = (uint32_t*)ring;
-    uint32_t code0 = x.code & 0xFFFFu, code1 = x.code >> 16;
-    int c00 = nib(code0, 0), c01 = nib(code0, 1), c02 = nib(code0, 2), c03 = nib(code0, 3);
-    int c10 = nib(code1, 0), c11 = nib(code1, 1), c12 = nib(code1, 2), c13 = nib(code1, 3);
-    if (comp) {  // the stored A is P - A~: c1 A = c1 P - c1 A~
-      c00 += c01;
-      c01 = -c01;
-      c10 += c11;
-      c11 = -c11;
-    }
-    const bool has0 = d.o0 != REF_NONE, has1 = d.o1 != REF_NONE;
-    for (uint32_t task = tid; task < kTileM * NP1; task += kThreads) {
-      const uint32_t r = task % kTileM, j = task / kTileM, i = row0 + r;
-      if (r >= rows) continue;
-      const uint32_t pidx = (i / a.ell) * L + (i % a.ell) / 32, pval = 1u << (i % 32);
-      int64_t carry0 = 0, carry1 = 0;
-      for (uint32_t w = j * L; w < (j + 1) * L; w++) {
-        const int64_t k = Kv[r * W + w];
-        const int64_t aw = (int64_t)tileA[r * W + w];
-        const int64_t bw = (int64_t)Bt[r * W + w];
-        const int64_t pw = w == pidx ? (int64_t)pval : 0;
-        const int64_t o0 = c03 * k + c01 * aw + c02 * bw + c00 * pw + carry0;
-        const int64_t o1 = c13 * k + c11 * aw + c12 * bw + c10 * pw + carry1;
-        carry0 = o0 >> 32;
-        carry1 = o1 >> 32;
-        T0[r * W + w] = (uint32_t)o0;
-        T1[r * W + w] = (uint32_t)o1;
-      }
-    }
     fence_proxy_async_smem();
-    __syncthreads();
+    __syncthreads();   // also: Kv is rewritten by the next item's phase 1
     if (tid == 0) {
-      if (has0)
-        bulk_s2g(a.base[d.o0 >> 30] + (uint64_t)(d.o0 & SLOT_MASK) * a.ctw + (uint64_t)row0 * W, T0,
+      if (gd.o0 != REF_NONE)
+        bulk_s2g(a.base[gd.o0 >> 30] + (uint64_t)(gd.o0 & SLOT_MASK) * a.ctw + (uint64_t)row0 * W, At,
                  rows * W * 4u);
-      if (has1)
-        bulk_s2g(a.base[d.o1 >> 30] + (uint64_t)(d.o1 & SLOT_MASK) * a.ctw + (uint64_t)row0 * W, T1,
+      if (gd.o1 != REF_NONE)
+        bulk_s2g(a.base[gd.o1 >> 30] + (uint64_t)(gd.o1 & SLOT_MASK) * a.ctw + (uint64_t)row0 * W, Bt,
                  rows * W * 4u);
       asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-      asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
     }
   }
+  // the output tiles stay untouched until the CTA ends: one wait for every store
+  if (tid == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    tmem_dealloc(tmem, t.tmem_cols);
+    tmem_dealloc(tmem, kTmemCols);
   }
 }
 
 namespace {
 
-bool make_tc_shape(const KArgs& a, TcShape* t) {
-  if (a.Ng < 128 || a.W == 0) return false;
-  t->nd = a.W * 4;
-  t->ndpad = (t->nd + 15) / 16 * 16;
+uint32_t tc_smem_bytes(uint32_t W, uint32_t btile, uint32_t ns, uint32_t J) {
+  return 1024u + ns * btile + 2u * J * (uint32_t)kTileM * W * 4u + 256u + 16u * J;
+}
+
+// Shape of the kernel for up to `jmax` items per CTA (0 = the largest that fits).
+bool make_tc_shape(const KArgs& a, TcShape* t, uint32_t jmax = 1) {
+  if (a.Ng < 128 || a.W == 0 || a.L == 0 || a.ell != 32 * a.L) return false;
+  const uint32_t NP1 = a.W / a.L;
+  // digit width: exact fp16 operand and every column sum below 2^24
+  t->dw = kMaxDigitBits;
+  while (t->dw > 1 && (uint64_t)a.Ng * ((1u << t->dw) - 1u) >= (1u << 24)) t->dw--;
+  t->D = (a.ell + t->dw - 1) / t->dw;
+  t->dpad = (t->D + 15) / 16 * 16;
+  t->ndpad = NP1 * t->dpad;
   if (t->ndpad > 512) return false;
-  t->n0_len = t->ndpad < 256 ? t->ndpad : 256;
+  // one MMA up to N = 256, else two balanced chunks (multiples of 16)
+  t->n0_len = t->ndpad <= 256 ? t->ndpad : (t->ndpad / 2 + 15) / 16 * 16;
   t->n1_len = t->ndpad - t->n0_len;
-  t->tmem_cols = 32;
-  while (t->tmem_cols < t->ndpad) t->tmem_cols *= 2;
   t->mtiles = (a.Ng + kTileM - 1) / kTileM;
   t->kblocks = (a.Ng + kBK - 1) / kBK;
   t->btile = t->ndpad * 128u;
-  for (uint32_t ns = 4; ns >= 3; ns--) {
-    const uint32_t bytes = 1024u + ns * t->btile + kAStages * 16384u + (uint32_t)kTileM * a.W * 4u +
-                           (uint32_t)kTileM * 4u + 256u;
-    if (bytes <= kMaxSmem) {
+  t->nstages = 0;
+  for (uint32_t ns = 8; ns >= kAStages; ns--)
+    if (tc_smem_bytes(a.W, t->btile, ns, 1) <= kMaxSmem) {
       t->nstages = ns;
-      t->smem_bytes = bytes;
-      return true;
+      break;
     }
-  }
-  return false;
+  // the epilogue keeps the int64 word sums (128 rows of W | 1) in the ring
+  if (!t->nstages || t->nstages * t->btile < 1024u * (a.W | 1u)) return false;
+  // items per CTA: TMEM columns, stage A room for the epilogue's B rows, smem
+  uint32_t J = 1;
+  const uint32_t cap = jmax ? jmax : 64;
+  if (t->ndpad + kAColumns > kTmemCols) return false;
+  while (J < cap && (J + 1) * t->ndpad + kAColumns <= kTmemCols &&
+         tc_smem_bytes(a.W, t->btile, t->nstages, J + 1) <= kMaxSmem)
+    J++;
+  t->items = J;
+  t->tmem_cols = kTmemCols;
+  t->smem_bytes = tc_smem_bytes(a.W, t->btile, t->nstages, J);
+  return true;
 }
 
 }  // namespace
@@ -566,6 +768,12 @@ uint64_t tc_bx_bytes_per_gate(const KArgs& a) {
   TcShape t;
   if (!make_tc_shape(a, &t)) return 0;
   return (uint64_t)t.kblocks * t.btile;
+}
+
+uint32_t tc_digit_columns(const KArgs& a) {
+  TcShape t;
+  if (!make_tc_shape(a, &t)) return 0;
+  return (a.W / a.L) * t.D;
 }
 
 // A level runs in chunks of gates (expand a chunk's B operands, then multiply
@@ -587,8 +795,8 @@ uint64_t tc_bx_bytes(const KArgs& a, uint64_t gates) {
 
 int launch_gates_tc(const KArgs& a, cudaStream_t st) {
   if (a.n == 0) return SFFT_OK;
-  TcShape t{};
-  if (!make_tc_shape(a, &t)) return fail(SFFT_EPARAM, "tensor-core kernel does not support this shape");
+  TcShape t0{};
+  if (!make_tc_shape(a, &t0, 0)) return fail(SFFT_EPARAM, "tensor-core kernel does not support this shape");
   if (!a.bx) return fail(SFFT_EINVAL, "tensor-core kernel needs its B expansion buffer");
   static bool configured = false;
   if (!configured) {
@@ -607,10 +815,16 @@ int launch_gates_tc(const KArgs& a, cudaStream_t st) {
     ca.n = (a.n - c0) < chunk ? (a.n - c0) : chunk;
     KArgs ea = ca;
     ea.n = a.bx_shared ? 1 : ca.n;
-    k_expand_b<<<(unsigned)(ea.n * t.kblocks), kExpandThreads, kBK * a.W * 4u, st>>>(ea, t);
+    k_expand_b<<<(unsigned)(ea.n * t0.kblocks), kExpandThreads, kBK * a.W * 4u, st>>>(ea, t0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "B expansion launch");
-    k_gate_tc<<<(unsigned)(ca.n * t.mtiles), kThreads, t.smem_bytes, st>>>(ca, t);
+    // items per CTA: as many as fit, but keep at least two CTAs per SM's worth of work
+    const uint64_t items = ca.n * t0.mtiles;
+    const uint64_t want = std::max<uint64_t>(1, items / (2 * 152));
+    TcShape t{};
+    make_tc_shape(a, &t, (uint32_t)std::min<uint64_t>(want, t0.items));
+    const uint64_t blocks = (items + t.items - 1) / t.items;
+    k_gate_tc<<<(unsigned)blocks, kThreads, t.smem_bytes, st>>>(ca, t);
     count_launches(2);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "tc gate kernel launch");

@@ -24,7 +24,7 @@ class sfft_plan_info(ctypes.Structure):
                 ("gates_or", c_u64), ("gates_not", c_u64), ("products", c_u64), ("levels", c_u64),
                 ("max_level_width", c_u64), ("scratch_slots", c_u64), ("scratch_bytes", c_u64),
                 ("ct_words", c_u64), ("noise_bits", c_u32), ("noise_ok", c_u32),
-                ("gate_kernel", c_u32), ("reserved", c_u32)]
+                ("gate_kernel", c_u32), ("tc_columns", c_u32)]
 
 
 P = ctypes.POINTER

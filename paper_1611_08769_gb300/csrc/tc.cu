@@ -54,7 +54,9 @@ constexpr uint32_t kSpinLimit = 1u << 26;
 constexpr uint64_t kWaitNs = 2000000000ull;    // bound of any single mbarrier wait
 constexpr uint32_t kMaxSmem = 232448;          // 227 KB opt-in per CTA
 constexpr int kExpandThreads = 256;
-constexpr uint32_t kMaxDigitBits = 11;         // fp16 holds the integers 0 .. 2048 exactly
+constexpr uint32_t kDigitBits = 11;            // fp16 holds the integers 0 .. 2048 exactly
+// 32 digits of 11 bits span 352 bits = 11 words: the epilogue's unit of work
+constexpr uint32_t kGroupDigits = 32, kGroupWords = 11;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -120,15 +122,13 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       : "memory");
 }
 
-// Bulk copy shared -> global (bulk-group completion).
-__device__ __forceinline__ void bulk_s2g(void* dst, const void* src, uint32_t bytes) {
-  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
-               "r"(smem_u32(src)), "r"(bytes)
-               : "memory");
+// 4-byte asynchronous copy global -> shared (completion by commit/wait group).
+__device__ __forceinline__ void cp_async4(uint32_t* dst, const uint32_t* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
 
-__device__ __forceinline__ void fence_proxy_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
 }
 
 __device__ __forceinline__ void tc_fence_before() {
@@ -268,10 +268,11 @@ struct TcShape {
   uint32_t dw;               // digit width in bits
   uint32_t D, dpad;          // digits per element, digit columns per element (multiple of 16)
   uint32_t ndpad;            // digit columns of a row (elements x dpad)
-  uint32_t tmem_cols, mtiles, kblocks, nstages;
+  uint32_t mtiles, kblocks, nstages;
   uint32_t n0_len, n1_len;   // MMA N of the two column chunks (n1_len 0 if one chunk)
   uint32_t btile;            // bytes of one expanded B slice (ndpad x 128)
-  uint32_t items;            // work items (gate x 128-row tile) per CTA
+  uint32_t G;                // digit groups of 32 per element (epilogue units)
+  uint32_t nacc;             // accumulator slots in tensor memory
   uint32_t smem_bytes;
 };
 
@@ -321,46 +322,54 @@ __global__ void __launch_bounds__(kExpandThreads) k_expand_b(KArgs a, TcShape t)
   }
 }
 
-
 // ---------------------------------------------------------------------------
-// Shared-memory layout of k_gate_tc (offsets from a 1024-aligned base), for J
-// work items per CTA (an item = one gate's 128-row output tile):
-//   ring    nstages x btile       expanded B slices (bulk copies)
-//   tileA   J x 128 x W words     A~ rows of every item
-//   brows   J x 128 x W words     B' rows of every item (epilogue)
-//   then 27 mbarriers, the TMEM address slot, a flag, and from the 32nd
-//   8-byte word on 4 words per item (gate, row0, rows, K rotation)
-// Tensor memory (512 columns): item j's accumulator at columns j ndpad ..
-// (j+1) ndpad - 1; the kAStages expanded A slices (32 columns each: 64 fp16
-// K values per lane = row) in the last 32 kAStages columns.
-// Epilogue (after the main loop): the ring holds the int64 word sums of the
-// current item (1024 (W | 1) bytes); output tiles 0 and 1 overwrite the
-// item's A~ and B' rows in place.
+// k_gate_tc is persistent: one CTA per SM, CTA b takes the work items b,
+// b + grid, b + 2 grid, ... (item x = 128-row output tile x % mtiles of gate
+// x / mtiles). Neighbouring CTAs work on tiles of the same gate at the same
+// time and share its B slices in L2; tile m runs its K slices in rotated
+// order (from slice m kblocks / mtiles on; the exact integer sums do not
+// depend on the order), so those tiles stream different slices at any moment.
 //
-// Warp roles in the main loop (no CTA-wide barrier inside it); the loop runs
-// over steps = (item, 64-wide K slice), J x kblocks of them. Step st uses B
-// slot st % nstages and A stage st % kAStages; one pair of barriers per slot:
-// full[slot] completes when the slice's B bytes landed (transaction count of
-// the producer's arrival) and the four expander warps of the step arrived;
-// bfree[slot] when the step's MMAs are done (their single commit).
-//   warp 0           MMA issuer (one elected lane issues, the warp runs the
-//                    loop): waits full, issues the slice's MMAs into the
-//                    item's TMEM columns, commits -> bfree
-//   warp 1, lane 0   producer: refills a B slot once the MMAs of its
-//                    previous step are done
-//   warps 4 .. 11    expanders, two groups of four warps (one warp per TMEM
-//                    lane quarter) taking alternate steps: once the MMAs of
-//                    step st - kAStages (the stage's last readers) are done,
-//                    each thread turns its row's 64 bits of the slice into 64
-//                    fp16 values and stores them to its lane of the stage's
-//                    columns; each warp arrives on full. (nstages >= kAStages
-//                    keeps these waits unambiguous: the next phase of the
-//                    slot needs this step's MMAs first.)
+// Shared memory (offsets from a 1024-aligned base):
+//   ring    nstages x btile            expanded B slices (bulk copies)
+//   tiles   2 x 128 x W words          A~ rows of two items (double buffer),
+//                                      complemented in place or generated
+//   carr    128 x NP1 x (G - 1) x 16   epilogue carries between digit groups
+//   ebuf    8 warps x 2 x 32 x 11 words  epilogue staging: a unit's A and B
+//                                      words, then its two output blocks
+//   then the mbarriers, the TMEM address slot and the stop flag
+// Tensor memory (512 columns): nacc accumulators of ndpad columns (item j of
+// the CTA in slot j % nacc), then kAStages expanded A slices of 32 columns
+// (64 fp16 K values per lane = row).
+//
+// The CTA's steps are its items in order, kblocks 64-wide K slices each;
+// step st uses B slot st % nstages and A stage st % kAStages. Barriers:
+//   full[slot]    the slice's B bytes landed (transaction count of the
+//                 producer's arrival) and the four expander warps arrived
+//   bfree[slot]   the step's MMAs are done (its one commit)
+//   tfull[buf]    an A tile landed;  tfree[buf] the expanders are done with it
+//   accfull[acc]  an item's MMAs are done;  accfree[acc] the epilogue has
+//                 read the accumulator
+// (nstages >= kAStages keeps every wait on a phase unambiguous: a barrier's
+// next phase needs progress that the waiter itself has to make first.)
+// Roles:
+//   warp 0       MMA issuer (one elected lane issues, the warp runs the loop)
+//   warp 1       lane 0: producer of A tiles and B slices (bulk copies)
+//   warps 4..7   expanders, one per TMEM lane quarter: each thread owns one
+//                row: prepares it (complement or generation) when an item
+//                starts, then turns its 64 bits of each K slice into 64 fp16
+//                values in its lane of the stage's columns
+//   warps 8..15  epilogue of item j while item j+1 is multiplied
+//   warps 2, 3   idle
 // ---------------------------------------------------------------------------
 constexpr uint32_t kAStages = 4;
-constexpr uint32_t kExpandGroups = 2;
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kAColumns = 32 * kAStages;   // tensor-memory columns of the A stages
+constexpr uint32_t kAColumn0 = kTmemCols - kAColumns;
+constexpr uint32_t kMaxAcc = 4;
+constexpr uint32_t kExpandWarp0 = 4, kEpiWarp0 = 8, kEpiWarps = 8;
+constexpr uint32_t kBars = 40;                   // mbarrier slots (8 bytes each)
+constexpr uint32_t kEbufWords = 2 * 32 * kGroupWords;   // epilogue staging per warp
 
 // Position of a main-loop step: B slot and the parity of its phase, item and
 // K slice. Advanced incrementally, so the per-step paths divide nothing.
@@ -384,327 +393,411 @@ struct StepPos {
   }
 };
 
+// Work item -> gate, first row, live rows, K rotation.
+struct ItemInfo {
+  uint32_t gate, row0, rows, rot;
+  __device__ __forceinline__ ItemInfo(uint64_t item, const KArgs& a, const TcShape& t) {
+    gate = (uint32_t)(item / t.mtiles);
+    const uint32_t m = (uint32_t)(item % t.mtiles);
+    row0 = m * kTileM;
+    rows = (a.Ng - row0) < (uint32_t)kTileM ? (a.Ng - row0) : (uint32_t)kTileM;
+    rot = m * t.kblocks / t.mtiles;
+  }
+};
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Barrier of the epilogue warps on an mbarrier (count kEpiWarps), so that the
+// wait is bounded like every other: true once all of them arrived.
+__device__ __forceinline__ bool epi_sync(uint64_t* bar, uint32_t& phase, volatile int* flag) {
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0) mbar_arrive(bar);
+  const bool ok = __all_sync(0xFFFFFFFFu, mbar_wait_flag(bar, phase, flag));
+  phase ^= 1u;
+  return ok;
+}
+
 __global__ void __launch_bounds__(kThreads, 1) k_gate_tc(KArgs a, TcShape t) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  const uint32_t W = a.W, L = a.L, NP1 = W / L, J = t.items;
+  const uint32_t W = a.W, L = a.L, NP1 = W / L, G = t.G;
   uint8_t* ring = smem;
-  uint32_t* tileA = (uint32_t*)(ring + t.nstages * t.btile);
-  uint32_t* brows = tileA + J * kTileM * W;
-  uint64_t* bars = (uint64_t*)(brows + J * kTileM * W);
-  uint64_t* full = bars;          // [8] B slice landed and A stage expanded
-  uint64_t* bfree = bars + 8;     // [8] MMAs of the slot's step finished
-  uint64_t* abar = bars + 24;     // A tiles landed
-  uint64_t* ebar = bars + 25;     // epilogue B rows landed
-  uint64_t* done = bars + 26;     // all MMAs finished
-  uint32_t* tslot = (uint32_t*)(bars + 28);
-  volatile int* sflag = (volatile int*)(tslot + 1);   // a bounded wait ran out
+  uint32_t* tiles = (uint32_t*)(ring + t.nstages * t.btile);
+  int64_t* carr = (int64_t*)(tiles + 2 * kTileM * W);
+  uint32_t* ebuf = (uint32_t*)((uint8_t*)carr + (size_t)kTileM * NP1 * (G - 1) * 16u);
+  uint64_t* bars = (uint64_t*)(ebuf + kEpiWarps * kEbufWords);
+  uint64_t* full = bars;          // [8]
+  uint64_t* bfree = bars + 8;     // [8]
+  uint64_t* tfull = bars + 16;    // [2]
+  uint64_t* tfree = bars + 18;    // [2]
+  uint64_t* accfull = bars + 20;  // [kMaxAcc]
+  uint64_t* accfree = bars + 24;  // [kMaxAcc]
+  uint64_t* drain = bars + 28;    // the issuer's MMAs are done (waited on in the error path)
+  uint64_t* esync = bars + 29;    // epilogue warps' barrier
+  uint32_t* tslot = (uint32_t*)(bars + 32);
+  volatile int* sflag = (volatile int*)(tslot + 1);   // some role gave up (bounded wait ran out)
 
   const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint64_t n_items = a.n * t.mtiles;
-  const uint64_t item0 = (uint64_t)blockIdx.x * J;
-  if (item0 >= n_items) return;
-  const uint32_t nj = (uint32_t)((n_items - item0) < J ? (n_items - item0) : J);  // live items
-  const uint32_t steps = nj * t.kblocks;
-  // item j: gate, first row, live rows (computed once, kept in shared memory)
-  // The K slices of an item run in rotated order (tile m starts at slice
-  // m kblocks / mtiles; the exact integer sums do not depend on the order), so
-  // the tiles of one gate stream different B slices at any moment.
-  uint32_t* iinfo = (uint32_t*)(bars + 32);   // [J][4]: gate, row0, rows, rotation
-  if (tid < nj) {
-    const uint64_t it = item0 + tid;
-    const uint32_t m = (uint32_t)(it % t.mtiles), r0 = m * kTileM;
-    iinfo[4 * tid] = (uint32_t)(it / t.mtiles);
-    iinfo[4 * tid + 1] = r0;
-    iinfo[4 * tid + 2] = (a.Ng - r0) < (uint32_t)kTileM ? (a.Ng - r0) : (uint32_t)kTileM;
-    iinfo[4 * tid + 3] = m * t.kblocks / t.mtiles;
-  }
-  auto item_gate = [&](uint32_t j) { return (uint64_t)iinfo[4 * j]; };
-  auto item_row0 = [&](uint32_t j) { return iinfo[4 * j + 1]; };
-  auto item_rows = [&](uint32_t j) { return iinfo[4 * j + 2]; };
-  // slice of K consumed by step st (item st / kblocks)
-  auto step_kb = [&](uint32_t st) {
-    const uint32_t kb = st % t.kblocks + iinfo[4 * (st / t.kblocks) + 3];
-    return kb < t.kblocks ? kb : kb - t.kblocks;
-  };
-  auto item_bx = [&](uint32_t j) {
-    return a.bx + (a.bx_shared ? 0 : item_gate(j)) * t.kblocks * (uint64_t)t.btile;
-  };
+  if (blockIdx.x >= n_items) return;
+  const uint32_t nloc = (uint32_t)((n_items - 1 - blockIdx.x) / gridDim.x + 1);   // items of this CTA
+  const uint32_t steps = nloc * t.kblocks;
+  auto item_of = [&](uint32_t jl) { return (uint64_t)blockIdx.x + (uint64_t)jl * gridDim.x; };
+  // encryption launches generate every A operand (and use neither A nor B linearly)
+  const bool gen = (a.desc[ItemInfo(item_of(0), a, t).gate].a >> 30) == REG_GEN;
 
   if (tid == 0) {
-    for (int b = 0; b < 27; b++) mbar_init(&bars[b], b < 8 ? 5u : 1u);   // full: producer + 4 warps
+    for (int b = 0; b < 8; b++) {
+      mbar_init(&full[b], 5u);   // producer + 4 expander warps
+      mbar_init(&bfree[b], 1u);
+    }
+    for (int b = 0; b < 2; b++) {
+      mbar_init(&tfull[b], 1u);
+      mbar_init(&tfree[b], 4u);
+    }
+    for (uint32_t b = 0; b < kMaxAcc; b++) {
+      mbar_init(&accfull[b], 1u);
+      mbar_init(&accfree[b], kEpiWarps);
+    }
+    mbar_init(drain, 1u);
+    mbar_init(esync, kEpiWarps);
     *sflag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) tmem_alloc(tslot, kTmemCols);
-  __syncthreads();
-  const bool gen = (a.desc[item_gate(0)].a >> 30) == REG_GEN;   // encryption: every item generated
-  if (tid == 0) {
-    uint32_t bytes = 0;
-    for (uint32_t j = 0; j < nj; j++) bytes += item_rows(j) * W * 4u;
-    if (!gen) {
-      mbar_expect_tx(abar, bytes);
-      for (uint32_t j = 0; j < nj; j++) {
-        const uint32_t* A = ct_ptr(a, a.desc[item_gate(j)].a);
-        bulk_g2s(tileA + j * kTileM * W, A + (uint64_t)item_row0(j) * W, item_rows(j) * W * 4u, abar);
-      }
-    }
-    // the epilogue's B' rows (for c2 B) arrive during the main loop
-    mbar_expect_tx(ebar, bytes);
-    for (uint32_t j = 0; j < nj; j++)
-      bulk_g2s(brows + j * kTileM * W, ct_ptr(a, a.desc[item_gate(j)].b) + (uint64_t)item_row0(j) * W,
-               item_rows(j) * W * 4u, ebar);
-    for (uint32_t s = 0; s < t.nstages && s < steps; s++) {
-      mbar_expect_tx(&full[s], t.btile);
-      bulk_g2s(ring + s * t.btile, item_bx(s / t.kblocks) + (uint64_t)step_kb(s) * t.btile,
-               t.btile, &full[s]);
-    }
-  }
-  bool timed_out = false;
-  if (gen) {
-    for (uint32_t e = tid; e < nj * kTileM * W; e += kThreads) {
-      const uint32_t j = e / (kTileM * W), r = (e / W) % kTileM, w = e % W;
-      const uint64_t gst = stream_out(a.gen_state, a.desc[item_gate(j)].a & SLOT_MASK);
-      tileA[e] = r < item_rows(j) ? r_word(gst, (uint64_t)(item_row0(j) + r) * W + w) : 0u;
-    }
-  } else {
-    timed_out = !mbar_wait_bounded(abar, 0);
-    for (uint32_t j = 0; j < nj; j++)   // rows past the last ciphertext row of a partial tile
-      for (uint32_t e = item_rows(j) * W + tid; e < kTileM * W; e += kThreads)
-        tileA[j * kTileM * W + e] = 0;
-  }
-  __syncthreads();
-  // Complement (P - A) row by row with the borrow chain of each element.
-  // Row i of P has one nonzero word: 2^(i % 32) at word (i / ell) L + (i % ell) / 32.
-  for (uint32_t task = tid; task < nj * kTileM; task += kThreads) {
-    const uint32_t j = task / kTileM, r = task % kTileM, i = item_row0(j) + r;
-    if (!(a.aux[item_gate(j)].flags & 1u) || r >= item_rows(j)) continue;
-    uint32_t* row = tileA + (j * kTileM + r) * W;
-    const uint32_t pidx = (i / a.ell) * L + (i % a.ell) / 32, pval = 1u << (i % 32);
-    uint32_t borrow = 0, l = 0;
-    for (uint32_t w = 0; w < W; w++) {
-      if (l == 0) borrow = 0;
-      const uint64_t dv = (uint64_t)(w == pidx ? pval : 0u) - row[w] - borrow;
-      row[w] = (uint32_t)dv;
-      borrow = (uint32_t)(dv >> 63);
-      if (++l == L) l = 0;
-    }
-  }
   tc_fence_before();
-  bool ok = !__syncthreads_or(timed_out);
+  __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
 
-  if (ok) {
-    if (warp == 0) {
-      // ---------------------------------------------------------- MMA issuer
-      const uint32_t idesc0 = idesc_f16(kTileM, t.n0_len), idesc1 = idesc_f16(kTileM, t.n1_len);
-      const uint32_t two = t.n1_len != 0, ring_s = smem_u32(ring);
-      const uint32_t acol = tmem + (kTmemCols - kAColumns);
-      bool issued_all = true;
-      StepPos p;
-      p.start(0, t);
-      for (uint32_t st = 0; st < steps; st++) {
-        if (!__all_sync(0xFFFFFFFFu, mbar_wait_flag(&full[p.slot], p.phase, sflag))) {
-          if (lane == 0) *sflag = 1;
-          issued_all = false;
-          break;
-        }
-        tc_fence_after();
-        const uint32_t b_base = ring_s + p.slot * t.btile;
-        const uint32_t d = tmem + p.j * t.ndpad;
-        mma_slice(d, d + t.n0_len, acol + 32u * (st & (kAStages - 1)), sw128_desc(b_base),
-                  sw128_desc(b_base + t.n0_len * 128u), idesc0, idesc1, p.kb != 0, two, &bfree[p.slot],
-                  done, st + 1 == steps);
-        p.next(t);
+  if (warp == 0) {
+    // ------------------------------------------------------------ MMA issuer
+    const uint32_t idesc0 = idesc_f16(kTileM, t.n0_len), idesc1 = idesc_f16(kTileM, t.n1_len);
+    const uint32_t two = t.n1_len != 0, ring_s = smem_u32(ring);
+    StepPos p;
+    p.start(0, t);
+    uint32_t acc = 0, accph = 0;   // item p.j's slot and the parity of that slot's use
+    bool ok = true;
+    for (uint32_t st = 0; st < steps; st++) {
+      // a slot's next item starts once the epilogue has read the previous one
+      if (p.kb == 0 && p.j >= t.nacc &&
+          !__all_sync(0xFFFFFFFFu, mbar_wait_flag(&accfree[acc], accph ^ 1u, sflag))) {
+        ok = false;
+        break;
       }
-      // after a failed wait, `done` still has to track the MMAs issued so far
-      if (!issued_all) mma_commit_elected(done);
-    } else if (warp == 1) {
-      // ------------------------------------------------------------ producer
-      if (lane == 0 && steps > t.nstages) {
-        StepPos p;
-        p.start(t.nstages, t);
-        uint32_t rot = iinfo[4 * p.j + 3];
-        const uint8_t* bx = item_bx(p.j);
-        for (uint32_t st = t.nstages; st < steps; st++) {
-          // the slot's previous step (st - nstages) ran in the other phase
-          if (!mbar_wait_flag(&bfree[p.slot], p.phase ^ 1u, sflag)) {
-            *sflag = 1;
-            break;
-          }
-          uint32_t kbr = p.kb + rot;
-          if (kbr >= t.kblocks) kbr -= t.kblocks;
-          mbar_expect_tx(&full[p.slot], t.btile);
-          bulk_g2s(ring + p.slot * t.btile, bx + (uint64_t)kbr * t.btile, t.btile, &full[p.slot]);
-          const uint32_t oj = p.j;
-          p.next(t);
-          if (p.j != oj && p.j < nj) {
-            rot = iinfo[4 * p.j + 3];
-            bx = item_bx(p.j);
-          }
-        }
+      if (!__all_sync(0xFFFFFFFFu, mbar_wait_flag(&full[p.slot], p.phase, sflag))) {
+        ok = false;
+        break;
       }
-    } else if (warp >= 4 && warp < 4 + 4 * kExpandGroups) {
-      // ----------------------------------------------------------- expanders
-      const uint32_t grp = (warp - 4) / 4, q = warp & 3, r = q * 32 + lane;
-      const uint32_t acol = tmem + ((q * 32u) << 16) + (kTmemCols - kAColumns);
-      StepPos p;
-      p.start(grp, t);
-      uint32_t rot = p.j < nj ? iinfo[4 * p.j + 3] : 0u;
-      for (uint32_t st = grp; st < steps; st += kExpandGroups) {
-        // lane 0 decides for the whole warp: go on once the MMAs of step
-        // st - kAStages (the stage's last readers) are done; that step used
-        // slot - kAStages, in the previous phase if the slot index wrapped
-        int stop = 0;
-        if (lane == 0 && st >= kAStages) {
-          const bool wrap = p.slot < kAStages;
-          const uint32_t ps = wrap ? p.slot + t.nstages - kAStages : p.slot - kAStages;
-          if (!mbar_wait_flag(&bfree[ps], wrap ? p.phase ^ 1u : p.phase, sflag)) {
-            *sflag = 1;
-            stop = 1;
-          }
-        }
-        if (__shfl_sync(0xFFFFFFFFu, stop, 0)) break;
-        tc_fence_after();
-        uint32_t kb = p.kb + rot;
-        if (kb >= t.kblocks) kb -= t.kblocks;
-        // row r's bits 64 kb .. 64 kb + 63 (words 2 kb, 2 kb + 1; zero past the
-        // row) -> 64 fp16 values, K value k in half k % 2 of column k / 2
-        const uint32_t* row = tileA + (p.j * kTileM + r) * W;
-        const uint32_t w0 = 2u * kb < W ? row[2u * kb] : 0u;
-        const uint32_t w1 = 2u * kb + 1u < W ? row[2u * kb + 1u] : 0u;
-        uint32_t v[32];
-#pragma unroll
-        for (uint32_t b = 0; b < 8; b++) {
-          const uint4 h = byte_to_h8(((b < 4 ? w0 : w1) >> (8u * (b & 3u))) & 0xFFu);
-          v[4 * b] = h.x;
-          v[4 * b + 1] = h.y;
-          v[4 * b + 2] = h.z;
-          v[4 * b + 3] = h.w;
-        }
-        tmem_st32(acol + 32u * (st & (kAStages - 1)), v);
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0)
-          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full[p.slot])) : "memory");
-        const uint32_t oj = p.j;
-        for (uint32_t k = 0; k < kExpandGroups; k++) p.next(t);
-        if (p.j != oj && p.j < nj) rot = iinfo[4 * p.j + 3];
+      tc_fence_after();
+      const uint32_t b_base = ring_s + p.slot * t.btile;
+      const uint32_t d = tmem + acc * t.ndpad;
+      mma_slice(d, d + t.n0_len, tmem + kAColumn0 + 32u * (st & (kAStages - 1)), sw128_desc(b_base),
+                sw128_desc(b_base + t.n0_len * 128u), idesc0, idesc1, p.kb != 0, two, &bfree[p.slot],
+                &accfull[acc], p.kb + 1 == t.kblocks);
+      p.next(t);
+      if (p.kb == 0 && ++acc == t.nacc) {
+        acc = 0;
+        accph ^= 1u;
       }
     }
-  }
-  __syncthreads();
-  if (ok && *sflag) ok = false;
-  if (ok) {
-    // every MMA finished and the B' rows landed
-    const bool w_ok = mbar_wait_bounded(done, 0) && mbar_wait_bounded(ebar, 0);
-    ok = !__syncthreads_or(!w_ok);
-  }
-  if (!ok) {
-    if (tid == 0 && a.err) atomicExch(a.err, KERR_MMA_TIMEOUT);
-    mbar_wait_bounded(done, 0);   // bounded: let own MMAs drain before TMEM is freed
-    mbar_wait_bounded(ebar, 0);   // and the bulk copies into shared memory
-  }
-  tc_fence_after();
+    if (!ok && lane == 0) *sflag = 1;
+    mma_commit_elected(drain);   // tracks every MMA issued
 
-  // Epilogue. Phase 1 (all warps): warp w reads TMEM lanes 32 (w % 4) .. +31
-  // (its rows) over the digit columns of the row's words [w/4 W/4, (w/4+1) W/4);
-  // digit d of element e adds S << (dw d mod 32) to word (dw d) / 32 of the
-  // element (every word gets at least two digits, in column order) and the
-  // int64 word sums go to Kv (row stride KS = W | 1 words of 8 bytes, odd, so
-  // a warp's rows fall in distinct bank pairs). Phase 2: one thread per (row,
-  // element) runs the element's carry chain with the linear terms; output
-  // tile 0 overwrites the item's A~ rows and tile 1 its B' rows in place.
-  int64_t* Kv = (int64_t*)ring;
-  const uint32_t KS = W | 1u;
-  for (uint32_t j = 0; ok && j < nj; j++) {
-    const uint64_t g = item_gate(j);
-    const uint32_t row0 = item_row0(j), rows = item_rows(j);
-    const GateDesc gd = a.desc[g];
-    const GateAux x = a.aux[g];
-    uint32_t* At = tileA + j * kTileM * W;               // A~ rows, then output tile 0
-    uint32_t* Bt = brows + j * kTileM * W;               // B' rows, then output tile 1
-    {
-      const uint32_t q = warp & 3, cg = warp >> 2, r = q * 32 + lane;
-      const uint32_t gw0 = cg * W / 4, gw1 = (cg + 1) * W / 4;
-      // first digit column of global word gw (element gw / L, local word gw % L)
-      auto first_col = [&](uint32_t gw) {
-        const uint32_t e = gw / L, wl = gw - e * L;
-        return e * t.dpad + (32u * wl + t.dw - 1) / t.dw;
+  } else if (warp == 1) {
+    // -------------------------------------------------------------- producer
+    if (lane == 0) {
+      // A tile of item jl into buffer jl % 2, once the expanders left item jl - 2
+      auto load_tile = [&](uint32_t jl) -> bool {
+        if (gen) return true;
+        const ItemInfo it(item_of(jl), a, t);
+        const uint32_t buf = jl & 1u;
+        if (jl >= 2 && !mbar_wait_flag(&tfree[buf], ((jl - 2) >> 1) & 1u, sflag)) return false;
+        mbar_expect_tx(&tfull[buf], it.rows * W * 4u);
+        bulk_g2s(tiles + buf * kTileM * W, ct_ptr(a, a.desc[it.gate].a) + (uint64_t)it.row0 * W,
+                 it.rows * W * 4u, &tfull[buf]);
+        return true;
       };
-      if (gw0 < gw1) {
-        const uint32_t n0 = first_col(gw0), n1 = first_col(gw1);
-        const uint32_t taddr = tmem + ((q * 32u) << 16) + j * t.ndpad;
-        int64_t acc = 0;
-        uint32_t cur = gw0;
-        for (uint32_t c0 = n0 & ~15u; c0 < n1; c0 += 16) {
-          uint32_t v[16];
-          tmem_ld16(taddr + c0, v);
-          const uint32_t e = c0 / t.dpad, dbase = c0 - e * t.dpad;   // a chunk lies in one element
-#pragma unroll
-          for (uint32_t k = 0; k < 16; k++) {
-            const uint32_t n = c0 + k, d = dbase + k;
-            if (n >= n0 && n < n1 && d < t.D) {
-              const uint32_t bit = d * t.dw, gw = e * L + (bit >> 5);
-              if (gw != cur) {
-                Kv[r * KS + cur] = acc;
-                acc = 0;
-                cur = gw;
-              }
-              acc += (int64_t)__float2int_rn(__uint_as_float(v[k])) << (bit & 31u);
+      bool ok = load_tile(0) && (nloc < 2 || load_tile(1));
+      StepPos p;
+      p.start(0, t);
+      ItemInfo it(item_of(0), a, t);
+      const uint8_t* bx = a.bx + (a.bx_shared ? 0 : (uint64_t)it.gate) * t.kblocks * (uint64_t)t.btile;
+      for (uint32_t st = 0; ok && st < steps; st++) {
+        // the next item's tile, halfway through this one
+        if (p.kb == t.kblocks / 2 && p.j >= 1 && p.j + 1 < nloc && !load_tile(p.j + 1)) {
+          ok = false;
+          break;
+        }
+        // the slot's previous step (st - nstages) ran in the other phase
+        if (st >= t.nstages && !mbar_wait_flag(&bfree[p.slot], p.phase ^ 1u, sflag)) {
+          ok = false;
+          break;
+        }
+        uint32_t kbr = p.kb + it.rot;
+        if (kbr >= t.kblocks) kbr -= t.kblocks;
+        mbar_expect_tx(&full[p.slot], t.btile);
+        bulk_g2s(ring + p.slot * t.btile, bx + (uint64_t)kbr * t.btile, t.btile, &full[p.slot]);
+        const uint32_t oj = p.j;
+        p.next(t);
+        if (p.j != oj && p.j < nloc) {
+          it = ItemInfo(item_of(p.j), a, t);
+          bx = a.bx + (a.bx_shared ? 0 : (uint64_t)it.gate) * t.kblocks * (uint64_t)t.btile;
+        }
+      }
+      if (!ok) *sflag = 1;
+    }
+  } else if (warp >= kExpandWarp0 && warp < kEpiWarp0) {
+    // ------------------------------------------------------------- expanders
+    const uint32_t q = warp & 3, r = q * 32 + lane;
+    const uint32_t arow = tmem + ((q * 32u) << 16) + kAColumn0;
+    StepPos p;
+    p.start(0, t);
+    uint32_t jcur = 0xFFFFFFFFu, rot = 0;
+    const uint32_t* row = nullptr;
+    bool ok = true;
+    for (uint32_t st = 0; st < steps; st++) {
+      if (p.j != jcur) {
+        if (jcur != 0xFFFFFFFFu) {   // done with the previous item's tile
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&tfree[jcur & 1u]);
+        }
+        jcur = p.j;
+        const ItemInfo it(item_of(jcur), a, t);
+        rot = it.rot;
+        uint32_t* trow = tiles + ((jcur & 1u) * kTileM + r) * W;
+        if (gen) {
+          const uint64_t gst = stream_out(a.gen_state, a.desc[it.gate].a & SLOT_MASK);
+          for (uint32_t w = 0; w < W; w++)
+            trow[w] = r < it.rows ? r_word(gst, (uint64_t)(it.row0 + r) * W + w) : 0u;
+        } else {
+          if (!__all_sync(0xFFFFFFFFu, mbar_wait_flag(&tfull[jcur & 1u], (jcur >> 1) & 1u, sflag))) {
+            ok = false;
+            break;
+          }
+          // P - A for a complemented operand: row i of P has one nonzero word,
+          // 2^(i % 32) at word (i / ell) L + (i % ell) / 32; borrows stay
+          // inside each element
+          if ((a.aux[it.gate].flags & 1u) && r < it.rows) {
+            const uint32_t i = it.row0 + r;
+            const uint32_t pidx = (i / a.ell) * L + (i % a.ell) / 32, pval = 1u << (i % 32);
+            uint32_t borrow = 0, l = 0;
+            for (uint32_t w = 0; w < W; w++) {
+              if (l == 0) borrow = 0;
+              const uint64_t dv = (uint64_t)(w == pidx ? pval : 0u) - trow[w] - borrow;
+              trow[w] = (uint32_t)dv;
+              borrow = (uint32_t)(dv >> 63);
+              if (++l == L) l = 0;
             }
           }
         }
-        Kv[r * KS + cur] = acc;   // word gw1 - 1
+        row = trow;
       }
+      // the MMAs of step st - kAStages (the stage's last readers) are done;
+      // that step used slot - kAStages, in the previous phase if the index wrapped
+      if (st >= kAStages) {
+        const bool wrap = p.slot < kAStages;
+        const uint32_t ps = wrap ? p.slot + t.nstages - kAStages : p.slot - kAStages;
+        if (!__all_sync(0xFFFFFFFFu, mbar_wait_flag(&bfree[ps], wrap ? p.phase ^ 1u : p.phase, sflag))) {
+          ok = false;
+          break;
+        }
+      }
+      tc_fence_after();
+      uint32_t kb = p.kb + rot;
+      if (kb >= t.kblocks) kb -= t.kblocks;
+      // bits 64 kb .. 64 kb + 63 of the row (words 2 kb, 2 kb + 1; zero past
+      // it) -> 64 fp16 values, K value k in half k % 2 of column k / 2
+      const uint32_t w0 = 2u * kb < W ? row[2u * kb] : 0u;
+      const uint32_t w1 = 2u * kb + 1u < W ? row[2u * kb + 1u] : 0u;
+      uint32_t v[32];
+#pragma unroll
+      for (uint32_t b = 0; b < 8; b++) {
+        const uint4 h = byte_to_h8(((b < 4 ? w0 : w1) >> (8u * (b & 3u))) & 0xFFu);
+        v[4 * b] = h.x;
+        v[4 * b + 1] = h.y;
+        v[4 * b + 2] = h.z;
+        v[4 * b + 3] = h.w;
+      }
+      tmem_st32(arow + 32u * (st & (kAStages - 1)), v);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&full[p.slot]);
+      p.next(t);
     }
-    __syncthreads();
-    {
-      const uint32_t code0 = x.code & 0xFFFFu, code1 = x.code >> 16;
-      int c00 = nib(code0, 0), c01 = nib(code0, 1), c02 = nib(code0, 2), c03 = nib(code0, 3);
-      int c10 = nib(code1, 0), c11 = nib(code1, 1), c12 = nib(code1, 2), c13 = nib(code1, 3);
-      if (x.flags & 1u) {  // the stored A is P - A~: c1 A = c1 P - c1 A~
-        c00 += c01;
-        c01 = -c01;
-        c10 += c11;
-        c11 = -c11;
+    if (!ok && lane == 0) *sflag = 1;
+  } else if (warp >= kEpiWarp0) {
+    // -------------------------------------------------------------- epilogue
+    // Pass A: a unit is (element e, digit group g) of an item: 32 digit
+    // columns. Warp w takes the units (w - 8) / 4, + 2, ... for the 32 rows of
+    // its lane quarter (w % 4). Digit k of the group adds S << (11k mod 32) to
+    // word (11k) / 32 of the group's 11 words (constant shifts); those words go
+    // through both output carry chains with the linear terms, carry-in 0, and
+    // straight to the output rows; the carries out of the group go to `carr`
+    // unless it is the element's last group. Pass B: one thread per (row,
+    // element) adds each group's carry into the next group's words.
+    const uint32_t q = warp & 3, cs = (warp - kEpiWarp0) >> 2, r = q * 32 + lane;
+    const uint32_t etid = tid - kEpiWarp0 * 32;
+    uint32_t acc = 0, accph = 0, eph = 0;
+    bool ok = true;
+    for (uint32_t jl = 0; ok && jl < nloc; jl++) {
+      const ItemInfo it(item_of(jl), a, t);
+      const GateDesc gd = a.desc[it.gate];
+      const uint32_t code = a.aux[it.gate].code;
+      const int c00 = nib(code, 0), c01 = nib(code, 1), c02 = nib(code, 2), c03 = nib(code, 3);
+      const int c10 = nib(code, 4), c11 = nib(code, 5), c12 = nib(code, 6), c13 = nib(code, 7);
+      const uint32_t i = it.row0 + r;
+      const uint32_t pe = i / a.ell, pw_at = (i % a.ell) / 32;
+      const int64_t pval = (int64_t)1 << (i % 32);
+      const int64_t p0 = c00 * pval, p1 = c10 * pval;   // the P term of both outputs
+      // a term c x (c small, x < 2^32) is c (x - 2^31) + c 2^31: one signed
+      // 32 x 32 -> 64 multiply-add, the constants summed once per output
+      const int64_t bias0 = (int64_t)(c01 + c02 + c03) << 31, bias1 = (int64_t)(c11 + c12 + c13) << 31;
+      const bool Ag = (c01 | c11) != 0, Bg = (c02 | c12) != 0;   // linear terms read A, B
+      uint32_t* O0 = gd.o0 != REF_NONE ? a.base[gd.o0 >> 30] + (uint64_t)(gd.o0 & SLOT_MASK) * a.ctw : nullptr;
+      uint32_t* O1 = gd.o1 != REF_NONE ? a.base[gd.o1 >> 30] + (uint64_t)(gd.o1 & SLOT_MASK) * a.ctw : nullptr;
+      if (!__all_sync(0xFFFFFFFFu, mbar_wait_flag(&accfull[acc], accph, sflag))) {
+        ok = false;
+        break;
       }
-      for (uint32_t task = tid; task < kTileM * NP1; task += kThreads) {
-        const uint32_t r = task % kTileM, e = task / kTileM, i = row0 + r;
-        if (r >= rows) continue;
-        // row i of P: 2^(i % 32) at word (i / ell) L + (i % ell) / 32
-        const uint32_t pw_at = (i / a.ell) * L + (i % a.ell) / 32;
-        const int64_t pval = (int64_t)1 << (i % 32);
-        uint32_t* Ar = At + r * W;
-        uint32_t* Br = Bt + r * W;
-        const int64_t* Kr = Kv + r * KS;
-        int64_t carry0 = 0, carry1 = 0;
-        for (uint32_t w = e * L; w < (e + 1) * L; w++) {
-          const int64_t k = Kr[w], aw = Ar[w], bw = Br[w], pw = w == pw_at ? pval : 0;
-          const int64_t o0 = c03 * k + c01 * aw + c02 * bw + c00 * pw + carry0;
-          const int64_t o1 = c13 * k + c11 * aw + c12 * bw + c10 * pw + carry1;
-          carry0 = o0 >> 32;
-          carry1 = o1 >> 32;
-          Ar[w] = (uint32_t)o0;
-          Br[w] = (uint32_t)o1;
+      tc_fence_after();
+      const uint32_t taddr0 = tmem + ((q * 32u) << 16) + acc * t.ndpad;
+      // this warp's staging: rows 32 q .. 32 q + 31 of the item, 11 words each
+      uint32_t* sa = ebuf + (warp - kEpiWarp0) * kEbufWords;
+      uint32_t* sb = sa + 32 * kGroupWords;
+      const uint64_t wrow0 = (uint64_t)(it.row0 + q * 32) * W;   // first row of the block
+      for (uint32_t u = cs; u < NP1 * G; u += kEpiWarps / 4) {
+        const uint32_t e = u / G, g = u - e * G;
+        const uint32_t wb = g * kGroupWords;   // first local word of the group
+        const uint32_t eo = e * L + wb;        // its word offset in a row
+        // block element x = 32 k + lane: row x / 11, word x % 11 (a row's 11
+        // words are contiguous, so a warp's copy touches a few segments)
+#pragma unroll
+        for (uint32_t k = 0; k < kGroupWords; k++) {
+          const uint32_t x = 32 * k + lane, br = x / kGroupWords, bw = x - br * kGroupWords;
+          const bool in = q * 32 + br < it.rows && wb + bw < L;
+          const uint64_t off = wrow0 + (uint64_t)br * W + eo + bw;
+          if (Ag && in) cp_async4(sa + x, ct_ptr(a, gd.a) + off); else sa[x] = 0u;
+          if (Bg && in) cp_async4(sb + x, ct_ptr(a, gd.b) + off); else sb[x] = 0u;
+        }
+        uint32_t v[32];
+        const uint32_t taddr = taddr0 + e * t.dpad + g * kGroupDigits;
+        tmem_ld16(taddr, *reinterpret_cast<uint32_t(*)[16]>(&v[0]));
+        if (g * kGroupDigits + 16 < t.dpad) {
+          tmem_ld16(taddr + 16, *reinterpret_cast<uint32_t(*)[16]>(&v[16]));
+        } else {
+#pragma unroll
+          for (int k = 16; k < 32; k++) v[k] = 0;
+        }
+        int64_t kw[kGroupWords];
+#pragma unroll
+        for (int k = 0; k < (int)kGroupWords; k++) kw[k] = 0;
+#pragma unroll
+        for (int k = 0; k < (int)kGroupDigits; k++)
+          kw[(k * (int)kDigitBits) >> 5] += (int64_t)__float2int_rn(__uint_as_float(v[k]))
+                                            << ((k * (int)kDigitBits) & 31);
+        cp_async_wait_all();
+        __syncwarp();
+        // own row: words at lane * 11 (odd stride: no bank conflicts)
+        // word k of the group: t = carry + c3 K + c1 A + c2 B (+ c0 P); the low
+        // half is the output word; the carry into the next word is the high
+        // half plus c3 times K's high half (K = 2^32 khi + klo, khi < 2^24)
+        const uint32_t kp = e == pe ? pw_at - wb : 0xFFFFFFFFu;   // group word holding P's bit
+        int32_t carry0 = 0, carry1 = 0;
+#pragma unroll
+        for (uint32_t k = 0; k < kGroupWords; k++) {
+          const int32_t xa = (int32_t)(sa[lane * kGroupWords + k] ^ 0x80000000u);
+          const int32_t xb = (int32_t)(sb[lane * kGroupWords + k] ^ 0x80000000u);
+          const int32_t xk = (int32_t)((uint32_t)kw[k] ^ 0x80000000u);
+          const int32_t khi = (int32_t)(kw[k] >> 32);
+          int64_t t0 = bias0 + carry0, t1 = bias1 + carry1;
+          t0 += (int64_t)c01 * xa;
+          t0 += (int64_t)c02 * xb;
+          t0 += (int64_t)c03 * xk;
+          t1 += (int64_t)c11 * xa;
+          t1 += (int64_t)c12 * xb;
+          t1 += (int64_t)c13 * xk;
+          if (k == kp) {
+            t0 += p0;
+            t1 += p1;
+          }
+          carry0 = (int32_t)(t0 >> 32) + c03 * khi;
+          carry1 = (int32_t)(t1 >> 32) + c13 * khi;
+          sa[lane * kGroupWords + k] = (uint32_t)t0;
+          sb[lane * kGroupWords + k] = (uint32_t)t1;
+        }
+        if (g + 1 < G) {
+          int64_t* cp = carr + (((uint64_t)r * NP1 + e) * (G - 1) + g) * 2;
+          cp[0] = carry0;
+          cp[1] = carry1;
+        }
+        __syncwarp();
+#pragma unroll
+        for (uint32_t k = 0; k < kGroupWords; k++) {
+          const uint32_t x = 32 * k + lane, br = x / kGroupWords, bw = x - br * kGroupWords;
+          if (q * 32 + br < it.rows && wb + bw < L) {
+            const uint64_t off = wrow0 + (uint64_t)br * W + eo + bw;
+            if (O0) O0[off] = sa[x];
+            if (O1) O1[off] = sb[x];
+          }
+        }
+        __syncwarp();   // the staging is refilled by the next unit
+      }
+      // this warp's reads of the accumulator are complete (tmem_ld16 waits)
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&accfree[acc]);
+      if (++acc == t.nacc) {
+        acc = 0;
+        accph ^= 1u;
+      }
+      // carries and output words of pass A are visible
+      if (!epi_sync(esync, eph, sflag)) {
+        ok = false;
+        break;
+      }
+      if (G > 1) {
+        for (uint32_t task = etid; task < kTileM * NP1; task += kEpiWarps * 32) {
+          const uint32_t rr = task / NP1, e = task - rr * NP1;
+          if (rr >= it.rows) continue;
+          const uint64_t roff = (uint64_t)(it.row0 + rr) * W + e * L;
+          uint32_t* P0 = O0 ? O0 + roff : nullptr;
+          uint32_t* P1 = O1 ? O1 + roff : nullptr;
+          const int64_t* cp = carr + ((uint64_t)rr * NP1 + e) * (G - 1) * 2;
+          int64_t in0 = 0, in1 = 0;
+          for (uint32_t g = 1; g < G; g++) {
+            in0 += cp[2 * (g - 1)];
+            in1 += cp[2 * (g - 1) + 1];
+            const uint32_t wend = (g + 1) * kGroupWords < L ? (g + 1) * kGroupWords : L;
+            for (uint32_t w = g * kGroupWords; P0 && w < wend && in0 != 0; w++) {
+              const int64_t o = (int64_t)P0[w] + in0;
+              P0[w] = (uint32_t)o;
+              in0 = o >> 32;
+            }
+            for (uint32_t w = g * kGroupWords; P1 && w < wend && in1 != 0; w++) {
+              const int64_t o = (int64_t)P1[w] + in1;
+              P1[w] = (uint32_t)o;
+              in1 = o >> 32;
+            }
+          }
+        }
+        // carr is rewritten by the next item
+        if (!epi_sync(esync, eph, sflag)) {
+          ok = false;
+          break;
         }
       }
     }
-    fence_proxy_async_smem();
-    __syncthreads();   // also: Kv is rewritten by the next item's phase 1
-    if (tid == 0) {
-      if (gd.o0 != REF_NONE)
-        bulk_s2g(a.base[gd.o0 >> 30] + (uint64_t)(gd.o0 & SLOT_MASK) * a.ctw + (uint64_t)row0 * W, At,
-                 rows * W * 4u);
-      if (gd.o1 != REF_NONE)
-        bulk_s2g(a.base[gd.o1 >> 30] + (uint64_t)(gd.o1 & SLOT_MASK) * a.ctw + (uint64_t)row0 * W, Bt,
-                 rows * W * 4u);
-      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-    }
+    if (!ok && lane == 0) *sflag = 1;
   }
-  // the output tiles stay untouched until the CTA ends: one wait for every store
-  if (tid == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+
+  __syncthreads();
+  if (*sflag) {
+    if (tid == 0 && a.err) atomicExch(a.err, KERR_MMA_TIMEOUT);
+    if (warp == 0) mbar_wait_bounded(drain, 0);   // let own MMAs drain before TMEM is freed
+  }
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
@@ -715,46 +808,50 @@ __global__ void __launch_bounds__(kThreads, 1) k_gate_tc(KArgs a, TcShape t) {
 
 namespace {
 
-uint32_t tc_smem_bytes(uint32_t W, uint32_t btile, uint32_t ns, uint32_t J) {
-  return 1024u + ns * btile + 2u * J * (uint32_t)kTileM * W * 4u + 256u + 16u * J;
+uint32_t tc_smem_bytes(uint32_t W, uint32_t btile, uint32_t ns, uint32_t carry_bytes) {
+  return 1024u + ns * btile + 2u * (uint32_t)kTileM * W * 4u + carry_bytes + kEpiWarps * kEbufWords * 4u +
+         kBars * 8u;
 }
 
-// Shape of the kernel for up to `jmax` items per CTA (0 = the largest that fits).
-bool make_tc_shape(const KArgs& a, TcShape* t, uint32_t jmax = 1) {
+bool make_tc_shape(const KArgs& a, TcShape* t) {
   if (a.Ng < 128 || a.W == 0 || a.L == 0 || a.ell != 32 * a.L) return false;
   const uint32_t NP1 = a.W / a.L;
   // digit width: exact fp16 operand and every column sum below 2^24
-  t->dw = kMaxDigitBits;
-  while (t->dw > 1 && (uint64_t)a.Ng * ((1u << t->dw) - 1u) >= (1u << 24)) t->dw--;
+  t->dw = kDigitBits;
+  if ((uint64_t)a.Ng * ((1u << kDigitBits) - 1u) >= (1u << 24)) return false;
   t->D = (a.ell + t->dw - 1) / t->dw;
   t->dpad = (t->D + 15) / 16 * 16;
   t->ndpad = NP1 * t->dpad;
-  if (t->ndpad > 512) return false;
+  if (t->ndpad + kAColumns > kTmemCols) return false;
+  t->nacc = std::min(kMaxAcc, (kTmemCols - kAColumns) / t->ndpad);
   // one MMA up to N = 256, else two balanced chunks (multiples of 16)
   t->n0_len = t->ndpad <= 256 ? t->ndpad : (t->ndpad / 2 + 15) / 16 * 16;
   t->n1_len = t->ndpad - t->n0_len;
   t->mtiles = (a.Ng + kTileM - 1) / kTileM;
   t->kblocks = (a.Ng + kBK - 1) / kBK;
   t->btile = t->ndpad * 128u;
+  t->G = (t->dpad + kGroupDigits - 1) / kGroupDigits;
+  const uint32_t carry_bytes = (uint32_t)kTileM * NP1 * (t->G - 1) * 16u;
   t->nstages = 0;
   for (uint32_t ns = 8; ns >= kAStages; ns--)
-    if (tc_smem_bytes(a.W, t->btile, ns, 1) <= kMaxSmem) {
+    if (tc_smem_bytes(a.W, t->btile, ns, carry_bytes) <= kMaxSmem) {
       t->nstages = ns;
       break;
     }
-  // the epilogue keeps the int64 word sums (128 rows of W | 1) in the ring
-  if (!t->nstages || t->nstages * t->btile < 1024u * (a.W | 1u)) return false;
-  // items per CTA: TMEM columns, stage A room for the epilogue's B rows, smem
-  uint32_t J = 1;
-  const uint32_t cap = jmax ? jmax : 64;
-  if (t->ndpad + kAColumns > kTmemCols) return false;
-  while (J < cap && (J + 1) * t->ndpad + kAColumns <= kTmemCols &&
-         tc_smem_bytes(a.W, t->btile, t->nstages, J + 1) <= kMaxSmem)
-    J++;
-  t->items = J;
-  t->tmem_cols = kTmemCols;
-  t->smem_bytes = tc_smem_bytes(a.W, t->btile, t->nstages, J);
+  if (!t->nstages) return false;
+  t->smem_bytes = tc_smem_bytes(a.W, t->btile, t->nstages, carry_bytes);
   return true;
+}
+
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+      n = 148;
+  }
+  return n;
 }
 
 }  // namespace
@@ -795,8 +892,8 @@ uint64_t tc_bx_bytes(const KArgs& a, uint64_t gates) {
 
 int launch_gates_tc(const KArgs& a, cudaStream_t st) {
   if (a.n == 0) return SFFT_OK;
-  TcShape t0{};
-  if (!make_tc_shape(a, &t0, 0)) return fail(SFFT_EPARAM, "tensor-core kernel does not support this shape");
+  TcShape t{};
+  if (!make_tc_shape(a, &t)) return fail(SFFT_EPARAM, "tensor-core kernel does not support this shape");
   if (!a.bx) return fail(SFFT_EINVAL, "tensor-core kernel needs its B expansion buffer");
   static bool configured = false;
   if (!configured) {
@@ -815,15 +912,12 @@ int launch_gates_tc(const KArgs& a, cudaStream_t st) {
     ca.n = (a.n - c0) < chunk ? (a.n - c0) : chunk;
     KArgs ea = ca;
     ea.n = a.bx_shared ? 1 : ca.n;
-    k_expand_b<<<(unsigned)(ea.n * t0.kblocks), kExpandThreads, kBK * a.W * 4u, st>>>(ea, t0);
+    k_expand_b<<<(unsigned)(ea.n * t.kblocks), kExpandThreads, kBK * a.W * 4u, st>>>(ea, t);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "B expansion launch");
-    // items per CTA: as many as fit, but keep at least two CTAs per SM's worth of work
-    const uint64_t items = ca.n * t0.mtiles;
-    const uint64_t want = std::max<uint64_t>(1, items / (2 * 152));
-    TcShape t{};
-    make_tc_shape(a, &t, (uint32_t)std::min<uint64_t>(want, t0.items));
-    const uint64_t blocks = (items + t.items - 1) / t.items;
+    // persistent: one CTA per SM (or per item, if fewer)
+    const uint64_t items = ca.n * t.mtiles;
+    const uint64_t blocks = std::min<uint64_t>(items, (uint64_t)sm_count());
     k_gate_tc<<<(unsigned)blocks, kThreads, t.smem_bytes, st>>>(ca, t);
     count_launches(2);
     e = cudaGetLastError();

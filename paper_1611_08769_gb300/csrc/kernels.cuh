@@ -20,8 +20,12 @@
 namespace sfft {
 
 
+// The region base is selected with constant indices: indexing the parameter
+// array with a runtime value would copy the kernel arguments to local memory.
 __device__ __forceinline__ uint32_t* resolve(const KArgs& a, uint32_t ref) {
-  return a.base[ref >> 30] + (uint64_t)(ref & SLOT_MASK) * a.ctw;
+  const uint32_t r = ref >> 30;
+  uint32_t* base = r == 0 ? a.base[0] : r == 1 ? a.base[1] : r == 2 ? a.base[2] : a.base[3];
+  return base + (uint64_t)(ref & SLOT_MASK) * a.ctw;
 }
 
 // Limb `l` of element `j` of row `i` of the gadget matrix P.

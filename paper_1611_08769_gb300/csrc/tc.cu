@@ -49,7 +49,7 @@ namespace {
 
 constexpr int kThreads = 512;
 constexpr int kTileM = 128;
-constexpr int kBK = 64;                        // K elements per slice (128 bytes of fp16)
+constexpr int kBK = 128;                       // K elements per step: two 64-wide swizzle atoms
 constexpr uint32_t kSpinLimit = 1u << 26;
 constexpr uint64_t kWaitNs = 2000000000ull;    // bound of any single mbarrier wait
 constexpr uint32_t kMaxSmem = 232448;          // 227 KB opt-in per CTA
@@ -150,41 +150,56 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
   asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
 
-// One 64-wide K slice of one item, issued by one elected lane of the calling
+// One 128-wide K step of one item, issued by one elected lane of the calling
 // warp (every lane executes the statement; the MMAs and the commits that
 // track them sit under the same elect.sync predicate, so one thread issues
 // all of them):
-//   D[d0] (+)= A * B0^T over four K=16 steps, the same into D[d1] with B1 when
-//   `two` is set; then commit -> fb, and -> fd if `last` (one commit per slice:
-//   a second one per slice costs the tensor pipe measurably).
+//   D[d0] (+)= A * B0^T over eight K=16 steps, the same into D[d1] with B1
+//   (= B0 + boff1 descriptor units) when `two` is set; then commit -> fb, and
+//   -> fd if `last` (one commit per step: a second one costs the tensor pipe
+//   measurably).
 // A sits in tensor memory at column `at` (row i in lane i, two fp16 K values
-// per 32-bit column: a K=16 step is 8 columns); B0, B1 are 128B-swizzled
-// K-major shared-memory tiles (a descriptor advances 32 bytes = 2 units per
-// step). `acc` = 0 starts the accumulator (first slice of the item).
-__device__ __forceinline__ void mma_slice(uint32_t d0, uint32_t d1, uint32_t at, uint64_t b0,
-                                          uint64_t b1, uint32_t id0, uint32_t id1, uint32_t acc,
-                                          uint32_t two, uint64_t* fb, uint64_t* fd, uint32_t last) {
+// per 32-bit column: a K=16 step is 8 columns). B is two 128B-swizzled
+// K-major shared-memory atoms of 64 K values, the second `aoff` descriptor
+// units (16 bytes each) after the first; within an atom a K=16 step advances
+// 32 bytes = 2 units. `acc` = 0 starts the accumulator (first step of an item).
+__device__ __forceinline__ void mma_step(uint32_t d0, uint32_t d1, uint32_t at, uint64_t b0, uint32_t aoff,
+                                         uint32_t boff1, uint32_t id0, uint32_t id1, uint32_t acc,
+                                         uint32_t two, uint64_t* fb, uint64_t* fd, uint32_t last) {
   asm volatile(
-      "{\n .reg .pred e, e2, e3, p, t;\n .reg .b32 a1, a2, a3;\n .reg .b64 x1, x2, x3, y1, y2, y3;\n"
+      "{\n .reg .pred e, e2, e3, p, t;\n .reg .b32 a1, a2, a3, a4, a5, a6, a7;\n"
+      " .reg .b64 o, o1, x0, x1, x2, x3, x4, x5, x6, x7, y0, y1, y2, y3, y4, y5, y6, y7;\n"
       " elect.sync _|e, 0xffffffff;\n"
       " setp.ne.b32 p, %8, 0;\n"
       " setp.eq.b32 t, %8, %8;\n"
       " setp.ne.and.b32 e2, %9, 0, e;\n"
       " setp.ne.and.b32 e3, %12, 0, e;\n"
-      " add.u32 a1, %3, 8;\n add.u32 a2, %3, 16;\n add.u32 a3, %3, 24;\n"
-      " add.u64 x1, %4, 2;\n add.u64 x2, %4, 4;\n add.u64 x3, %4, 6;\n"
-      " add.u64 y1, %5, 2;\n add.u64 y2, %5, 4;\n add.u64 y3, %5, 6;\n"
-      " @e tcgen05.mma.cta_group::1.kind::f16 [%1], [%3], %4, %6, p;\n"
-      " @e tcgen05.mma.cta_group::1.kind::f16 [%1], [a1], x1, %6, t;\n"
-      " @e tcgen05.mma.cta_group::1.kind::f16 [%1], [a2], x2, %6, t;\n"
-      " @e tcgen05.mma.cta_group::1.kind::f16 [%1], [a3], x3, %6, t;\n"
-      " @e2 tcgen05.mma.cta_group::1.kind::f16 [%2], [%3], %5, %7, p;\n"
-      " @e2 tcgen05.mma.cta_group::1.kind::f16 [%2], [a1], y1, %7, t;\n"
-      " @e2 tcgen05.mma.cta_group::1.kind::f16 [%2], [a2], y2, %7, t;\n"
-      " @e2 tcgen05.mma.cta_group::1.kind::f16 [%2], [a3], y3, %7, t;\n"
+      " add.u32 a1, %2, 8;\n add.u32 a2, %2, 16;\n add.u32 a3, %2, 24;\n add.u32 a4, %2, 32;\n"
+      " add.u32 a5, %2, 40;\n add.u32 a6, %2, 48;\n add.u32 a7, %2, 56;\n"
+      " cvt.u64.u32 o, %4;\n cvt.u64.u32 o1, %5;\n"
+      " mov.b64 x0, %3;\n add.u64 x1, x0, 2;\n add.u64 x2, x0, 4;\n add.u64 x3, x0, 6;\n"
+      " add.u64 x4, x0, o;\n add.u64 x5, x4, 2;\n add.u64 x6, x4, 4;\n add.u64 x7, x4, 6;\n"
+      " add.u64 y0, x0, o1;\n add.u64 y1, x1, o1;\n add.u64 y2, x2, o1;\n add.u64 y3, x3, o1;\n"
+      " add.u64 y4, x4, o1;\n add.u64 y5, x5, o1;\n add.u64 y6, x6, o1;\n add.u64 y7, x7, o1;\n"
+      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], [%2], x0, %6, p;\n"
+      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], [a1], x1, %6, t;\n"
+      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], [a2], x2, %6, t;\n"
+      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], [a3], x3, %6, t;\n"
+      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], [a4], x4, %6, t;\n"
+      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], [a5], x5, %6, t;\n"
+      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], [a6], x6, %6, t;\n"
+      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], [a7], x7, %6, t;\n"
+      " @e2 tcgen05.mma.cta_group::1.kind::f16 [%1], [%2], y0, %7, p;\n"
+      " @e2 tcgen05.mma.cta_group::1.kind::f16 [%1], [a1], y1, %7, t;\n"
+      " @e2 tcgen05.mma.cta_group::1.kind::f16 [%1], [a2], y2, %7, t;\n"
+      " @e2 tcgen05.mma.cta_group::1.kind::f16 [%1], [a3], y3, %7, t;\n"
+      " @e2 tcgen05.mma.cta_group::1.kind::f16 [%1], [a4], y4, %7, t;\n"
+      " @e2 tcgen05.mma.cta_group::1.kind::f16 [%1], [a5], y5, %7, t;\n"
+      " @e2 tcgen05.mma.cta_group::1.kind::f16 [%1], [a6], y6, %7, t;\n"
+      " @e2 tcgen05.mma.cta_group::1.kind::f16 [%1], [a7], y7, %7, t;\n"
       " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%10];\n"
-      " @e3 tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%11];\n}\n" ::"r"(0u),
-      "r"(d0), "r"(d1), "r"(at), "l"(b0), "l"(b1), "r"(id0), "r"(id1), "r"(acc), "r"(two),
+      " @e3 tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%11];\n}\n" ::"r"(d0),
+      "r"(d1), "r"(at), "l"(b0), "r"(aoff), "r"(boff1), "r"(id0), "r"(id1), "r"(acc), "r"(two),
       "r"(smem_u32(fb)), "r"(smem_u32(fd)), "r"(last)
       : "memory");
 }
@@ -258,8 +273,15 @@ __device__ __forceinline__ uint4 byte_to_h8(uint32_t x) {
   return v;
 }
 
-__device__ __forceinline__ const uint32_t* ct_ptr(const KArgs& a, uint32_t ref) {
-  return a.base[ref >> 30] + (uint64_t)(ref & SLOT_MASK) * a.ctw;
+// Region base of a reference, selected with constant indices: indexing the
+// parameter array with a runtime value would copy the kernel arguments to
+// local memory.
+__device__ __forceinline__ uint32_t* region_base(const KArgs& a, uint32_t region) {
+  return region == 0 ? a.base[0] : region == 1 ? a.base[1] : region == 2 ? a.base[2] : a.base[3];
+}
+
+__device__ __forceinline__ uint32_t* ct_ptr(const KArgs& a, uint32_t ref) {
+  return region_base(a, ref >> 30) + (uint64_t)(ref & SLOT_MASK) * a.ctw;
 }
 
 }  // namespace
@@ -270,7 +292,7 @@ struct TcShape {
   uint32_t ndpad;            // digit columns of a row (elements x dpad)
   uint32_t mtiles, kblocks, nstages;
   uint32_t n0_len, n1_len;   // MMA N of the two column chunks (n1_len 0 if one chunk)
-  uint32_t btile;            // bytes of one expanded B slice (ndpad x 128)
+  uint32_t btile;            // bytes of one expanded B step (two atoms of ndpad x 128)
   uint32_t G;                // digit groups of 32 per element (epilogue units)
   uint32_t nacc;             // accumulator slots in tensor memory
   uint32_t smem_bytes;
@@ -282,7 +304,7 @@ struct TcShape {
 // a.bx_shared). Output slice (j, kb) lives at a.bx + (j kblocks + kb) btile.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kExpandThreads) k_expand_b(KArgs a, TcShape t) {
-  extern __shared__ uint32_t raw[];   // 64 rows x W words
+  extern __shared__ uint32_t raw[];   // kBK rows x W words
   const uint32_t W = a.W, L = a.L;
   const uint64_t job = blockIdx.x / t.kblocks;
   const uint32_t kb = blockIdx.x % t.kblocks;
@@ -296,17 +318,20 @@ __global__ void __launch_bounds__(kExpandThreads) k_expand_b(KArgs a, TcShape t)
   __syncthreads();
   uint4* dst = (uint4*)(a.bx + (job * t.kblocks + kb) * (uint64_t)t.btile);
   const uint32_t mask = (1u << t.dw) - 1u;
-  // 16-byte unit u of the tile image: row n = u / 8, stored position p = u % 8
-  // holds K chunk c = p ^ (n & 7); row n is digit d = n % dpad of element
-  // e = n / dpad: bits dw d .. dw d + dw - 1 of the element (zero past ell).
-  for (uint32_t u = threadIdx.x; u < t.ndpad * 8u; u += kExpandThreads) {
-    const uint32_t n = u >> 3, c = (u & 7u) ^ (n & 7u);
+  // The step's image is two atoms (K values 0..63, 64..127 of the step), each
+  // ndpad rows of 128 bytes. 16-byte unit uu of an atom: row n = uu / 8,
+  // stored position p = uu % 8 holds K chunk c = p ^ (n & 7); row n is digit
+  // d = n % dpad of element e = n / dpad: bits dw d .. dw d + dw - 1 of the
+  // element (zero past ell).
+  for (uint32_t u = threadIdx.x; u < 2u * t.ndpad * 8u; u += kExpandThreads) {
+    const uint32_t atom = u >= t.ndpad * 8u ? 1u : 0u, uu = u - atom * t.ndpad * 8u;
+    const uint32_t n = uu >> 3, c = (uu & 7u) ^ (n & 7u);
     const uint32_t e = n / t.dpad, d = n - e * t.dpad;
     uint4 v = make_uint4(0, 0, 0, 0);
     if (d < t.D) {
       const uint32_t bit = d * t.dw, wl = bit >> 5, sh = bit & 31u;
       const bool hi = wl + 1 < L;   // the digit may continue in the element's next limb
-      const uint32_t* rp = raw + c * 8u * W + e * L + wl;
+      const uint32_t* rp = raw + (atom * 64u + c * 8u) * W + e * L + wl;
       uint32_t h[8];
 #pragma unroll
       for (int q = 0; q < 8; q++) {
@@ -339,10 +364,10 @@ __global__ void __launch_bounds__(kExpandThreads) k_expand_b(KArgs a, TcShape t)
 //                                      words, then its two output blocks
 //   then the mbarriers, the TMEM address slot and the stop flag
 // Tensor memory (512 columns): nacc accumulators of ndpad columns (item j of
-// the CTA in slot j % nacc), then kAStages expanded A slices of 32 columns
-// (64 fp16 K values per lane = row).
+// the CTA in slot j % nacc), then kAStages expanded A steps of 64 columns
+// (128 fp16 K values per lane = row).
 //
-// The CTA's steps are its items in order, kblocks 64-wide K slices each;
+// The CTA's steps are its items in order, kblocks 128-wide K steps each;
 // step st uses B slot st % nstages and A stage st % kAStages. Barriers:
 //   full[slot]    the slice's B bytes landed (transaction count of the
 //                 producer's arrival) and the four expander warps arrived
@@ -362,9 +387,10 @@ __global__ void __launch_bounds__(kExpandThreads) k_expand_b(KArgs a, TcShape t)
 //   warps 8..15  epilogue of item j while item j+1 is multiplied
 //   warps 2, 3   idle
 // ---------------------------------------------------------------------------
-constexpr uint32_t kAStages = 4;
+constexpr uint32_t kAStages = 2;
+constexpr uint32_t kAStageCols = kBK / 2;        // 128 fp16 K values per lane
 constexpr uint32_t kTmemCols = 512;
-constexpr uint32_t kAColumns = 32 * kAStages;   // tensor-memory columns of the A stages
+constexpr uint32_t kAColumns = kAStageCols * kAStages;   // tensor-memory columns of the A stages
 constexpr uint32_t kAColumn0 = kTmemCols - kAColumns;
 constexpr uint32_t kMaxAcc = 4;
 constexpr uint32_t kExpandWarp0 = 4, kEpiWarp0 = 8, kEpiWarps = 8;
@@ -374,19 +400,21 @@ constexpr uint32_t kEbufWords = 2 * 32 * kGroupWords;   // epilogue staging per 
 // Position of a main-loop step: B slot and the parity of its phase, item and
 // K slice. Advanced incrementally, so the per-step paths divide nothing.
 struct StepPos {
-  uint32_t slot, phase, j, kb;
-  __device__ __forceinline__ void start(uint32_t st, const TcShape& t) {
-    slot = st % t.nstages;
-    phase = (st / t.nstages) & 1u;
-    j = st / t.kblocks;
-    kb = st % t.kblocks;
+  uint32_t slot, phase, j, kb, ns, kbs;
+  __device__ __forceinline__ void start(uint32_t st, uint32_t nstages, uint32_t kblocks) {
+    ns = nstages;
+    kbs = kblocks;
+    slot = st % ns;
+    phase = (st / ns) & 1u;
+    j = st / kbs;
+    kb = st % kbs;
   }
-  __device__ __forceinline__ void next(const TcShape& t) {
-    if (++slot == t.nstages) {
+  __device__ __forceinline__ void next() {
+    if (++slot == ns) {
       slot = 0;
       phase ^= 1u;
     }
-    if (++kb == t.kblocks) {
+    if (++kb == kbs) {
       kb = 0;
       j++;
     }
@@ -396,12 +424,12 @@ struct StepPos {
 // Work item -> gate, first row, live rows, K rotation.
 struct ItemInfo {
   uint32_t gate, row0, rows, rot;
-  __device__ __forceinline__ ItemInfo(uint64_t item, const KArgs& a, const TcShape& t) {
-    gate = (uint32_t)(item / t.mtiles);
-    const uint32_t m = (uint32_t)(item % t.mtiles);
+  __device__ __forceinline__ ItemInfo(uint64_t item, uint32_t Ng, uint32_t mtiles, uint32_t kblocks) {
+    gate = (uint32_t)(item / mtiles);
+    const uint32_t m = (uint32_t)(item % mtiles);
     row0 = m * kTileM;
-    rows = (a.Ng - row0) < (uint32_t)kTileM ? (a.Ng - row0) : (uint32_t)kTileM;
-    rot = m * t.kblocks / t.mtiles;
+    rows = (Ng - row0) < (uint32_t)kTileM ? (Ng - row0) : (uint32_t)kTileM;
+    rot = m * kblocks / mtiles;
   }
 };
 
@@ -444,9 +472,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_gate_tc(KArgs a, TcShape t) {
   if (blockIdx.x >= n_items) return;
   const uint32_t nloc = (uint32_t)((n_items - 1 - blockIdx.x) / gridDim.x + 1);   // items of this CTA
   const uint32_t steps = nloc * t.kblocks;
-  auto item_of = [&](uint32_t jl) { return (uint64_t)blockIdx.x + (uint64_t)jl * gridDim.x; };
+  const uint32_t Ng = a.Ng, mtiles = t.mtiles, kblocks = t.kblocks;
+  auto item_of = [](uint32_t jl) { return (uint64_t)blockIdx.x + (uint64_t)jl * gridDim.x; };
   // encryption launches generate every A operand (and use neither A nor B linearly)
-  const bool gen = (a.desc[ItemInfo(item_of(0), a, t).gate].a >> 30) == REG_GEN;
+  const bool gen = (a.desc[ItemInfo(item_of(0), Ng, mtiles, kblocks).gate].a >> 30) == REG_GEN;
 
   if (tid == 0) {
     for (int b = 0; b < 8; b++) {
@@ -476,8 +505,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_gate_tc(KArgs a, TcShape t) {
     // ------------------------------------------------------------ MMA issuer
     const uint32_t idesc0 = idesc_f16(kTileM, t.n0_len), idesc1 = idesc_f16(kTileM, t.n1_len);
     const uint32_t two = t.n1_len != 0, ring_s = smem_u32(ring);
+    const uint32_t aoff = (t.ndpad * 128u) >> 4, boff1 = (t.n0_len * 128u) >> 4;   // descriptor units
     StepPos p;
-    p.start(0, t);
+    p.start(0, t.nstages, t.kblocks);
     uint32_t acc = 0, accph = 0;   // item p.j's slot and the parity of that slot's use
     bool ok = true;
     for (uint32_t st = 0; st < steps; st++) {
@@ -494,10 +524,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_gate_tc(KArgs a, TcShape t) {
       tc_fence_after();
       const uint32_t b_base = ring_s + p.slot * t.btile;
       const uint32_t d = tmem + acc * t.ndpad;
-      mma_slice(d, d + t.n0_len, tmem + kAColumn0 + 32u * (st & (kAStages - 1)), sw128_desc(b_base),
-                sw128_desc(b_base + t.n0_len * 128u), idesc0, idesc1, p.kb != 0, two, &bfree[p.slot],
-                &accfull[acc], p.kb + 1 == t.kblocks);
-      p.next(t);
+      mma_step(d, d + t.n0_len, tmem + kAColumn0 + kAStageCols * (st & (kAStages - 1)), sw128_desc(b_base),
+               aoff, boff1, idesc0, idesc1, p.kb != 0, two, &bfree[p.slot], &accfull[acc],
+               p.kb + 1 == t.kblocks);
+      p.next();
       if (p.kb == 0 && ++acc == t.nacc) {
         acc = 0;
         accph ^= 1u;
@@ -512,7 +542,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gate_tc(KArgs a, TcShape t) {
       // A tile of item jl into buffer jl % 2, once the expanders left item jl - 2
       auto load_tile = [&](uint32_t jl) -> bool {
         if (gen) return true;
-        const ItemInfo it(item_of(jl), a, t);
+        const ItemInfo it(item_of(jl), Ng, mtiles, kblocks);
         const uint32_t buf = jl & 1u;
         if (jl >= 2 && !mbar_wait_flag(&tfree[buf], ((jl - 2) >> 1) & 1u, sflag)) return false;
         mbar_expect_tx(&tfull[buf], it.rows * W * 4u);
@@ -522,8 +552,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gate_tc(KArgs a, TcShape t) {
       };
       bool ok = load_tile(0) && (nloc < 2 || load_tile(1));
       StepPos p;
-      p.start(0, t);
-      ItemInfo it(item_of(0), a, t);
+      p.start(0, t.nstages, t.kblocks);
+      ItemInfo it(item_of(0), Ng, mtiles, kblocks);
       const uint8_t* bx = a.bx + (a.bx_shared ? 0 : (uint64_t)it.gate) * t.kblocks * (uint64_t)t.btile;
       for (uint32_t st = 0; ok && st < steps; st++) {
         // the next item's tile, halfway through this one
@@ -541,9 +571,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_gate_tc(KArgs a, TcShape t) {
         mbar_expect_tx(&full[p.slot], t.btile);
         bulk_g2s(ring + p.slot * t.btile, bx + (uint64_t)kbr * t.btile, t.btile, &full[p.slot]);
         const uint32_t oj = p.j;
-        p.next(t);
+        p.next();
         if (p.j != oj && p.j < nloc) {
-          it = ItemInfo(item_of(p.j), a, t);
+          it = ItemInfo(item_of(p.j), Ng, mtiles, kblocks);
           bx = a.bx + (a.bx_shared ? 0 : (uint64_t)it.gate) * t.kblocks * (uint64_t)t.btile;
         }
       }
@@ -554,7 +584,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gate_tc(KArgs a, TcShape t) {
     const uint32_t q = warp & 3, r = q * 32 + lane;
     const uint32_t arow = tmem + ((q * 32u) << 16) + kAColumn0;
     StepPos p;
-    p.start(0, t);
+    p.start(0, t.nstages, t.kblocks);
     uint32_t jcur = 0xFFFFFFFFu, rot = 0;
     const uint32_t* row = nullptr;
     bool ok = true;
@@ -565,7 +595,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gate_tc(KArgs a, TcShape t) {
           if (lane == 0) mbar_arrive(&tfree[jcur & 1u]);
         }
         jcur = p.j;
-        const ItemInfo it(item_of(jcur), a, t);
+        const ItemInfo it(item_of(jcur), Ng, mtiles, kblocks);
         rot = it.rot;
         uint32_t* trow = tiles + ((jcur & 1u) * kTileM + r) * W;
         if (gen) {
@@ -608,24 +638,29 @@ __global__ void __launch_bounds__(kThreads, 1) k_gate_tc(KArgs a, TcShape t) {
       tc_fence_after();
       uint32_t kb = p.kb + rot;
       if (kb >= t.kblocks) kb -= t.kblocks;
-      // bits 64 kb .. 64 kb + 63 of the row (words 2 kb, 2 kb + 1; zero past
-      // it) -> 64 fp16 values, K value k in half k % 2 of column k / 2
-      const uint32_t w0 = 2u * kb < W ? row[2u * kb] : 0u;
-      const uint32_t w1 = 2u * kb + 1u < W ? row[2u * kb + 1u] : 0u;
-      uint32_t v[32];
+      // bits 128 kb .. 128 kb + 127 of the row (words 4 kb .. 4 kb + 3; zero
+      // past it) -> 128 fp16 values, K value k in half k % 2 of column k / 2
+      const uint32_t scol = arow + kAStageCols * (st & (kAStages - 1));
 #pragma unroll
-      for (uint32_t b = 0; b < 8; b++) {
-        const uint4 h = byte_to_h8(((b < 4 ? w0 : w1) >> (8u * (b & 3u))) & 0xFFu);
-        v[4 * b] = h.x;
-        v[4 * b + 1] = h.y;
-        v[4 * b + 2] = h.z;
-        v[4 * b + 3] = h.w;
+      for (uint32_t hpart = 0; hpart < 2; hpart++) {
+        const uint32_t wi = 4u * kb + 2u * hpart;
+        const uint32_t w0 = wi < W ? row[wi] : 0u;
+        const uint32_t w1 = wi + 1u < W ? row[wi + 1u] : 0u;
+        uint32_t v[32];
+#pragma unroll
+        for (uint32_t b = 0; b < 8; b++) {
+          const uint4 h = byte_to_h8(((b < 4 ? w0 : w1) >> (8u * (b & 3u))) & 0xFFu);
+          v[4 * b] = h.x;
+          v[4 * b + 1] = h.y;
+          v[4 * b + 2] = h.z;
+          v[4 * b + 3] = h.w;
+        }
+        tmem_st32(scol + 32u * hpart, v);
       }
-      tmem_st32(arow + 32u * (st & (kAStages - 1)), v);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&full[p.slot]);
-      p.next(t);
+      p.next();
     }
     if (!ok && lane == 0) *sflag = 1;
   } else if (warp >= kEpiWarp0) {
@@ -643,7 +678,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gate_tc(KArgs a, TcShape t) {
     uint32_t acc = 0, accph = 0, eph = 0;
     bool ok = true;
     for (uint32_t jl = 0; ok && jl < nloc; jl++) {
-      const ItemInfo it(item_of(jl), a, t);
+      const ItemInfo it(item_of(jl), Ng, mtiles, kblocks);
       const GateDesc gd = a.desc[it.gate];
       const uint32_t code = a.aux[it.gate].code;
       const int c00 = nib(code, 0), c01 = nib(code, 1), c02 = nib(code, 2), c03 = nib(code, 3);
@@ -656,8 +691,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_gate_tc(KArgs a, TcShape t) {
       // 32 x 32 -> 64 multiply-add, the constants summed once per output
       const int64_t bias0 = (int64_t)(c01 + c02 + c03) << 31, bias1 = (int64_t)(c11 + c12 + c13) << 31;
       const bool Ag = (c01 | c11) != 0, Bg = (c02 | c12) != 0;   // linear terms read A, B
-      uint32_t* O0 = gd.o0 != REF_NONE ? a.base[gd.o0 >> 30] + (uint64_t)(gd.o0 & SLOT_MASK) * a.ctw : nullptr;
-      uint32_t* O1 = gd.o1 != REF_NONE ? a.base[gd.o1 >> 30] + (uint64_t)(gd.o1 & SLOT_MASK) * a.ctw : nullptr;
+      uint32_t* O0 = gd.o0 != REF_NONE ? ct_ptr(a, gd.o0) : nullptr;
+      uint32_t* O1 = gd.o1 != REF_NONE ? ct_ptr(a, gd.o1) : nullptr;
+      const uint32_t* Asrc = Ag ? ct_ptr(a, gd.a) : nullptr;
+      const uint32_t* Bsrc = Bg ? ct_ptr(a, gd.b) : nullptr;
       if (!__all_sync(0xFFFFFFFFu, mbar_wait_flag(&accfull[acc], accph, sflag))) {
         ok = false;
         break;
@@ -679,8 +716,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gate_tc(KArgs a, TcShape t) {
           const uint32_t x = 32 * k + lane, br = x / kGroupWords, bw = x - br * kGroupWords;
           const bool in = q * 32 + br < it.rows && wb + bw < L;
           const uint64_t off = wrow0 + (uint64_t)br * W + eo + bw;
-          if (Ag && in) cp_async4(sa + x, ct_ptr(a, gd.a) + off); else sa[x] = 0u;
-          if (Bg && in) cp_async4(sb + x, ct_ptr(a, gd.b) + off); else sb[x] = 0u;
+          if (Ag && in) cp_async4(sa + x, Asrc + off); else sa[x] = 0u;
+          if (Bg && in) cp_async4(sb + x, Bsrc + off); else sb[x] = 0u;
         }
         uint32_t v[32];
         const uint32_t taddr = taddr0 + e * t.dpad + g * kGroupDigits;
@@ -829,7 +866,7 @@ bool make_tc_shape(const KArgs& a, TcShape* t) {
   t->n1_len = t->ndpad - t->n0_len;
   t->mtiles = (a.Ng + kTileM - 1) / kTileM;
   t->kblocks = (a.Ng + kBK - 1) / kBK;
-  t->btile = t->ndpad * 128u;
+  t->btile = t->ndpad * 256u;
   t->G = (t->dpad + kGroupDigits - 1) / kGroupDigits;
   const uint32_t carry_bytes = (uint32_t)kTileM * NP1 * (t->G - 1) * 16u;
   t->nstages = 0;

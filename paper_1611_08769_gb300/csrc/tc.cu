@@ -26,9 +26,9 @@
 //    warp issues the step's tcgen05.mma instructions (one elected lane, the
 //    MMAs and their commits in one instruction group) into the item's TMEM
 //    accumulator; the commits free the A buffer and the ring slot. The
-//    epilogue reads each accumulator with tcgen05.ld (all 16 warps turn digit
-//    sums into int64 word sums), then one thread per (row, element) runs the
-//    element's carry chain, and both output tiles go back by bulk stores.
+//    epilogue (overlapped with the next item's MMAs) reads the accumulator
+//    with tcgen05.ld, forms the words of each 32-digit group and runs both
+//    output carry chains with the linear terms.
 // Every mbarrier wait is bounded (~2 s); on timeout the kernel records
 // KERR_MMA_TIMEOUT, waits (bounded) for its own MMAs, frees its TMEM and
 // returns.
@@ -359,8 +359,7 @@ __global__ void __launch_bounds__(kExpandThreads) k_expand_b(KArgs a, TcShape t)
 //   ring    nstages x btile            expanded B slices (bulk copies)
 //   tiles   2 x 128 x W words          A~ rows of two items (double buffer),
 //                                      complemented in place or generated
-//   carr    128 x NP1 x (G - 1) x 16   epilogue carries between digit groups
-//   ebuf    8 warps x 2 x 32 x 11 words  epilogue staging: a unit's A and B
+//   ebuf    8 warps x 2 x 32 x 11 words  epilogue staging: a group's A and B
 //                                      words, then its two output blocks
 //   then the mbarriers, the TMEM address slot and the stop flag
 // Tensor memory (512 columns): nacc accumulators of ndpad columns (item j of
@@ -437,24 +436,13 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// Barrier of the epilogue warps on an mbarrier (count kEpiWarps), so that the
-// wait is bounded like every other: true once all of them arrived.
-__device__ __forceinline__ bool epi_sync(uint64_t* bar, uint32_t& phase, volatile int* flag) {
-  __syncwarp();
-  if ((threadIdx.x & 31) == 0) mbar_arrive(bar);
-  const bool ok = __all_sync(0xFFFFFFFFu, mbar_wait_flag(bar, phase, flag));
-  phase ^= 1u;
-  return ok;
-}
-
 __global__ void __launch_bounds__(kThreads, 1) k_gate_tc(KArgs a, TcShape t) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const uint32_t W = a.W, L = a.L, NP1 = W / L, G = t.G;
   uint8_t* ring = smem;
   uint32_t* tiles = (uint32_t*)(ring + t.nstages * t.btile);
-  int64_t* carr = (int64_t*)(tiles + 2 * kTileM * W);
-  uint32_t* ebuf = (uint32_t*)((uint8_t*)carr + (size_t)kTileM * NP1 * (G - 1) * 16u);
+  uint32_t* ebuf = tiles + 2 * kTileM * W;
   uint64_t* bars = (uint64_t*)(ebuf + kEpiWarps * kEbufWords);
   uint64_t* full = bars;          // [8]
   uint64_t* bfree = bars + 8;     // [8]
@@ -463,7 +451,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_gate_tc(KArgs a, TcShape t) {
   uint64_t* accfull = bars + 20;  // [kMaxAcc]
   uint64_t* accfree = bars + 24;  // [kMaxAcc]
   uint64_t* drain = bars + 28;    // the issuer's MMAs are done (waited on in the error path)
-  uint64_t* esync = bars + 29;    // epilogue warps' barrier
   uint32_t* tslot = (uint32_t*)(bars + 32);
   volatile int* sflag = (volatile int*)(tslot + 1);   // some role gave up (bounded wait ran out)
 
@@ -491,7 +478,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_gate_tc(KArgs a, TcShape t) {
       mbar_init(&accfree[b], kEpiWarps);
     }
     mbar_init(drain, 1u);
-    mbar_init(esync, kEpiWarps);
     *sflag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -665,17 +651,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_gate_tc(KArgs a, TcShape t) {
     if (!ok && lane == 0) *sflag = 1;
   } else if (warp >= kEpiWarp0) {
     // -------------------------------------------------------------- epilogue
-    // Pass A: a unit is (element e, digit group g) of an item: 32 digit
-    // columns. Warp w takes the units (w - 8) / 4, + 2, ... for the 32 rows of
-    // its lane quarter (w % 4). Digit k of the group adds S << (11k mod 32) to
-    // word (11k) / 32 of the group's 11 words (constant shifts); those words go
-    // through both output carry chains with the linear terms, carry-in 0, and
-    // straight to the output rows; the carries out of the group go to `carr`
-    // unless it is the element's last group. Pass B: one thread per (row,
-    // element) adds each group's carry into the next group's words.
+    // Warp w takes the elements (w - 8) / 4, + 2, ... of the 32 rows of its
+    // lane quarter (w % 4), one digit group (32 digit columns, 11 words) at a
+    // time in order: digit k of the group adds S << (11k mod 32) to word
+    // (11k) / 32 (constant shifts), and the words go through both output carry
+    // chains with the linear terms (the carries run on from group to group in
+    // registers) and out through the warp's staging block.
     const uint32_t q = warp & 3, cs = (warp - kEpiWarp0) >> 2, r = q * 32 + lane;
-    const uint32_t etid = tid - kEpiWarp0 * 32;
-    uint32_t acc = 0, accph = 0, eph = 0;
+    uint32_t acc = 0, accph = 0;
     bool ok = true;
     for (uint32_t jl = 0; ok && jl < nloc; jl++) {
       const ItemInfo it(item_of(jl), Ng, mtiles, kblocks);
@@ -705,82 +688,80 @@ __global__ void __launch_bounds__(kThreads, 1) k_gate_tc(KArgs a, TcShape t) {
       uint32_t* sa = ebuf + (warp - kEpiWarp0) * kEbufWords;
       uint32_t* sb = sa + 32 * kGroupWords;
       const uint64_t wrow0 = (uint64_t)(it.row0 + q * 32) * W;   // first row of the block
-      for (uint32_t u = cs; u < NP1 * G; u += kEpiWarps / 4) {
-        const uint32_t e = u / G, g = u - e * G;
-        const uint32_t wb = g * kGroupWords;   // first local word of the group
-        const uint32_t eo = e * L + wb;        // its word offset in a row
-        // block element x = 32 k + lane: row x / 11, word x % 11 (a row's 11
-        // words are contiguous, so a warp's copy touches a few segments)
-#pragma unroll
-        for (uint32_t k = 0; k < kGroupWords; k++) {
-          const uint32_t x = 32 * k + lane, br = x / kGroupWords, bw = x - br * kGroupWords;
-          const bool in = q * 32 + br < it.rows && wb + bw < L;
-          const uint64_t off = wrow0 + (uint64_t)br * W + eo + bw;
-          if (Ag && in) cp_async4(sa + x, Asrc + off); else sa[x] = 0u;
-          if (Bg && in) cp_async4(sb + x, Bsrc + off); else sb[x] = 0u;
-        }
-        uint32_t v[32];
-        const uint32_t taddr = taddr0 + e * t.dpad + g * kGroupDigits;
-        tmem_ld16(taddr, *reinterpret_cast<uint32_t(*)[16]>(&v[0]));
-        if (g * kGroupDigits + 16 < t.dpad) {
-          tmem_ld16(taddr + 16, *reinterpret_cast<uint32_t(*)[16]>(&v[16]));
-        } else {
-#pragma unroll
-          for (int k = 16; k < 32; k++) v[k] = 0;
-        }
-        int64_t kw[kGroupWords];
-#pragma unroll
-        for (int k = 0; k < (int)kGroupWords; k++) kw[k] = 0;
-#pragma unroll
-        for (int k = 0; k < (int)kGroupDigits; k++)
-          kw[(k * (int)kDigitBits) >> 5] += (int64_t)__float2int_rn(__uint_as_float(v[k]))
-                                            << ((k * (int)kDigitBits) & 31);
-        cp_async_wait_all();
-        __syncwarp();
-        // own row: words at lane * 11 (odd stride: no bank conflicts)
-        // word k of the group: t = carry + c3 K + c1 A + c2 B (+ c0 P); the low
-        // half is the output word; the carry into the next word is the high
-        // half plus c3 times K's high half (K = 2^32 khi + klo, khi < 2^24)
-        const uint32_t kp = e == pe ? pw_at - wb : 0xFFFFFFFFu;   // group word holding P's bit
+      // elements e = cs, cs + 2, ...; an element's groups in order, the carries
+      // between them kept in registers
+      for (uint32_t e = cs; e < NP1; e += kEpiWarps / 4) {
         int32_t carry0 = 0, carry1 = 0;
+        for (uint32_t g = 0; g < G; g++) {
+          const uint32_t wb = g * kGroupWords;   // first local word of the group
+          const uint32_t eo = e * L + wb;        // its word offset in a row
+          // block element x = 32 k + lane: row x / 11, word x % 11 (a row's 11
+          // words are contiguous, so a warp's copy touches a few segments)
 #pragma unroll
-        for (uint32_t k = 0; k < kGroupWords; k++) {
-          const int32_t xa = (int32_t)(sa[lane * kGroupWords + k] ^ 0x80000000u);
-          const int32_t xb = (int32_t)(sb[lane * kGroupWords + k] ^ 0x80000000u);
-          const int32_t xk = (int32_t)((uint32_t)kw[k] ^ 0x80000000u);
-          const int32_t khi = (int32_t)(kw[k] >> 32);
-          int64_t t0 = bias0 + carry0, t1 = bias1 + carry1;
-          t0 += (int64_t)c01 * xa;
-          t0 += (int64_t)c02 * xb;
-          t0 += (int64_t)c03 * xk;
-          t1 += (int64_t)c11 * xa;
-          t1 += (int64_t)c12 * xb;
-          t1 += (int64_t)c13 * xk;
-          if (k == kp) {
-            t0 += p0;
-            t1 += p1;
-          }
-          carry0 = (int32_t)(t0 >> 32) + c03 * khi;
-          carry1 = (int32_t)(t1 >> 32) + c13 * khi;
-          sa[lane * kGroupWords + k] = (uint32_t)t0;
-          sb[lane * kGroupWords + k] = (uint32_t)t1;
-        }
-        if (g + 1 < G) {
-          int64_t* cp = carr + (((uint64_t)r * NP1 + e) * (G - 1) + g) * 2;
-          cp[0] = carry0;
-          cp[1] = carry1;
-        }
-        __syncwarp();
-#pragma unroll
-        for (uint32_t k = 0; k < kGroupWords; k++) {
-          const uint32_t x = 32 * k + lane, br = x / kGroupWords, bw = x - br * kGroupWords;
-          if (q * 32 + br < it.rows && wb + bw < L) {
+          for (uint32_t k = 0; k < kGroupWords; k++) {
+            const uint32_t x = 32 * k + lane, br = x / kGroupWords, bw = x - br * kGroupWords;
+            const bool in = q * 32 + br < it.rows && wb + bw < L;
             const uint64_t off = wrow0 + (uint64_t)br * W + eo + bw;
-            if (O0) O0[off] = sa[x];
-            if (O1) O1[off] = sb[x];
+            if (Ag && in) cp_async4(sa + x, Asrc + off); else sa[x] = 0u;
+            if (Bg && in) cp_async4(sb + x, Bsrc + off); else sb[x] = 0u;
           }
+          uint32_t v[32];
+          const uint32_t taddr = taddr0 + e * t.dpad + g * kGroupDigits;
+          tmem_ld16(taddr, *reinterpret_cast<uint32_t(*)[16]>(&v[0]));
+          if (g * kGroupDigits + 16 < t.dpad) {
+            tmem_ld16(taddr + 16, *reinterpret_cast<uint32_t(*)[16]>(&v[16]));
+          } else {
+#pragma unroll
+            for (int k = 16; k < 32; k++) v[k] = 0;
+          }
+          int64_t kw[kGroupWords];
+#pragma unroll
+          for (int k = 0; k < (int)kGroupWords; k++) kw[k] = 0;
+#pragma unroll
+          for (int k = 0; k < (int)kGroupDigits; k++)
+            kw[(k * (int)kDigitBits) >> 5] += (int64_t)__float2int_rn(__uint_as_float(v[k]))
+                                              << ((k * (int)kDigitBits) & 31);
+          cp_async_wait_all();
+          __syncwarp();
+          // own row: words at lane * 11 (odd stride: no bank conflicts)
+          // word k of the group: t = carry + c3 K + c1 A + c2 B (+ c0 P); the low
+          // half is the output word; the carry into the next word is the high
+          // half plus c3 times K's high half (K = 2^32 khi + klo, khi < 2^24)
+          const uint32_t kp = e == pe ? pw_at - wb : 0xFFFFFFFFu;   // group word holding P's bit
+#pragma unroll
+          for (uint32_t k = 0; k < kGroupWords; k++) {
+            const int32_t xa = (int32_t)(sa[lane * kGroupWords + k] ^ 0x80000000u);
+            const int32_t xb = (int32_t)(sb[lane * kGroupWords + k] ^ 0x80000000u);
+            const int32_t xk = (int32_t)((uint32_t)kw[k] ^ 0x80000000u);
+            const int32_t khi = (int32_t)(kw[k] >> 32);
+            int64_t t0 = bias0 + carry0, t1 = bias1 + carry1;
+            t0 += (int64_t)c01 * xa;
+            t0 += (int64_t)c02 * xb;
+            t0 += (int64_t)c03 * xk;
+            t1 += (int64_t)c11 * xa;
+            t1 += (int64_t)c12 * xb;
+            t1 += (int64_t)c13 * xk;
+            if (k == kp) {
+              t0 += p0;
+              t1 += p1;
+            }
+            carry0 = (int32_t)(t0 >> 32) + c03 * khi;
+            carry1 = (int32_t)(t1 >> 32) + c13 * khi;
+            sa[lane * kGroupWords + k] = (uint32_t)t0;
+            sb[lane * kGroupWords + k] = (uint32_t)t1;
+          }
+          __syncwarp();
+#pragma unroll
+          for (uint32_t k = 0; k < kGroupWords; k++) {
+            const uint32_t x = 32 * k + lane, br = x / kGroupWords, bw = x - br * kGroupWords;
+            if (q * 32 + br < it.rows && wb + bw < L) {
+              const uint64_t off = wrow0 + (uint64_t)br * W + eo + bw;
+              if (O0) O0[off] = sa[x];
+              if (O1) O1[off] = sb[x];
+            }
+          }
+          __syncwarp();   // the staging is refilled by the next group
         }
-        __syncwarp();   // the staging is refilled by the next unit
       }
       // this warp's reads of the accumulator are complete (tmem_ld16 waits)
       tc_fence_before();
@@ -789,42 +770,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_gate_tc(KArgs a, TcShape t) {
       if (++acc == t.nacc) {
         acc = 0;
         accph ^= 1u;
-      }
-      // carries and output words of pass A are visible
-      if (!epi_sync(esync, eph, sflag)) {
-        ok = false;
-        break;
-      }
-      if (G > 1) {
-        for (uint32_t task = etid; task < kTileM * NP1; task += kEpiWarps * 32) {
-          const uint32_t rr = task / NP1, e = task - rr * NP1;
-          if (rr >= it.rows) continue;
-          const uint64_t roff = (uint64_t)(it.row0 + rr) * W + e * L;
-          uint32_t* P0 = O0 ? O0 + roff : nullptr;
-          uint32_t* P1 = O1 ? O1 + roff : nullptr;
-          const int64_t* cp = carr + ((uint64_t)rr * NP1 + e) * (G - 1) * 2;
-          int64_t in0 = 0, in1 = 0;
-          for (uint32_t g = 1; g < G; g++) {
-            in0 += cp[2 * (g - 1)];
-            in1 += cp[2 * (g - 1) + 1];
-            const uint32_t wend = (g + 1) * kGroupWords < L ? (g + 1) * kGroupWords : L;
-            for (uint32_t w = g * kGroupWords; P0 && w < wend && in0 != 0; w++) {
-              const int64_t o = (int64_t)P0[w] + in0;
-              P0[w] = (uint32_t)o;
-              in0 = o >> 32;
-            }
-            for (uint32_t w = g * kGroupWords; P1 && w < wend && in1 != 0; w++) {
-              const int64_t o = (int64_t)P1[w] + in1;
-              P1[w] = (uint32_t)o;
-              in1 = o >> 32;
-            }
-          }
-        }
-        // carr is rewritten by the next item
-        if (!epi_sync(esync, eph, sflag)) {
-          ok = false;
-          break;
-        }
       }
     }
     if (!ok && lane == 0) *sflag = 1;
@@ -845,8 +790,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gate_tc(KArgs a, TcShape t) {
 
 namespace {
 
-uint32_t tc_smem_bytes(uint32_t W, uint32_t btile, uint32_t ns, uint32_t carry_bytes) {
-  return 1024u + ns * btile + 2u * (uint32_t)kTileM * W * 4u + carry_bytes + kEpiWarps * kEbufWords * 4u +
+uint32_t tc_smem_bytes(uint32_t W, uint32_t btile, uint32_t ns) {
+  return 1024u + ns * btile + 2u * (uint32_t)kTileM * W * 4u + kEpiWarps * kEbufWords * 4u +
          kBars * 8u;
 }
 
@@ -868,15 +813,14 @@ bool make_tc_shape(const KArgs& a, TcShape* t) {
   t->kblocks = (a.Ng + kBK - 1) / kBK;
   t->btile = t->ndpad * 256u;
   t->G = (t->dpad + kGroupDigits - 1) / kGroupDigits;
-  const uint32_t carry_bytes = (uint32_t)kTileM * NP1 * (t->G - 1) * 16u;
   t->nstages = 0;
   for (uint32_t ns = 8; ns >= kAStages; ns--)
-    if (tc_smem_bytes(a.W, t->btile, ns, carry_bytes) <= kMaxSmem) {
+    if (tc_smem_bytes(a.W, t->btile, ns) <= kMaxSmem) {
       t->nstages = ns;
       break;
     }
   if (!t->nstages) return false;
-  t->smem_bytes = tc_smem_bytes(a.W, t->btile, t->nstages, carry_bytes);
+  t->smem_bytes = tc_smem_bytes(a.W, t->btile, t->nstages);
   return true;
 }
 

@@ -131,6 +131,14 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "of fallback"
 
 
+# DRAM bytes (read + write) per product of the tensor-core gate kernel, from an
+# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum of one launch over
+# a 512-gate level at n = 1, ell = 1056, inputs larger than L2), keyed by
+# (n, ell). The algorithmic bytes of a product at these parameters are 3.07 MB:
+# the expanded B operand once, the A and B rows, the two output rows.
+TC_DRAM_BYTES_PER_PRODUCT = {(1, 1056): 3.088e6}
+
+
 def roofline(params, gate_kernel, gate_ms, launches, gates_timed, tc_columns=0):
     """Roofline of the dominant kernel (the gate product) from CUDA-event times.
 
@@ -151,8 +159,11 @@ def roofline(params, gate_kernel, gate_ms, launches, gates_timed, tc_columns=0):
         flops = 2.0 * Ng * Ng * cols * gates_timed
         achieved = flops / sec / 1e12
         peak = float(peaks["bf16_tflops_sustained"])
+        per = TC_DRAM_BYTES_PER_PRODUCT.get((params.n, params.ell))
+        traffic = per * gates_timed / max(1, launches) if per else None
         return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "kernel": "k_gate_tc (+k_expand_b)",
+                "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per launch",
+                "kernel": "k_gate_tc (+k_expand_b)",
                 "avg_launch_ms": avg_launch_ms, "flops_per_product": 2.0 * Ng * Ng * cols,
                 "peak_source": f"bf16_tflops_sustained {src}"}
     ops = float(Ng) * Ng * (params.n + 1) * L * gates_timed

@@ -154,55 +154,68 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
 // warp (every lane executes the statement; the MMAs and the commits that
 // track them sit under the same elect.sync predicate, so one thread issues
 // all of them):
-//   D[d0] (+)= A * B0^T over eight K=16 steps, the same into D[d1] with B1
-//   (= B0 + boff1 descriptor units) when `two` is set; then commit -> fb, and
+//   D[d0] (+)= A * B0^T over eight K=16 steps, for TWO also the same into
+//   D[d1] with B1 (= B0 + boff1 descriptor units); then commit -> fb, and
 //   -> fd if `last` (one commit per step: a second one costs the tensor pipe
-//   measurably).
+//   measurably). The one-chunk and two-chunk forms are separate instruction
+//   sequences: a predicated-off MMA still takes its turn in the tensor pipe.
 // A sits in tensor memory at column `at` (row i in lane i, two fp16 K values
 // per 32-bit column: a K=16 step is 8 columns). B is two 128B-swizzled
 // K-major shared-memory atoms of 64 K values, the second `aoff` descriptor
 // units (16 bytes each) after the first; within an atom a K=16 step advances
 // 32 bytes = 2 units. `acc` = 0 starts the accumulator (first step of an item).
+#define SFFT_MMA_PROLOGUE                                                                        \
+  "{\n .reg .pred e, e3, p, t;\n .reg .b32 a1, a2, a3, a4, a5, a6, a7;\n"                       \
+  " .reg .b64 o, o1, x0, x1, x2, x3, x4, x5, x6, x7, y0, y1, y2, y3, y4, y5, y6, y7;\n"         \
+  " elect.sync _|e, 0xffffffff;\n"                                                               \
+  " setp.ne.b32 p, %8, 0;\n"                                                                     \
+  " setp.eq.b32 t, %8, %8;\n"                                                                    \
+  " setp.ne.and.b32 e3, %11, 0, e;\n"                                                            \
+  " add.u32 a1, %2, 8;\n add.u32 a2, %2, 16;\n add.u32 a3, %2, 24;\n add.u32 a4, %2, 32;\n"     \
+  " add.u32 a5, %2, 40;\n add.u32 a6, %2, 48;\n add.u32 a7, %2, 56;\n"                          \
+  " cvt.u64.u32 o, %4;\n cvt.u64.u32 o1, %5;\n"                                                 \
+  " mov.b64 x0, %3;\n add.u64 x1, x0, 2;\n add.u64 x2, x0, 4;\n add.u64 x3, x0, 6;\n"          \
+  " add.u64 x4, x0, o;\n add.u64 x5, x4, 2;\n add.u64 x6, x4, 4;\n add.u64 x7, x4, 6;\n"        \
+  " @e tcgen05.mma.cta_group::1.kind::f16 [%0], [%2], x0, %6, p;\n"                             \
+  " @e tcgen05.mma.cta_group::1.kind::f16 [%0], [a1], x1, %6, t;\n"                             \
+  " @e tcgen05.mma.cta_group::1.kind::f16 [%0], [a2], x2, %6, t;\n"                             \
+  " @e tcgen05.mma.cta_group::1.kind::f16 [%0], [a3], x3, %6, t;\n"                             \
+  " @e tcgen05.mma.cta_group::1.kind::f16 [%0], [a4], x4, %6, t;\n"                             \
+  " @e tcgen05.mma.cta_group::1.kind::f16 [%0], [a5], x5, %6, t;\n"                             \
+  " @e tcgen05.mma.cta_group::1.kind::f16 [%0], [a6], x6, %6, t;\n"                             \
+  " @e tcgen05.mma.cta_group::1.kind::f16 [%0], [a7], x7, %6, t;\n"
+#define SFFT_MMA_SECOND                                                                          \
+  " add.u64 y0, x0, o1;\n add.u64 y1, x1, o1;\n add.u64 y2, x2, o1;\n add.u64 y3, x3, o1;\n"    \
+  " add.u64 y4, x4, o1;\n add.u64 y5, x5, o1;\n add.u64 y6, x6, o1;\n add.u64 y7, x7, o1;\n"    \
+  " @e tcgen05.mma.cta_group::1.kind::f16 [%1], [%2], y0, %7, p;\n"                             \
+  " @e tcgen05.mma.cta_group::1.kind::f16 [%1], [a1], y1, %7, t;\n"                             \
+  " @e tcgen05.mma.cta_group::1.kind::f16 [%1], [a2], y2, %7, t;\n"                             \
+  " @e tcgen05.mma.cta_group::1.kind::f16 [%1], [a3], y3, %7, t;\n"                             \
+  " @e tcgen05.mma.cta_group::1.kind::f16 [%1], [a4], y4, %7, t;\n"                             \
+  " @e tcgen05.mma.cta_group::1.kind::f16 [%1], [a5], y5, %7, t;\n"                             \
+  " @e tcgen05.mma.cta_group::1.kind::f16 [%1], [a6], y6, %7, t;\n"                             \
+  " @e tcgen05.mma.cta_group::1.kind::f16 [%1], [a7], y7, %7, t;\n"
+#define SFFT_MMA_COMMITS                                                                         \
+  " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%9];\n"           \
+  " @e3 tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%10];\n}\n"
+
+template <bool TWO>
 __device__ __forceinline__ void mma_step(uint32_t d0, uint32_t d1, uint32_t at, uint64_t b0, uint32_t aoff,
                                          uint32_t boff1, uint32_t id0, uint32_t id1, uint32_t acc,
-                                         uint32_t two, uint64_t* fb, uint64_t* fd, uint32_t last) {
-  asm volatile(
-      "{\n .reg .pred e, e2, e3, p, t;\n .reg .b32 a1, a2, a3, a4, a5, a6, a7;\n"
-      " .reg .b64 o, o1, x0, x1, x2, x3, x4, x5, x6, x7, y0, y1, y2, y3, y4, y5, y6, y7;\n"
-      " elect.sync _|e, 0xffffffff;\n"
-      " setp.ne.b32 p, %8, 0;\n"
-      " setp.eq.b32 t, %8, %8;\n"
-      " setp.ne.and.b32 e2, %9, 0, e;\n"
-      " setp.ne.and.b32 e3, %12, 0, e;\n"
-      " add.u32 a1, %2, 8;\n add.u32 a2, %2, 16;\n add.u32 a3, %2, 24;\n add.u32 a4, %2, 32;\n"
-      " add.u32 a5, %2, 40;\n add.u32 a6, %2, 48;\n add.u32 a7, %2, 56;\n"
-      " cvt.u64.u32 o, %4;\n cvt.u64.u32 o1, %5;\n"
-      " mov.b64 x0, %3;\n add.u64 x1, x0, 2;\n add.u64 x2, x0, 4;\n add.u64 x3, x0, 6;\n"
-      " add.u64 x4, x0, o;\n add.u64 x5, x4, 2;\n add.u64 x6, x4, 4;\n add.u64 x7, x4, 6;\n"
-      " add.u64 y0, x0, o1;\n add.u64 y1, x1, o1;\n add.u64 y2, x2, o1;\n add.u64 y3, x3, o1;\n"
-      " add.u64 y4, x4, o1;\n add.u64 y5, x5, o1;\n add.u64 y6, x6, o1;\n add.u64 y7, x7, o1;\n"
-      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], [%2], x0, %6, p;\n"
-      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], [a1], x1, %6, t;\n"
-      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], [a2], x2, %6, t;\n"
-      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], [a3], x3, %6, t;\n"
-      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], [a4], x4, %6, t;\n"
-      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], [a5], x5, %6, t;\n"
-      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], [a6], x6, %6, t;\n"
-      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], [a7], x7, %6, t;\n"
-      " @e2 tcgen05.mma.cta_group::1.kind::f16 [%1], [%2], y0, %7, p;\n"
-      " @e2 tcgen05.mma.cta_group::1.kind::f16 [%1], [a1], y1, %7, t;\n"
-      " @e2 tcgen05.mma.cta_group::1.kind::f16 [%1], [a2], y2, %7, t;\n"
-      " @e2 tcgen05.mma.cta_group::1.kind::f16 [%1], [a3], y3, %7, t;\n"
-      " @e2 tcgen05.mma.cta_group::1.kind::f16 [%1], [a4], y4, %7, t;\n"
-      " @e2 tcgen05.mma.cta_group::1.kind::f16 [%1], [a5], y5, %7, t;\n"
-      " @e2 tcgen05.mma.cta_group::1.kind::f16 [%1], [a6], y6, %7, t;\n"
-      " @e2 tcgen05.mma.cta_group::1.kind::f16 [%1], [a7], y7, %7, t;\n"
-      " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%10];\n"
-      " @e3 tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%11];\n}\n" ::"r"(d0),
-      "r"(d1), "r"(at), "l"(b0), "r"(aoff), "r"(boff1), "r"(id0), "r"(id1), "r"(acc), "r"(two),
-      "r"(smem_u32(fb)), "r"(smem_u32(fd)), "r"(last)
-      : "memory");
+                                         uint64_t* fb, uint64_t* fd, uint32_t last) {
+  if (TWO)
+    asm volatile(SFFT_MMA_PROLOGUE SFFT_MMA_SECOND SFFT_MMA_COMMITS ::"r"(d0), "r"(d1), "r"(at), "l"(b0),
+                 "r"(aoff), "r"(boff1), "r"(id0), "r"(id1), "r"(acc), "r"(smem_u32(fb)), "r"(smem_u32(fd)),
+                 "r"(last)
+                 : "memory");
+  else
+    asm volatile(SFFT_MMA_PROLOGUE SFFT_MMA_COMMITS ::"r"(d0), "r"(d1), "r"(at), "l"(b0), "r"(aoff),
+                 "r"(boff1), "r"(id0), "r"(id1), "r"(acc), "r"(smem_u32(fb)), "r"(smem_u32(fd)), "r"(last)
+                 : "memory");
 }
+#undef SFFT_MMA_PROLOGUE
+#undef SFFT_MMA_SECOND
+#undef SFFT_MMA_COMMITS
 
 // Commit -> bar from the elected lane of the calling warp (the lane that
 // issued the warp's MMAs: with every lane active, elect.sync picks the same
@@ -510,9 +523,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_gate_tc(KArgs a, TcShape t) {
       tc_fence_after();
       const uint32_t b_base = ring_s + p.slot * t.btile;
       const uint32_t d = tmem + acc * t.ndpad;
-      mma_step(d, d + t.n0_len, tmem + kAColumn0 + kAStageCols * (st & (kAStages - 1)), sw128_desc(b_base),
-               aoff, boff1, idesc0, idesc1, p.kb != 0, two, &bfree[p.slot], &accfull[acc],
-               p.kb + 1 == t.kblocks);
+      const uint32_t at = tmem + kAColumn0 + kAStageCols * (st & (kAStages - 1));
+      if (two)
+        mma_step<true>(d, d + t.n0_len, at, sw128_desc(b_base), aoff, boff1, idesc0, idesc1, p.kb != 0,
+                       &bfree[p.slot], &accfull[acc], p.kb + 1 == t.kblocks);
+      else
+        mma_step<false>(d, d + t.n0_len, at, sw128_desc(b_base), aoff, boff1, idesc0, idesc1, p.kb != 0,
+                        &bfree[p.slot], &accfull[acc], p.kb + 1 == t.kblocks);
       p.next();
       if (p.kb == 0 && ++acc == t.nacc) {
         acc = 0;
@@ -855,14 +872,16 @@ uint32_t tc_digit_columns(const KArgs& a) {
 }
 
 // A level runs in chunks of gates (expand a chunk's B operands, then multiply
-// it) so that the expansion buffer stays bounded; the chunk is large enough
-// that each GEMM launch spans many waves of CTAs.
-constexpr uint64_t kBxL2Budget = 512ull << 20;
+// it) so that the expansion buffer stays bounded (2 GB: one chunk per level
+// for the 1056-bit FFT). Larger chunks amortize the persistent GEMM's pipeline
+// fill and tail; chunks small enough for the expanded operands to stay in L2
+// (tens of MB) measured slower.
+constexpr uint64_t kBxBudget = 2048ull << 20;
 
 uint64_t tc_chunk_gates(const KArgs& a) {
   const uint64_t per = tc_bx_bytes_per_gate(a);
   if (per == 0) return 0;
-  const uint64_t c = std::min<uint64_t>(kBxL2Budget / per, 4096);
+  const uint64_t c = std::min<uint64_t>(kBxBudget / per, 4096);
   return c ? c : 1;
 }
 

@@ -123,9 +123,10 @@ int sfft_gather_dec_rows(const sfft_params* p, const uint32_t* d_ct, uint64_t n_
 /* Smallest ell (multiple of 32, <= 8192) for which the static worst-case
  * noise bound of the FFT circuit stays below q/4 with m = Ng and error bound
  * chi (the leveled reading of the scheme's noise management; Sec. 5 ends by
- * pointing at refreshing). 0 if none. */
+ * pointing at refreshing). flags: the circuit variant (SFFT_PLAN_XCARRY).
+ * 0 if none. */
 uint32_t sfft_min_ell(uint32_t N1, uint32_t N2, uint32_t F, uint32_t f, uint32_t n,
-                      uint32_t chi);
+                      uint32_t chi, uint32_t flags);
 
 typedef struct sfft_plan_info {
   uint64_t inputs, outputs;     /* ciphertexts in / out */
@@ -141,6 +142,7 @@ typedef struct sfft_plan_info {
   uint32_t gate_kernel;         /* 1 integer-ALU kernel, 2 tensor-core kernel */
   uint32_t tc_columns;          /* tensor-core kernel: digit columns of a product row
                                    ((n+1) ceil(ell / dw), dw = 11 bits); 0 otherwise */
+  uint64_t gates_xadd;          /* linear exclusive-carry sums (SFFT_PLAN_XCARRY), no product */
 } sfft_plan_info;
 
 /* Builds the canonical gate circuit of a 1-D (N2 == 1) or row-column 2-D FFT
@@ -151,6 +153,13 @@ typedef struct sfft_plan_info {
  * if the static noise bound reaches q/4. flags: SFFT_PLAN_* below. */
 #define SFFT_PLAN_ALLOW_NOISY 1u   /* build even if the noise bound fails */
 #define SFFT_PLAN_INT_KERNEL 2u    /* integer-ALU gate kernel even where tensor cores apply */
+/* Circuit variant (not the paper's): the full adder's carry is the sum of its
+ * two half-adder carries, which are never both 1 (Lemma 6's OR, exact on
+ * every input it meets), a linear gate (0, 1, 1, 0) with no ciphertext
+ * product whose noise adds instead of growing by Ng. Fewer products and a
+ * smaller ell (sfft_min_ell with the same flag); different ciphertexts. Linear
+ * gates run after the products of their level. */
+#define SFFT_PLAN_XCARRY 8u
 int sfft_plan_create(const sfft_params* p, uint32_t N1, uint32_t N2, uint32_t F, uint32_t f,
                      uint32_t flags, sfft_plan** out);
 int sfft_plan_info_get(const sfft_plan* plan, sfft_plan_info* info);
@@ -176,9 +185,10 @@ int sfft_eval_fft_host(sfft_plan* plan, const uint32_t* h_in, uint32_t* h_out,
                        uint64_t scratch_bytes, void* stream);
 
 /* Host-only statistics of the compiled circuit (no device memory touched):
- * fills every field of sfft_plan_info as sfft_plan_create would. */
+ * fills every field of sfft_plan_info as sfft_plan_create would with the
+ * same flags (only SFFT_PLAN_XCARRY changes the circuit). */
 int sfft_circuit_info(const sfft_params* p, uint32_t N1, uint32_t N2, uint32_t F, uint32_t f,
-                      sfft_plan_info* info);
+                      uint32_t flags, sfft_plan_info* info);
 
 /* Host-only plaintext run of the compiled device program (test hook): the
  * same levels, scratch slots, output fix-ups and adjusted gate coefficients
@@ -186,7 +196,8 @@ int sfft_circuit_info(const sfft_params* p, uint32_t N1, uint32_t N2, uint32_t F
  * out = c0 + c1 a + c2 b + c3 A~ b). h_in_bits: info.inputs bytes (0/1),
  * h_out_bits: info.outputs bytes. */
 int sfft_program_eval_plain(const sfft_params* p, uint32_t N1, uint32_t N2, uint32_t F,
-                            uint32_t f, const uint8_t* h_in_bits, uint8_t* h_out_bits);
+                            uint32_t f, uint32_t flags, const uint8_t* h_in_bits,
+                            uint8_t* h_out_bits);
 
 /* sfft_eval_fft without any allocation (the paper has no counterpart; this
  * is a library service). For callers that must not call cudaMalloc while
@@ -267,8 +278,9 @@ typedef struct sfft_server_stats {
   double p50_ms, p99_ms, max_ms;   /* submit-to-completion latency of completed requests */
 } sfft_server_stats;
 
+/* flags: SFFT_PLAN_XCARRY selects the exclusive-carry circuit for every request. */
 int sfft_server_create(const sfft_params* p, uint64_t hbm_budget_bytes, uint32_t max_active,
-                       sfft_server** out);
+                       uint32_t flags, sfft_server** out);
 /* Queues one request. h_in: its input ciphertexts (layout of sfft_eval_fft's
  * d_in), h_out: room for its output ciphertexts; both caller-owned and valid
  * until sfft_server_wait returned for the ticket. ENOMEM if the request alone

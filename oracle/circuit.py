@@ -20,7 +20,11 @@ choices the paper leaves open (all readings, stated in the design doc):
   scheme these replacements are bit-exact (BitDecomp(P) = I, BitDecomp(A')P =
   A'), so folding never changes a ciphertext.
 * HA(x,y) = (XOR(x,y), AND(x,y)); FA(x,y,z) = HA(x,y) -> (s1,c1),
-  HA(s1,z) -> (s,c2), carry OR(c1,c2) (Lemma 6).
+  HA(s1,z) -> (s,c2), carry OR(c1,c2) (Lemma 6). Variant (``xcarry``): the
+  two carries are never both 1 (c1 = 1 forces s1 = 0, hence c2 = 0), so the
+  carry is their sum XADD(c1,c2), a linear gate with no product whose noise
+  adds instead of growing by Ng; XADD folds like OR (x + 0 = x, and a
+  constant 1 forces the other carry to 0, giving 1).
 * ADD_F(x,y,cin): bit 0 is HA when cin is the constant 0, else FA; bits
   1..F-1 FA; carry out of the top bit dropped. SUB_F(x,y) = ADD_F(x, NOT y, 1).
 * MUL(x, w) for a plaintext constant w, T = f + F: sign-extend x and w to T
@@ -37,6 +41,8 @@ choices the paper leaves open (all readings, stated in the design doc):
   s = 1..log2 N with span m = 2^s and twiddle W_N^(j N/m); no 1/N scaling.
   2-D: every row, then every column.
 
+Depth (for the operand rule): XADD, like NOT, is linear: the max of its inputs.
+
 Wires are non-negative ints; the trivial constants are ZERO = -1, ONE = -2.
 Input wire number (k * 2 + part) * F + bit holds bit ``bit`` of the real
 (part 0) or imaginary (part 1) word of sample k.
@@ -49,7 +55,8 @@ ZERO, ONE = -1, -2
 
 
 class Circuit:
-    def __init__(self):
+    def __init__(self, xcarry=False):
+        self.xcarry = xcarry   # full-adder carry as XADD instead of OR
         self.gates = []      # (op, a, b, out); b is None for NOT
         self.depth = []      # per wire
         self.inputs = []
@@ -108,6 +115,16 @@ class Circuit:
             return a
         return self._emit("OR", a, b, 1 + max(self.d(a), self.d(b)))
 
+    def XADD(self, a, b):
+        """Sum of two bits that are never both 1 (linear)."""
+        if a == ONE or b == ONE:
+            return ONE
+        if a == ZERO:
+            return b
+        if b == ZERO:
+            return a
+        return self._emit("XADD", a, b, max(self.d(a), self.d(b)))
+
     # -- adders (Lemmas 5-7) ---------------------------------------------
     def HA(self, a, b):
         return self.XOR(a, b), self.AND(a, b)
@@ -115,7 +132,7 @@ class Circuit:
     def FA(self, a, b, c):
         s1, c1 = self.HA(a, b)
         s, c2 = self.HA(s1, c)
-        return s, self.OR(c1, c2)
+        return s, (self.XADD(c1, c2) if self.xcarry else self.OR(c1, c2))
 
     def ADD(self, x, y, cin=ZERO):
         F = len(x)
@@ -225,16 +242,17 @@ def twiddles(N, f):
     return tw
 
 
-def fft_circuit(N1, N2, F, f):
+def fft_circuit(N1, N2, F, f, xcarry=False):
     """Circuit of a 1-D (N2 == 1) or row-column 2-D encrypted FFT.
 
     1-D: N1 samples. 2-D: an N1 x N2 image, sample k = r * N2 + c; all row
-    FFTs (length N2) first, then all column FFTs (length N1).
+    FFTs (length N2) first, then all column FFTs (length N1). ``xcarry``
+    selects the exclusive-carry full adder.
     """
     for n in (N1, N2):
         if n < 1 or n & (n - 1):
             raise ValueError("FFT sizes must be powers of two")
-    c = Circuit()
+    c = Circuit(xcarry)
     count = N1 * N2
     samples = []
     for k in range(count):
@@ -261,12 +279,12 @@ def fft_circuit(N1, N2, F, f):
     return c
 
 
-def word_circuit(kind, F, f=0, w=None):
+def word_circuit(kind, F, f=0, w=None, xcarry=False):
     """Small circuits over two input words (x, y) for the arithmetic pins.
 
     kind: 'add', 'sub' (x op y), 'mul' (x times plaintext w, fixed point f).
     """
-    c = Circuit()
+    c = Circuit(xcarry)
     x = [c.new_input() for _ in range(F)]
     y = [c.new_input() for _ in range(F)]
     if kind == "add":
@@ -283,8 +301,9 @@ def word_circuit(kind, F, f=0, w=None):
 
 
 def stats(c):
-    """Counts of each gate kind and of ciphertext products (AND/XOR/OR)."""
-    s = {"NOT": 0, "AND": 0, "XOR": 0, "OR": 0}
+    """Counts of each gate kind and of ciphertext products (AND/XOR/OR;
+    XADD and NOT are linear)."""
+    s = {"NOT": 0, "AND": 0, "XOR": 0, "OR": 0, "XADD": 0}
     for op, *_ in c.gates:
         s[op] += 1
     # One product per distinct (kind, A, B) after value numbering: an HA's XOR
@@ -306,7 +325,8 @@ def stats(c):
         if key not in seen:
             seen[key] = (o, 0)
         canon[o] = seen[key]
-        pairs.add(("OR" if op == "OR" else "HA", canon[A], canon[B]))
+        if op != "XADD":
+            pairs.add(("OR" if op == "OR" else "HA", canon[A], canon[B]))
     s["products"] = len(pairs)
     s["depth"] = max((c.depth[o] for _, _, _, o in c.gates), default=0)
     return s

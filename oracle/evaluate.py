@@ -16,7 +16,14 @@ TRUTH = {
     "AND": lambda a, b: a & b,
     "XOR": lambda a, b: a ^ b,
     "OR": lambda a, b: a | b,
+    "XADD": lambda a, b: _exclusive_sum(a, b),
 }
+
+
+def _exclusive_sum(a, b):
+    if a & b:
+        raise AssertionError("XADD applied to two set bits")
+    return a + b
 
 
 def eval_plain(c, in_bits):

@@ -48,6 +48,9 @@ GATE_CODES = {
     "XOR": (0, 1, 1, -2),   # a + b - 2ab
     "NOR": (1, -1, -1, 1),  # 1 - a - b + ab
     "XNOR": (1, -1, -1, 2),  # 1 - a - b + 2ab
+    # a + b for two bits that are never both 1 (the carries of a full adder):
+    # linear, no product; equals OR on every input it is applied to
+    "XADD": (0, 1, 1, 0),
 }
 
 

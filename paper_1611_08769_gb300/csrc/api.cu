@@ -107,9 +107,10 @@ int run_program(const Shape& s, const DeviceProgram& dp, const uint32_t* d_in, u
   a.err = dp.err;
   a.kernel = dp.kernel;
   for (size_t l = 0; l + 1 < dp.level_off.size(); l++) {
+    const uint64_t mid = dp.lin_start[l];
     a.desc = dp.desc + dp.level_off[l];
     a.aux = dp.aux + dp.level_off[l];
-    a.n = dp.level_off[l + 1] - dp.level_off[l];
+    a.n = mid - dp.level_off[l];
     const bool timed = tm && tm->on && a.n;
     if (timed) cudaEventRecord(tm->next(), st);
     int rc = launch_gates(a, st);
@@ -119,8 +120,21 @@ int run_program(const Shape& s, const DeviceProgram& dp, const uint32_t* d_in, u
       tm->launches++;
       tm->products += a.n;
     }
+    a.desc = dp.desc + mid;
+    a.aux = dp.aux + mid;
+    a.n = dp.level_off[l + 1] - mid;
+    if ((rc = launch_linear(a, st))) return rc;
   }
   return launch_fixups(dp.fix, dp.n_fix, a, st);
+}
+
+int launch_linear(const KArgs& a, cudaStream_t st) {
+  if (a.n == 0) return SFFT_OK;
+  const uint32_t tasks = a.Ng * (a.W / a.L), per = (tasks + 255) / 256;
+  k_linear<<<(unsigned)(a.n * per), 256, 0, st>>>(a, per);
+  count_launches(1);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SFFT_OK : cuda_fail(e, "linear gate launch");
 }
 
 int launch_fixups(const FixDesc* d_fix, uint64_t n, const KArgs& a, cudaStream_t st) {
@@ -142,6 +156,7 @@ int make_device_program(const Program& p, DeviceProgram* dp) {
   dp->fix = (FixDesc*)ptr;
   dp->n_fix = p.fix.size();
   dp->level_off = p.level_off;
+  dp->lin_start = p.lin_start;
   dp->scratch_slots = p.scratch_slots;
   cudaError_t e = cudaMalloc((void**)&dp->err, sizeof(int));
   if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
@@ -182,8 +197,10 @@ const char* sfft_version(void) { return "sfft-gb300 0.1 (sm_103a)"; }
 
 uint64_t sfft_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
-uint32_t sfft_min_ell(uint32_t N1, uint32_t N2, uint32_t F, uint32_t f, uint32_t n, uint32_t chi) {
+uint32_t sfft_min_ell(uint32_t N1, uint32_t N2, uint32_t F, uint32_t f, uint32_t n, uint32_t chi,
+                      uint32_t flags) {
   Circuit c;
+  c.xcarry = (flags & SFFT_PLAN_XCARRY) != 0;
   if (!build_fft(&c, N1, N2, F, f)) return 0;
   for (uint32_t ell = 32; ell <= 8192; ell += 32) {
     sfft_params p{n, ell, (n + 1) * ell, chi};
@@ -202,6 +219,7 @@ int sfft_plan_create(const sfft_params* p, uint32_t N1, uint32_t N2, uint32_t F,
   if (!pl) return fail(SFFT_ENOMEM, "host allocation failed");
   int rc = make_shape(p, &pl->s, false);
   if (rc) return rc;
+  pl->circuit.xcarry = (flags & SFFT_PLAN_XCARRY) != 0;
   if (!build_fft(&pl->circuit, N1, N2, F, f))
     return fail(SFFT_EINVAL, "N1, N2 must be powers of two, 2 <= F <= 48, f < F");
   compile(pl->circuit, pl->s, &pl->prog);
@@ -233,6 +251,7 @@ int sfft_plan_info_get(const sfft_plan* pl, sfft_plan_info* info) {
   info->gates_xor = pl->circuit.n_xor;
   info->gates_or = pl->circuit.n_or;
   info->gates_not = pl->circuit.n_not;
+  info->gates_xadd = pl->circuit.n_xadd;
   info->products = pl->prog.products;
   info->levels = pl->prog.level_off.size() - 1;
   info->max_level_width = pl->prog.max_width;

@@ -45,27 +45,36 @@ void merge_programs(const std::vector<Program>& parts, const std::vector<std::ar
   out->aux.clear();
   out->fix.clear();
   out->level_off.assign(1, 0);
+  out->lin_start.clear();
   out->max_width = 0;
   out->products = 0;
   out->noise_ok = true;
   out->noise_bits = 0;
   for (size_t l = 0; l < levels; l++) {
+    // every request's products of level l, then every request's linear gates
     const uint64_t before = out->desc.size();
-    for (size_t r = 0; r < parts.size(); r++) {
-      const Program& p = parts[r];
-      if (l + 1 >= p.level_off.size()) continue;
-      for (uint64_t g = p.level_off[l]; g < p.level_off[l + 1]; g++) {
-        GateDesc d = p.desc[g];
-        d.a = shift_ref(d.a, off[r].data());
-        d.b = shift_ref(d.b, off[r].data());
-        d.o0 = shift_ref(d.o0, off[r].data());
-        d.o1 = shift_ref(d.o1, off[r].data());
-        out->desc.push_back(d);
-        out->aux.push_back(p.aux[g]);
+    for (int phase = 0; phase < 2; phase++) {
+      if (phase == 1) out->lin_start.push_back(out->desc.size());
+      for (size_t r = 0; r < parts.size(); r++) {
+        const Program& p = parts[r];
+        if (l + 1 >= p.level_off.size()) continue;
+        const uint64_t g0 = phase ? p.lin_start[l] : p.level_off[l];
+        const uint64_t g1 = phase ? p.level_off[l + 1] : p.lin_start[l];
+        for (uint64_t g = g0; g < g1; g++) {
+          GateDesc d = p.desc[g];
+          d.a = shift_ref(d.a, off[r].data());
+          d.b = shift_ref(d.b, off[r].data());
+          d.o0 = shift_ref(d.o0, off[r].data());
+          d.o1 = shift_ref(d.o1, off[r].data());
+          out->desc.push_back(d);
+          out->aux.push_back(p.aux[g]);
+        }
       }
     }
+    const uint64_t width = out->lin_start.back() - before;
     out->level_off.push_back(out->desc.size());
-    out->max_width = std::max<uint64_t>(out->max_width, out->desc.size() - before);
+    out->max_width = std::max<uint64_t>(out->max_width, width);
+    out->products += width;
   }
   for (size_t r = 0; r < parts.size(); r++) {
     for (FixDesc f : parts[r].fix) {
@@ -76,7 +85,6 @@ void merge_programs(const std::vector<Program>& parts, const std::vector<std::ar
     out->noise_ok = out->noise_ok && parts[r].noise_ok;
     out->noise_bits = std::max(out->noise_bits, parts[r].noise_bits);
   }
-  out->products = out->desc.size();
 }
 
 // Graph replay of run_program for fixed pointers and stream.
@@ -150,6 +158,7 @@ int sfft_batch_create(const sfft_params* p, const sfft_request* reqs, uint32_t c
   uint64_t in = 0, outp = 0, scr = 0;
   for (uint32_t r = 0; r < count; r++) {
     Circuit c;
+    c.xcarry = (flags & SFFT_PLAN_XCARRY) != 0;
     if (!build_fft(&c, reqs[r].N1, reqs[r].N2, reqs[r].F, reqs[r].f))
       return fail(SFFT_EINVAL, "request " + std::to_string(r) + ": invalid FFT shape");
     Program prog;

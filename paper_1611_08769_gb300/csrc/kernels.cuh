@@ -142,6 +142,32 @@ __global__ void k_fixup(const FixDesc* fix, uint64_t n, KArgs a) {
   }
 }
 
+// Linear gates (c3 = 0): out = c0 P + c1 A + c2 B, limb carries inside each
+// element (mod 2^ell). Grid = gates x blocks over the Ng (n+1) (row, element)
+// tasks; one thread per task walks the element's L limbs.
+__global__ void k_linear(KArgs a, uint32_t blocks_per_gate) {
+  const uint64_t g = blockIdx.x / blocks_per_gate;
+  if (g >= a.n) return;
+  const GateDesc d = a.desc[g];
+  const uint32_t code = a.aux[g].code & 0xFFFFu;
+  const int c0 = nib(code, 0), c1 = nib(code, 1), c2 = nib(code, 2);
+  const uint32_t* A = resolve(a, d.a);
+  const uint32_t* B = resolve(a, d.b);
+  uint32_t* O = resolve(a, d.o0);
+  const uint32_t NP1 = a.W / a.L;
+  const uint32_t t = (blockIdx.x % blocks_per_gate) * blockDim.x + threadIdx.x;
+  if (d.o0 == REF_NONE || t >= a.Ng * NP1) return;
+  const uint32_t i = t / NP1, j = t % NP1;
+  const uint64_t base = (uint64_t)i * a.W + j * a.L;
+  int64_t carry = 0;
+  for (uint32_t l = 0; l < a.L; l++) {
+    const int64_t v = (int64_t)c0 * p_word(i, j, l, a.ell) + (int64_t)c1 * A[base + l] +
+                      (int64_t)c2 * B[base + l] + carry;
+    O[base + l] = (uint32_t)v;
+    carry = v >> 32;
+  }
+}
+
 // Row ell-1 of each ciphertext (what decryption reads).
 __global__ void k_gather_rows(const uint32_t* ct, uint64_t n, uint64_t ctw, uint32_t W,
                               uint32_t row, uint32_t* out) {

@@ -54,6 +54,7 @@ void Circuit::HA(Sig a, Sig b, Sig* s, Sig* c) {
     p.b = b;
   }
   p.is_or = false;
+  p.is_add = false;
   const uint64_t key = ((uint64_t)p.a << 32) | p.b;
   auto hit = memo_ha.find(key);
   if (hit != memo_ha.end()) {
@@ -88,6 +89,7 @@ Sig Circuit::OR(Sig a, Sig b) {
     p.b = b;
   }
   p.is_or = true;
+  p.is_add = false;
   p.out_and = 0;
   const uint64_t key = ((uint64_t)p.a << 32) | p.b;
   auto hit = memo_or.find(key);
@@ -101,11 +103,39 @@ Sig Circuit::OR(Sig a, Sig b) {
   return n;
 }
 
+Sig Circuit::XADD(Sig a, Sig b) {
+  if (a == SIG_ONE || b == SIG_ONE) return SIG_ONE;
+  if (a == SIG_ZERO) return b;
+  if (b == SIG_ZERO) return a;
+  uint32_t d = std::max(dep(a), dep(b));   // linear: no new multiplicative level
+  Product p;
+  if (dep(b) > dep(a)) {
+    p.a = b;
+    p.b = a;
+  } else {
+    p.a = a;
+    p.b = b;
+  }
+  p.is_or = false;
+  p.is_add = true;
+  p.out_and = 0;
+  const uint64_t key = ((uint64_t)p.a << 32) | p.b;
+  auto hit = memo_add.find(key);
+  if (hit != memo_add.end()) return products[hit->second].out_xor;
+  int32_t id = (int32_t)products.size();
+  memo_add[key] = id;
+  products.push_back(p);
+  uint32_t n = new_node(d, id);
+  products[id].out_xor = n;
+  n_xadd++;
+  return n;
+}
+
 void Circuit::FA(Sig a, Sig b, Sig c, Sig* s, Sig* co) {
   Sig s1, c1, c2;
   HA(a, b, &s1, &c1);
   HA(s1, c, s, &c2);
-  *co = OR(c1, c2);
+  *co = xcarry ? XADD(c1, c2) : OR(c1, c2);
 }
 
 std::vector<Sig> Circuit::ADD(const std::vector<Sig>& x, const std::vector<Sig>& y, Sig cin) {
@@ -339,6 +369,7 @@ struct Code {
 constexpr Code kXor = {0, 1, 1, -2};
 constexpr Code kAnd = {0, 0, 0, 1};
 constexpr Code kOr = {0, 1, 1, -1};
+constexpr Code kAdd = {0, 1, 1, 0};
 
 // Liveness: which products and nodes reach an output.
 void liveness(const Circuit& c, std::vector<char>* live_node, std::vector<char>* live_prod) {
@@ -377,7 +408,9 @@ uint32_t noise_bits(const Circuit& c, const Shape& s) {
       best = std::max(best, e.bits());
       E[node] = e;
     };
-    if (g.is_or) {
+    if (g.is_add) {
+      apply(g.out_xor, kAdd);
+    } else if (g.is_or) {
       apply(g.out_xor, kOr);
     } else {
       apply(g.out_xor, kXor);
@@ -417,14 +450,32 @@ void compile(const Circuit& c, const Shape& s, Program* prog) {
   const size_t nn = c.depth.size();
   std::vector<uint32_t> home(nn, REF_NONE);
   std::vector<uint32_t> last(nn, 0);
+  // Schedule level of every node: a product runs in level 1 + max of its
+  // inputs' levels; a linear gate runs after the products of the level of its
+  // inputs (one level later for an input that is itself a linear output of
+  // that level), and never before level 1.
+  std::vector<uint32_t> sl(nn, 0);
+  std::vector<uint32_t> plev(c.products.size(), 0);
+  std::vector<char> lin_node(nn, 0);
   uint32_t maxlev = 0;
   for (size_t p = 0; p < c.products.size(); p++) {
     if (!lp[p]) continue;
     const Product& g = c.products[p];
-    uint32_t lev = c.depth[g.out_xor ? g.out_xor : g.out_and];
+    const uint32_t na = sig_node(g.a), nb = sig_node(g.b);
+    uint32_t lev;
+    if (g.is_add)
+      lev = std::max(1u, std::max(sl[na] + lin_node[na], sl[nb] + lin_node[nb]));
+    else
+      lev = 1 + std::max(sl[na], sl[nb]);
+    plev[p] = lev;
+    for (uint32_t node : {g.out_xor, g.out_and})
+      if (node) {
+        sl[node] = lev;
+        lin_node[node] = g.is_add;
+      }
     maxlev = std::max(maxlev, lev);
-    last[sig_node(g.a)] = std::max(last[sig_node(g.a)], lev);
-    last[sig_node(g.b)] = std::max(last[sig_node(g.b)], lev);
+    last[na] = std::max(last[na], lev);
+    last[nb] = std::max(last[nb], lev);
   }
   for (size_t i = 0; i < c.inputs.size(); i++) home[c.inputs[i]] = make_ref(REG_IN, (uint32_t)i);
 
@@ -447,12 +498,12 @@ void compile(const Circuit& c, const Shape& s, Program* prog) {
     if (node) last[node] = std::max(last[node], maxlev + 1);
   }
 
-  // Group live products by level (creation order inside a level).
-  std::vector<std::vector<uint32_t>> by_level(maxlev + 1);
+  // Group live gates by level: products first, then linear gates (each in
+  // creation order, which is topological).
+  std::vector<std::vector<uint32_t>> by_level(maxlev + 1), lin_level(maxlev + 1);
   for (size_t p = 0; p < c.products.size(); p++) {
     if (!lp[p]) continue;
-    const Product& g = c.products[p];
-    by_level[c.depth[g.out_xor ? g.out_xor : g.out_and]].push_back((uint32_t)p);
+    (c.products[p].is_add ? lin_level : by_level)[plev[p]].push_back((uint32_t)p);
   }
   std::vector<std::vector<uint32_t>> release(maxlev + 2);
   std::vector<uint32_t> free_slots;
@@ -460,9 +511,13 @@ void compile(const Circuit& c, const Shape& s, Program* prog) {
   prog->desc.clear();
   prog->aux.clear();
   prog->level_off.assign(1, 0);
+  prog->lin_start.clear();
   prog->max_width = 0;
+  uint64_t n_products = 0;
   for (uint32_t lev = 1; lev <= maxlev; lev++) {
-    for (uint32_t p : by_level[lev]) {
+    for (int phase = 0; phase < 2; phase++) {
+    if (phase == 1) prog->lin_start.push_back(prog->desc.size());
+    for (uint32_t p : phase ? lin_level[lev] : by_level[lev]) {
       const Product& g = c.products[p];
       for (uint32_t node : {g.out_xor, g.out_and}) {
         if (!node || !ln[node] || home[node] != REF_NONE) continue;
@@ -482,7 +537,11 @@ void compile(const Circuit& c, const Shape& s, Program* prog) {
       d.a = home[sig_node(g.a)];
       d.b = home[sig_node(g.b)];
       uint16_t k0, k1 = 0;
-      if (g.is_or) {
+      if (g.is_add) {
+        d.o0 = ln[g.out_xor] ? home[g.out_xor] : REF_NONE;
+        d.o1 = REF_NONE;
+        k0 = adjusted(kAdd, negA, negB);
+      } else if (g.is_or) {
         d.o0 = ln[g.out_xor] ? home[g.out_xor] : REF_NONE;
         d.o1 = REF_NONE;
         k0 = adjusted(kOr, negA, negB);
@@ -493,10 +552,12 @@ void compile(const Circuit& c, const Shape& s, Program* prog) {
         k1 = adjusted(kAnd, negA, negB);
       }
       x.code = (uint32_t)k0 | ((uint32_t)k1 << 16);
-      x.flags = negA ? 1u : 0u;
+      x.flags = (negA && !g.is_add) ? 1u : 0u;   // complement A before BitDecomp (products only)
       prog->desc.push_back(d);
       prog->aux.push_back(x);
     }
+    }
+    n_products += by_level[lev].size();
     prog->level_off.push_back(prog->desc.size());
     prog->max_width = std::max<uint64_t>(prog->max_width, by_level[lev].size());
     for (uint32_t node : release[lev]) {
@@ -508,7 +569,7 @@ void compile(const Circuit& c, const Shape& s, Program* prog) {
   prog->n_inputs = c.inputs.size();
   prog->n_outputs = c.outputs.size();
   prog->scratch_slots = next_slot;
-  prog->products = prog->desc.size();
+  prog->products = n_products;
   prog->noise_bits = noise_bits(c, s);
   prog->noise_ok = prog->noise_bits <= s.ell - 2;
 }

@@ -19,6 +19,14 @@
 // NOT gates never reach the device: a signal carries a complement bit, the
 // kernel complements A before BitDecomp, and a complemented B is absorbed
 // into the gate's coefficients (BitDecomp(A)(P - B) = A - BitDecomp(A) B).
+//
+// Variant (Circuit::xcarry): the full adder's two carries are never both 1
+// (c1 = 1 forces s1 = 0, hence c2 = 0), so its carry is their sum, a linear
+// gate XADD = (0, 1, 1, 0) with no ciphertext product whose noise adds
+// instead of growing by Ng. XADD folds like OR (a constant 1 on one side
+// forces the other carry to 0). For the operand rule it is linear (depth =
+// max of its inputs); on the device it runs after the products of its
+// schedule level.
 #pragma once
 
 #include <cstdint>
@@ -38,9 +46,10 @@ inline bool sig_neg(Sig s) { return (s >> 31) != 0; }
 
 struct Product {
   Sig a, b;          // A (bit-decomposed) and B, already ordered by the depth rule
-  uint32_t out_xor;  // node of the XOR output (HA) or the OR output; 0 = none
+  uint32_t out_xor;  // node of the XOR output (HA), the OR or the XADD output; 0 = none
   uint32_t out_and;  // node of the AND output (HA only); 0 = none
   bool is_or;
+  bool is_add;       // linear exclusive sum (XADD): no ciphertext product
 };
 
 struct Circuit {
@@ -49,10 +58,11 @@ struct Circuit {
   std::vector<Product> products;
   std::vector<uint32_t> inputs;    // input nodes in ciphertext order
   std::vector<Sig> outputs;        // output signals in ciphertext order
-  uint64_t n_and = 0, n_xor = 0, n_or = 0, n_not = 0;   // logical gates before pruning
+  uint64_t n_and = 0, n_xor = 0, n_or = 0, n_not = 0, n_xadd = 0;   // logical gates before pruning
+  bool xcarry = false;             // full-adder carry as XADD instead of OR
   // Common subexpressions: identical (kind, A, B) gates give identical
   // ciphertexts, so each is computed once (bit-exact).
-  std::unordered_map<uint64_t, int32_t> memo_ha, memo_or;
+  std::unordered_map<uint64_t, int32_t> memo_ha, memo_or, memo_add;
 
   uint32_t new_node(uint32_t d, int32_t prod);
   uint32_t new_input();
@@ -61,6 +71,7 @@ struct Circuit {
   Sig NOT(Sig a);
   void HA(Sig a, Sig b, Sig* s, Sig* c);
   Sig OR(Sig a, Sig b);
+  Sig XADD(Sig a, Sig b);
   void FA(Sig a, Sig b, Sig c, Sig* s, Sig* co);
   std::vector<Sig> ADD(const std::vector<Sig>& x, const std::vector<Sig>& y, Sig cin);
   std::vector<Sig> SUB(const std::vector<Sig>& x, const std::vector<Sig>& y);
@@ -78,7 +89,10 @@ void twiddles(uint32_t N, uint32_t f, std::vector<int64_t>* wr, std::vector<int6
 struct Program {
   std::vector<GateDesc> desc;      // all gates, level by level
   std::vector<GateAux> aux;
-  std::vector<uint64_t> level_off; // level l = [level_off[l], level_off[l+1])
+  // level l = [level_off[l], level_off[l+1]): its products, then from
+  // lin_start[l] on the linear gates (XADD) that run after them
+  std::vector<uint64_t> level_off;
+  std::vector<uint64_t> lin_start;
   std::vector<FixDesc> fix;        // output fix-ups
   uint64_t n_inputs = 0, n_outputs = 0, scratch_slots = 0, products = 0;
   uint64_t max_width = 0;

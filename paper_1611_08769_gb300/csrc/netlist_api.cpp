@@ -17,10 +17,11 @@ using namespace sfft;
 
 namespace {
 
-int build(const sfft_params* p, uint32_t N1, uint32_t N2, uint32_t F, uint32_t f, Shape* s,
-          Circuit* c, Program* prog) {
+int build(const sfft_params* p, uint32_t N1, uint32_t N2, uint32_t F, uint32_t f, uint32_t flags,
+          Shape* s, Circuit* c, Program* prog) {
   int rc = make_shape(p, s, false);
   if (rc) return rc;
+  c->xcarry = (flags & SFFT_PLAN_XCARRY) != 0;
   if (!build_fft(c, N1, N2, F, f))
     return fail(SFFT_EINVAL, "N1, N2 must be powers of two, 2 <= F <= 48, f < F");
   compile(*c, *s, prog);
@@ -34,12 +35,12 @@ int nib(uint32_t code, int k) { return (int)((int32_t)(code << (28 - 4 * k)) >> 
 extern "C" {
 
 int sfft_circuit_info(const sfft_params* p, uint32_t N1, uint32_t N2, uint32_t F, uint32_t f,
-                      sfft_plan_info* info) {
+                      uint32_t flags, sfft_plan_info* info) {
   if (!info) return fail(SFFT_EINVAL, "info is NULL");
   Shape s;
   Circuit c;
   Program prog;
-  int rc = build(p, N1, N2, F, f, &s, &c, &prog);
+  int rc = build(p, N1, N2, F, f, flags, &s, &c, &prog);
   if (rc) return rc;
   std::memset(info, 0, sizeof(*info));
   info->inputs = prog.n_inputs;
@@ -48,6 +49,7 @@ int sfft_circuit_info(const sfft_params* p, uint32_t N1, uint32_t N2, uint32_t F
   info->gates_xor = c.n_xor;
   info->gates_or = c.n_or;
   info->gates_not = c.n_not;
+  info->gates_xadd = c.n_xadd;
   info->products = prog.products;
   info->levels = prog.level_off.size() - 1;
   info->max_level_width = prog.max_width;
@@ -78,12 +80,12 @@ int sfft_circuit_info(const sfft_params* p, uint32_t N1, uint32_t N2, uint32_t F
 }
 
 int sfft_program_eval_plain(const sfft_params* p, uint32_t N1, uint32_t N2, uint32_t F,
-                            uint32_t f, const uint8_t* h_in_bits, uint8_t* h_out_bits) {
+                            uint32_t f, uint32_t flags, const uint8_t* h_in_bits, uint8_t* h_out_bits) {
   if (!h_in_bits || !h_out_bits) return fail(SFFT_EINVAL, "null argument");
   Shape s;
   Circuit c;
   Program prog;
-  int rc = build(p, N1, N2, F, f, &s, &c, &prog);
+  int rc = build(p, N1, N2, F, f, flags, &s, &c, &prog);
   if (rc) return rc;
   std::vector<int> reg[3];
   reg[REG_SCRATCH].assign(prog.scratch_slots, -1);

@@ -18,6 +18,7 @@ struct DeviceProgram {
   FixDesc* fix = nullptr;
   uint64_t n_fix = 0;
   std::vector<uint64_t> level_off;
+  std::vector<uint64_t> lin_start;   // per level: first linear gate (after its products)
   uint64_t scratch_slots = 0;
   int* err = nullptr;            // device error word of the kernels
   uint32_t kernel = 0;           // KERNEL_AUTO / KERNEL_INT / KERNEL_TC
@@ -34,6 +35,8 @@ int cuda_fail(cudaError_t e, const char* what);
 int upload(const void* h, size_t bytes, void** d);
 KArgs make_args(const Shape& s);
 int launch_gates(const KArgs& a, cudaStream_t st);
+// Linear gates (no ciphertext product) of one level.
+int launch_linear(const KArgs& a, cudaStream_t st);
 // Output fix-ups (copies, complements, constants) of n entries.
 int launch_fixups(const FixDesc* d_fix, uint64_t n, const KArgs& a, cudaStream_t st);
 // Process-wide count of this library's kernel launches (sfft_launch_count).

@@ -126,6 +126,7 @@ struct sfft_server {
   int* err = nullptr;
   cudaStream_t stream = nullptr;
   bool tc = false;
+  bool xcarry = false;             // exclusive-carry full adders in every circuit
 
   std::map<sfft::Shape4, std::unique_ptr<sfft::Program>> programs;
   std::mutex mu;
@@ -224,32 +225,38 @@ int ensure_tick_capacity(sfft_server* sv, uint64_t n) {
 // One tick (worker thread, lock not held): the next level of every active request.
 int tick(sfft_server* sv, std::vector<std::shared_ptr<Request>>& act) {
   cudaStream_t st = sv->stream;
-  uint64_t n = 0;
-  for (auto& r : act) {
-    const Program& p = *r->prog;
-    if (r->level + 1 < p.level_off.size()) n += p.level_off[r->level + 1] - p.level_off[r->level];
-  }
-  int rc = ensure_tick_capacity(sv, n);
-  if (rc) return rc;
-  uint64_t at = 0;
+  // the level's products of every active request, then their linear gates
+  uint64_t n = 0, nprod = 0;
   for (auto& r : act) {
     const Program& p = *r->prog;
     if (r->level + 1 >= p.level_off.size()) continue;
-    const uint64_t b = p.level_off[r->level], cnt = p.level_off[r->level + 1] - b;
-    if (cnt) {
-      cudaMemcpyAsync(sv->tick_desc + at, sv->dpool + r->dbase + b, cnt * sizeof(GateDesc),
-                      cudaMemcpyDeviceToDevice, st);
-      cudaMemcpyAsync(sv->tick_aux + at, sv->apool + r->dbase + b, cnt * sizeof(GateAux),
-                      cudaMemcpyDeviceToDevice, st);
+    n += p.level_off[r->level + 1] - p.level_off[r->level];
+    nprod += p.lin_start[r->level] - p.level_off[r->level];
+  }
+  int rc = ensure_tick_capacity(sv, n);
+  if (rc) return rc;
+  uint64_t at[2] = {0, nprod};
+  for (auto& r : act) {
+    const Program& p = *r->prog;
+    if (r->level + 1 >= p.level_off.size()) continue;
+    const uint64_t cut[3] = {p.level_off[r->level], p.lin_start[r->level], p.level_off[r->level + 1]};
+    for (int ph = 0; ph < 2; ph++) {
+      const uint64_t b = cut[ph], cnt = cut[ph + 1] - cut[ph];
+      if (cnt) {
+        cudaMemcpyAsync(sv->tick_desc + at[ph], sv->dpool + r->dbase + b, cnt * sizeof(GateDesc),
+                        cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(sv->tick_aux + at[ph], sv->apool + r->dbase + b, cnt * sizeof(GateAux),
+                        cudaMemcpyDeviceToDevice, st);
+      }
+      at[ph] += cnt;
     }
-    at += cnt;
     r->level++;
   }
   if (n) {
     KArgs a = make_args(sv->s);
     a.desc = sv->tick_desc;
     a.aux = sv->tick_aux;
-    a.n = n;
+    a.n = nprod;
     a.base[REG_SCRATCH] = sv->arena;
     a.base[REG_IN] = sv->arena;
     a.base[REG_OUT] = sv->arena;
@@ -257,6 +264,10 @@ int tick(sfft_server* sv, std::vector<std::shared_ptr<Request>>& act) {
     a.kernel = KERNEL_AUTO;
     a.bx = sv->bx;
     if ((rc = launch_gates(a, st))) return rc;
+    a.desc = sv->tick_desc + nprod;
+    a.aux = sv->tick_aux + nprod;
+    a.n = n - nprod;
+    if ((rc = launch_linear(a, st))) return rc;
   }
   sv->ticks++;
   sv->tick_gates += n;
@@ -357,7 +368,7 @@ using namespace sfft;
 extern "C" {
 
 int sfft_server_create(const sfft_params* p, uint64_t hbm_budget_bytes, uint32_t max_active,
-                       sfft_server** out) {
+                       uint32_t flags, sfft_server** out) {
   if (!out) return fail(SFFT_EINVAL, "out is NULL");
   *out = nullptr;
   std::unique_ptr<sfft_server> sv(new (std::nothrow) sfft_server);
@@ -365,6 +376,7 @@ int sfft_server_create(const sfft_params* p, uint64_t hbm_budget_bytes, uint32_t
   int rc = make_shape(p, &sv->s, false);
   if (rc) return rc;
   sv->max_active = max_active ? max_active : 64;
+  sv->xcarry = (flags & SFFT_PLAN_XCARRY) != 0;
   const uint64_t ctb = sv->s.ctw * 4;
   KArgs k = make_args(sv->s);
   sv->tc = tc_supported(k);
@@ -409,6 +421,7 @@ int sfft_server_submit(sfft_server* sv, const sfft_request* req, const uint32_t*
   auto it = sv->programs.find(shape);
   if (it == sv->programs.end()) {
     Circuit c;
+    c.xcarry = sv->xcarry;
     if (!build_fft(&c, req->N1, req->N2, req->F, req->f))
       return fail(SFFT_EINVAL, "invalid FFT shape");
     std::unique_ptr<Program> prog(new Program);

@@ -24,7 +24,7 @@ class sfft_plan_info(ctypes.Structure):
                 ("gates_or", c_u64), ("gates_not", c_u64), ("products", c_u64), ("levels", c_u64),
                 ("max_level_width", c_u64), ("scratch_slots", c_u64), ("scratch_bytes", c_u64),
                 ("ct_words", c_u64), ("noise_bits", c_u32), ("noise_ok", c_u32),
-                ("gate_kernel", c_u32), ("tc_columns", c_u32)]
+                ("gate_kernel", c_u32), ("tc_columns", c_u32), ("gates_xadd", c_u64)]
 
 
 P = ctypes.POINTER
@@ -44,7 +44,7 @@ SIGNATURES = {
     "sfft_decrypt": (c_i32, [c_void_p, c_u32_p, c_u64, c_u64, c_u32, c_u32, c_double_p,
                              c_double_p, c_i64_p]),
     "sfft_gather_dec_rows": (c_i32, [P(sfft_params), c_void_p, c_u64, c_void_p, c_void_p]),
-    "sfft_min_ell": (c_u32, [c_u32, c_u32, c_u32, c_u32, c_u32, c_u32]),
+    "sfft_min_ell": (c_u32, [c_u32, c_u32, c_u32, c_u32, c_u32, c_u32, c_u32]),
     "sfft_plan_create": (c_i32, [P(sfft_params), c_u32, c_u32, c_u32, c_u32, c_u32, P(c_void_p)]),
     "sfft_plan_info_get": (c_i32, [c_void_p, P(sfft_plan_info)]),
     "sfft_plan_free": (None, [c_void_p]),
@@ -55,8 +55,10 @@ SIGNATURES = {
     "sfft_noalloc_scratch_bytes": (c_u64, []),
     "sfft_plan_set_timing": (c_i32, [c_void_p, ctypes.c_int]),
     "sfft_plan_timing": (c_i32, [c_void_p, c_double_p, P(c_u64), P(c_u64)]),
-    "sfft_circuit_info": (c_i32, [P(sfft_params), c_u32, c_u32, c_u32, c_u32, P(sfft_plan_info)]),
-    "sfft_program_eval_plain": (c_i32, [P(sfft_params), c_u32, c_u32, c_u32, c_u32, c_u8_p, c_u8_p]),
+    "sfft_circuit_info": (c_i32, [P(sfft_params), c_u32, c_u32, c_u32, c_u32, c_u32,
+                                  P(sfft_plan_info)]),
+    "sfft_program_eval_plain": (c_i32, [P(sfft_params), c_u32, c_u32, c_u32, c_u32, c_u32, c_u8_p,
+                                        c_u8_p]),
     "sfft_gate_level": (c_i32, [P(sfft_params), c_void_p, c_void_p, c_void_p, c_void_p, c_u16_p,
                                 c_u16_p, c_u8_p, c_u64, c_u32, c_void_p]),
     "sfft_plan_check": (c_i32, [c_void_p, c_void_p]),
@@ -84,7 +86,7 @@ class sfft_server_stats(ctypes.Structure):
 
 
 SIGNATURES.update({
-    "sfft_server_create": (c_i32, [P(sfft_params), c_u64, c_u32, P(c_void_p)]),
+    "sfft_server_create": (c_i32, [P(sfft_params), c_u64, c_u32, c_u32, P(c_void_p)]),
     "sfft_server_submit": (c_i32, [c_void_p, P(sfft_request), c_void_p, c_void_p, P(c_u64)]),
     "sfft_server_wait": (c_i32, [c_void_p, c_u64, c_u32, c_double_p]),
     "sfft_server_get_stats": (c_i32, [c_void_p, P(sfft_server_stats)]),

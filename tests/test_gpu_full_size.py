@@ -5,7 +5,8 @@ tensor-core product). The encrypted run is too large for the oracle to evaluate 
 (~3,400 s on 16 cores), so every one of the 2048 output ciphertexts is decrypted with the
 oracle's keys and compared with the oracle's closed-form integer FFT of the same quantized
 inputs, and the exact noise of sampled outputs is checked against the static bound. Single
-gates at ell = 1056 are compared ciphertext for ciphertext in test_gpu_parity."""
+gates at ell = 1056 are compared ciphertext for ciphertext in test_gpu_parity. The same
+runs for the exclusive-carry circuit variant at its own smallest ell (768)."""
 import numpy as np
 import pytest
 
@@ -36,10 +37,11 @@ class _Row:
         return self.data
 
 
-def test_full_size_fft_decrypts_to_closed_form():
+@pytest.mark.parametrize("xcarry,ell_expected", [(False, 1056), (True, 768)])
+def test_full_size_fft_decrypts_to_closed_form(xcarry, ell_expected):
     N, F, f = 64, 16, 8
-    ell = sf.min_ell(N, 1, F, f, n=1, chi=1)
-    assert ell == 1056
+    ell = sf.min_ell(N, 1, F, f, n=1, chi=1, xcarry=xcarry)
+    assert ell == ell_expected
     sp = sf.param_set("P1", ell)
     p = gsw.Params(sp.n, sp.ell, sp.m, sp.chi)
     key_seed, enc_seed = 21, 5
@@ -47,7 +49,7 @@ def test_full_size_fft_decrypts_to_closed_form():
 
     keys = sf.keygen(sp, key_seed)
     pub = torch.from_numpy(keys.public().view(np.int32)).cuda()
-    batch = sf.Batch(sp, [(N, 1, F, f)])
+    batch = sf.Batch(sp, [(N, 1, F, f)], sf.PLAN_XCARRY if xcarry else 0)
     info = batch.info
     assert info["gate_kernel"] == sf.KERNEL_TC and info["noise_ok"] == 1
     cw = sf.ct_words(sp)

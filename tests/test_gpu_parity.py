@@ -156,6 +156,36 @@ def test_fft_noisy_leveled_parameters_bit_exact(flags):
     assert [gsw.decrypt(ko, ct) for ct in got] == evaluate.eval_plain(c, bits)
 
 
+@pytest.mark.parametrize("flags", [0, sf.PLAN_INT_KERNEL])
+def test_fft_exclusive_carry_variant_bit_exact(flags):
+    """The exclusive-carry circuit (linear carry gates between product levels)
+    at its own smallest ell, noisy chi = 1: tensor-core and integer kernels."""
+    N, F, f = 8, 8, 4
+    ell = sf.min_ell(N, 1, F, f, n=1, chi=1, xcarry=True)
+    sp = sf.param_set("P1", ell)
+    p = gsw.Params(sp.n, sp.ell, sp.m, sp.chi)
+    re_, im_ = signal_1d(N, -1, 1, 6)
+    keys = sf.keygen(sp, 6)
+    d_in = torch.zeros((N * 2 * F, sf.ct_words(sp)), dtype=torch.int32, device="cuda")
+    sf.encrypt_bits_device(sp, dev(keys.public()), re_, im_, F, f, 4, d_in)
+    plan, out = _run_plan(sp, N, 1, F, f, d_in, flags | sf.PLAN_XCARRY)
+    assert plan.info["gates_xadd"] > 0
+    got = host(out, (N * 2 * F, p.Ng, p.n + 1, p.L))
+    ko = gsw.Keys(p, 6)
+    c = circuit.fft_circuit(N, 1, F, f, xcarry=True)
+    cts, bits = [], []
+    xr = [fx.quantize(float(x), F, f) for x in re_]
+    xi = [fx.quantize(float(x), F, f) for x in im_]
+    for k in range(N):
+        for part, v in enumerate((xr[k], xi[k])):
+            for b, bit in enumerate(fx.to_bits(v, F)):
+                cts.append(gsw.encrypt(ko, bit, 4, (k * 2 + part) * F + b))
+                bits.append(bit)
+    want = evaluate.eval_encrypted(c, p, cts)
+    assert np.array_equal(got, want)
+    assert [gsw.decrypt(ko, ct) for ct in got] == evaluate.eval_plain(c, bits)
+
+
 def test_fft_2d_toy_parameters_bit_exact():
     N1, N2, F, f = 4, 4, 8, 3
     sp = sf.param_set("P0")

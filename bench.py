@@ -12,7 +12,9 @@ graph); the plain level-by-level evaluator is timed beside it.
 Other workloads (--config): fft8_8bit_toy (toy noise-free parameters),
 fft16x16_image_noisy (2-D row-column FFT of a 16 x 16 image, 10.6 words),
 batch256_p2 (256 independent 1-D FFTs, N in {16..128}, F in {16, 24}, four
-client key sets, one graph-replayed level-merged batch; noise-free ell 128).
+client key sets, one graph-replayed level-merged batch; noise-free ell 128),
+fft64_16bit_xcarry (the default workload built with exclusive-carry full
+adders, a circuit variant: fewer products, its own smaller ell).
 
 Keys beyond the base contract:
   roofline      the gate-product kernel against its peak (tensor or ALU)
@@ -49,6 +51,9 @@ CONFIGS = {
     "fft8_8bit_toy": dict(kind="fft", N1=8, N2=1, F=8, f=4, lo=-1.0, hi=1.0, pset="P0"),
     "fft16x16_image_noisy": dict(kind="fft", N1=16, N2=16, F=16, f=6, lo=None, hi=None, pset="P1"),
     "fft64_16bit_p2": dict(kind="fft", N1=64, N2=1, F=16, f=8, lo=-8.0, hi=8.0, pset="P2"),
+    # circuit variant: exclusive-carry full adders (linear carry gates, smaller ell)
+    "fft64_16bit_xcarry": dict(kind="fft", N1=64, N2=1, F=16, f=8, lo=-8.0, hi=8.0, pset="P1",
+                               xcarry=True),
     "batch256_p2": dict(kind="batch", count=256, pset="P2", key_sets=4),
     "serve_p2": dict(kind="serve", pset="P2", key_sets=8, requests=400, calib=48),
 }
@@ -174,9 +179,13 @@ def roofline(params, gate_kernel, gate_ms, launches, gates_timed, tc_columns=0):
             "peak_source": "derived: 152 SMs x 128 INT32 lanes x 2.07 GHz"}
 
 
-def params_for(sf, pset, dims_list):
+def xcarry_of(cfg):
+    return bool(CONFIGS[cfg].get("xcarry", False))
+
+
+def params_for(sf, pset, dims_list, xcarry=False):
     if pset == "P1":
-        ell = max(sf.min_ell(*d, n=1, chi=1) for d in dims_list)
+        ell = max(sf.min_ell(*d, n=1, chi=1, xcarry=xcarry) for d in dims_list)
         return sf.param_set("P1", ell)
     return sf.param_set(pset)
 
@@ -187,7 +196,7 @@ def fft_workload(cfg):
     from synthetic import image_2d, signal_1d
     c = CONFIGS[cfg]
     dims = (c["N1"], c["N2"], c["F"], c["f"])
-    params = params_for(sf, c["pset"], [dims])
+    params = params_for(sf, c["pset"], [dims], xcarry_of(cfg))
     if c["N2"] == 1:
         re_, im_ = signal_1d(c["N1"], c["lo"], c["hi"], seed=0)
     else:
@@ -223,7 +232,7 @@ def workload(cfg):
     return fft_workload(cfg)
 
 
-def cpu_oracle_sample(params, items, budget_s):
+def cpu_oracle_sample(params, items, budget_s, xcarry=False):
     """Oracle on a bounded prefix of the first request's circuit.
 
     Returns (FFTs/s, gates/s, description). FFT time is the per-gate time
@@ -231,7 +240,7 @@ def cpu_oracle_sample(params, items, budget_s):
     from oracle import circuit, fixedpoint as fx, gsw
     p = gsw.Params(params.n, params.ell, params.m, params.chi)
     (N1, N2, F, f), re_, im_, _, _ = items[0]
-    c = circuit.fft_circuit(N1, N2, F, f)
+    c = circuit.fft_circuit(N1, N2, F, f, xcarry=xcarry)
     keys = gsw.Keys(p, 0)
     cts = {}
     zero, one = gsw.zero_ct(p), gsw.one_ct(p)
@@ -260,7 +269,7 @@ def cpu_oracle_sample(params, items, budget_s):
             break
     per_gate = dt / done
     shapes = sorted({d for d, *_ in items})
-    sizes = {d: (len(c.gates) if d == (N1, N2, F, f) else len(circuit.fft_circuit(*d).gates))
+    sizes = {d: (len(c.gates) if d == (N1, N2, F, f) else len(circuit.fft_circuit(*d, xcarry=xcarry).gates))
              for d in shapes}
     mean_gates = sum(sizes[d] for d, *_ in items) / len(items)
     fft_s = per_gate * mean_gates
@@ -278,7 +287,7 @@ def run_reference(args, rank, world):
     vals = []
     detail = ""
     for s in range(args.warmup + args.steps):
-        fps, gps, detail = cpu_oracle_sample(params, items, budget)
+        fps, gps, detail = cpu_oracle_sample(params, items, budget, xcarry_of(args.config))
         if s >= args.warmup:
             vals.append(fps)
     v = statistics.mean(vals)
@@ -296,6 +305,8 @@ def run_reference(args, rank, world):
 def config_json(cfg, params, items):
     out = {"workload": cfg, "n": params.n, "ell": params.ell, "m": params.m, "chi": params.chi,
            "requests": len(items)}
+    if xcarry_of(cfg):
+        out["circuit"] = "exclusive-carry full adders (variant; carries are linear gates)"
     if len(items) == 1:
         (N1, N2, F, f), *_ = items[0]
         out.update({"N1": N1, "N2": N2, "F": F, "f": f})
@@ -451,6 +462,8 @@ def main():
     sfbuild.build()
     params, items = workload(args.config)
     flags = sf.PLAN_INT_KERNEL if args.kernel == "int" else 0
+    if xcarry_of(args.config):
+        flags |= sf.PLAN_XCARRY
     cw = sf.ct_words(params)
     reqs = [d for d, *_ in items]
 
@@ -546,7 +559,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        fps, gps, detail = cpu_oracle_sample(params, items, args.cpu_seconds)
+        fps, gps, detail = cpu_oracle_sample(params, items, args.cpu_seconds, xcarry_of(args.config))
         cpu = {"value": fps, "unit": "FFT/s", "cores": os.cpu_count(), "kind": "oracle",
                "sample": detail, "gates_per_s": gps}
 

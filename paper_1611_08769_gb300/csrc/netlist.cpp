@@ -516,46 +516,46 @@ void compile(const Circuit& c, const Shape& s, Program* prog) {
   uint64_t n_products = 0;
   for (uint32_t lev = 1; lev <= maxlev; lev++) {
     for (int phase = 0; phase < 2; phase++) {
-    if (phase == 1) prog->lin_start.push_back(prog->desc.size());
-    for (uint32_t p : phase ? lin_level[lev] : by_level[lev]) {
-      const Product& g = c.products[p];
-      for (uint32_t node : {g.out_xor, g.out_and}) {
-        if (!node || !ln[node] || home[node] != REF_NONE) continue;
-        uint32_t slot;
-        if (!free_slots.empty()) {
-          slot = free_slots.back();
-          free_slots.pop_back();
-        } else {
-          slot = next_slot++;
+      if (phase == 1) prog->lin_start.push_back(prog->desc.size());
+      for (uint32_t p : phase ? lin_level[lev] : by_level[lev]) {
+        const Product& g = c.products[p];
+        for (uint32_t node : {g.out_xor, g.out_and}) {
+          if (!node || !ln[node] || home[node] != REF_NONE) continue;
+          uint32_t slot;
+          if (!free_slots.empty()) {
+            slot = free_slots.back();
+            free_slots.pop_back();
+          } else {
+            slot = next_slot++;
+          }
+          home[node] = make_ref(REG_SCRATCH, slot);
+          release[last[node]].push_back(node);
         }
-        home[node] = make_ref(REG_SCRATCH, slot);
-        release[last[node]].push_back(node);
+        GateDesc d;
+        GateAux x;
+        bool negA = sig_neg(g.a), negB = sig_neg(g.b);
+        d.a = home[sig_node(g.a)];
+        d.b = home[sig_node(g.b)];
+        uint16_t k0, k1 = 0;
+        if (g.is_add) {
+          d.o0 = ln[g.out_xor] ? home[g.out_xor] : REF_NONE;
+          d.o1 = REF_NONE;
+          k0 = adjusted(kAdd, negA, negB);
+        } else if (g.is_or) {
+          d.o0 = ln[g.out_xor] ? home[g.out_xor] : REF_NONE;
+          d.o1 = REF_NONE;
+          k0 = adjusted(kOr, negA, negB);
+        } else {
+          d.o0 = (g.out_xor && ln[g.out_xor]) ? home[g.out_xor] : REF_NONE;
+          d.o1 = (g.out_and && ln[g.out_and]) ? home[g.out_and] : REF_NONE;
+          k0 = adjusted(kXor, negA, negB);
+          k1 = adjusted(kAnd, negA, negB);
+        }
+        x.code = (uint32_t)k0 | ((uint32_t)k1 << 16);
+        x.flags = (negA && !g.is_add) ? 1u : 0u;   // complement A before BitDecomp (products only)
+        prog->desc.push_back(d);
+        prog->aux.push_back(x);
       }
-      GateDesc d;
-      GateAux x;
-      bool negA = sig_neg(g.a), negB = sig_neg(g.b);
-      d.a = home[sig_node(g.a)];
-      d.b = home[sig_node(g.b)];
-      uint16_t k0, k1 = 0;
-      if (g.is_add) {
-        d.o0 = ln[g.out_xor] ? home[g.out_xor] : REF_NONE;
-        d.o1 = REF_NONE;
-        k0 = adjusted(kAdd, negA, negB);
-      } else if (g.is_or) {
-        d.o0 = ln[g.out_xor] ? home[g.out_xor] : REF_NONE;
-        d.o1 = REF_NONE;
-        k0 = adjusted(kOr, negA, negB);
-      } else {
-        d.o0 = (g.out_xor && ln[g.out_xor]) ? home[g.out_xor] : REF_NONE;
-        d.o1 = (g.out_and && ln[g.out_and]) ? home[g.out_and] : REF_NONE;
-        k0 = adjusted(kXor, negA, negB);
-        k1 = adjusted(kAnd, negA, negB);
-      }
-      x.code = (uint32_t)k0 | ((uint32_t)k1 << 16);
-      x.flags = (negA && !g.is_add) ? 1u : 0u;   // complement A before BitDecomp (products only)
-      prog->desc.push_back(d);
-      prog->aux.push_back(x);
-    }
     }
     n_products += by_level[lev].size();
     prog->level_off.push_back(prog->desc.size());

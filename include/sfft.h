@@ -123,8 +123,8 @@ int sfft_gather_dec_rows(const sfft_params* p, const uint32_t* d_ct, uint64_t n_
 /* Smallest ell (multiple of 32, <= 8192) for which the static worst-case
  * noise bound of the FFT circuit stays below q/4 with m = Ng and error bound
  * chi (the leveled reading of the scheme's noise management; Sec. 5 ends by
- * pointing at refreshing). flags: the circuit variant (SFFT_PLAN_XCARRY).
- * 0 if none. */
+ * pointing at refreshing). flags: the circuit variant (SFFT_PLAN_XCARRY or
+ * SFFT_PLAN_NAND). 0 if none or if both variants are set. */
 uint32_t sfft_min_ell(uint32_t N1, uint32_t N2, uint32_t F, uint32_t f, uint32_t n,
                       uint32_t chi, uint32_t flags);
 
@@ -160,6 +160,14 @@ typedef struct sfft_plan_info {
  * smaller ell (sfft_min_ell with the same flag); different ciphertexts. Linear
  * gates run after the products of their level. */
 #define SFFT_PLAN_XCARRY 8u
+/* Circuit variant (the paper's literal construction, Lemma 4 and Sec. 7's gate
+ * counts): every gate that survives constant folding is built from GSW NAND
+ * gates (1, 0, 0, -1), one ciphertext product each: NOT a = NAND(a, a), AND =
+ * NOT(NAND), OR = NAND(NOT a, NOT b), a half adder t = NAND(a, b), XOR =
+ * NAND(NAND(a, t), NAND(b, t)), AND = NAND(t, t). Several times the products
+ * and a larger ell; decrypts to the same words. Exclusive with
+ * SFFT_PLAN_XCARRY (EINVAL). */
+#define SFFT_PLAN_NAND 16u
 int sfft_plan_create(const sfft_params* p, uint32_t N1, uint32_t N2, uint32_t F, uint32_t f,
                      uint32_t flags, sfft_plan** out);
 int sfft_plan_info_get(const sfft_plan* plan, sfft_plan_info* info);
@@ -186,7 +194,7 @@ int sfft_eval_fft_host(sfft_plan* plan, const uint32_t* h_in, uint32_t* h_out,
 
 /* Host-only statistics of the compiled circuit (no device memory touched):
  * fills every field of sfft_plan_info as sfft_plan_create would with the
- * same flags (only SFFT_PLAN_XCARRY changes the circuit). */
+ * same flags (only SFFT_PLAN_XCARRY and SFFT_PLAN_NAND change the circuit). */
 int sfft_circuit_info(const sfft_params* p, uint32_t N1, uint32_t N2, uint32_t F, uint32_t f,
                       uint32_t flags, sfft_plan_info* info);
 
@@ -278,7 +286,8 @@ typedef struct sfft_server_stats {
   double p50_ms, p99_ms, max_ms;   /* submit-to-completion latency of completed requests */
 } sfft_server_stats;
 
-/* flags: SFFT_PLAN_XCARRY selects the exclusive-carry circuit for every request. */
+/* flags: SFFT_PLAN_XCARRY or SFFT_PLAN_NAND selects that circuit variant for
+ * every request. */
 int sfft_server_create(const sfft_params* p, uint64_t hbm_budget_bytes, uint32_t max_active,
                        uint32_t flags, sfft_server** out);
 /* Queues one request. h_in: its input ciphertexts (layout of sfft_eval_fft's

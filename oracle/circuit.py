@@ -43,6 +43,13 @@ choices the paper leaves open (all readings, stated in the design doc):
 
 Depth (for the operand rule): XADD, like NOT, is linear: the max of its inputs.
 
+NAND-only variant (``nand``, the paper's literal construction, Lemma 4 and
+Sec. 7's counts): constants fold first exactly as above; every remaining gate
+is made of GSW NAND gates (one product each, code (1, 0, 0, -1)): NOT a =
+NAND(a, a), AND = NOT(NAND(a, b)), OR = NAND(NOT a, NOT b), XOR =
+NAND(NAND(a, t), NAND(b, t)) with t = NAND(a, b); a half adder shares t
+between its XOR and its AND = NAND(t, t).
+
 Wires are non-negative ints; the trivial constants are ZERO = -1, ONE = -2.
 Input wire number (k * 2 + part) * F + bit holds bit ``bit`` of the real
 (part 0) or imaginary (part 1) word of sample k.
@@ -55,8 +62,11 @@ ZERO, ONE = -1, -2
 
 
 class Circuit:
-    def __init__(self, xcarry=False):
+    def __init__(self, xcarry=False, nand=False):
+        if xcarry and nand:
+            raise ValueError("the NAND-only circuit has no linear carry")
         self.xcarry = xcarry   # full-adder carry as XADD instead of OR
+        self.nand = nand       # every gate made of NAND gates
         self.gates = []      # (op, a, b, out); b is None for NOT
         self.depth = []      # per wire
         self.inputs = []
@@ -79,11 +89,17 @@ class Circuit:
         return w
 
     # -- gates with constant folding (Lemma 4) -----------------------------
+    def _nand(self, a, b):
+        """A GSW NAND gate on two non-constant wires (NAND-only variant)."""
+        return self._emit("NAND", a, b, 1 + max(self.d(a), self.d(b)))
+
     def NOT(self, a):
         if a == ZERO:
             return ONE
         if a == ONE:
             return ZERO
+        if self.nand:
+            return self._nand(a, a)
         return self._emit("NOT", a, None, self.d(a))
 
     def AND(self, a, b):
@@ -93,6 +109,8 @@ class Circuit:
             return b
         if b == ONE:
             return a
+        if self.nand:
+            return self.NOT(self._nand(a, b))
         return self._emit("AND", a, b, 1 + max(self.d(a), self.d(b)))
 
     def XOR(self, a, b):
@@ -104,6 +122,9 @@ class Circuit:
             return self.NOT(b)
         if b == ONE:
             return self.NOT(a)
+        if self.nand:
+            t = self._nand(a, b)
+            return self._nand(self._nand(a, t), self._nand(b, t))
         return self._emit("XOR", a, b, 1 + max(self.d(a), self.d(b)))
 
     def OR(self, a, b):
@@ -113,6 +134,8 @@ class Circuit:
             return b
         if b == ZERO:
             return a
+        if self.nand:
+            return self._nand(self.NOT(a), self.NOT(b))
         return self._emit("OR", a, b, 1 + max(self.d(a), self.d(b)))
 
     def XADD(self, a, b):
@@ -127,6 +150,9 @@ class Circuit:
 
     # -- adders (Lemmas 5-7) ---------------------------------------------
     def HA(self, a, b):
+        if self.nand and a not in (ZERO, ONE) and b not in (ZERO, ONE):
+            t = self._nand(a, b)
+            return self._nand(self._nand(a, t), self._nand(b, t)), self._nand(t, t)
         return self.XOR(a, b), self.AND(a, b)
 
     def FA(self, a, b, c):
@@ -242,7 +268,7 @@ def twiddles(N, f):
     return tw
 
 
-def fft_circuit(N1, N2, F, f, xcarry=False):
+def fft_circuit(N1, N2, F, f, xcarry=False, nand=False):
     """Circuit of a 1-D (N2 == 1) or row-column 2-D encrypted FFT.
 
     1-D: N1 samples. 2-D: an N1 x N2 image, sample k = r * N2 + c; all row
@@ -252,7 +278,7 @@ def fft_circuit(N1, N2, F, f, xcarry=False):
     for n in (N1, N2):
         if n < 1 or n & (n - 1):
             raise ValueError("FFT sizes must be powers of two")
-    c = Circuit(xcarry)
+    c = Circuit(xcarry, nand)
     count = N1 * N2
     samples = []
     for k in range(count):
@@ -279,12 +305,12 @@ def fft_circuit(N1, N2, F, f, xcarry=False):
     return c
 
 
-def word_circuit(kind, F, f=0, w=None, xcarry=False):
+def word_circuit(kind, F, f=0, w=None, xcarry=False, nand=False):
     """Small circuits over two input words (x, y) for the arithmetic pins.
 
     kind: 'add', 'sub' (x op y), 'mul' (x times plaintext w, fixed point f).
     """
-    c = Circuit(xcarry)
+    c = Circuit(xcarry, nand)
     x = [c.new_input() for _ in range(F)]
     y = [c.new_input() for _ in range(F)]
     if kind == "add":
@@ -303,7 +329,7 @@ def word_circuit(kind, F, f=0, w=None, xcarry=False):
 def stats(c):
     """Counts of each gate kind and of ciphertext products (AND/XOR/OR;
     XADD and NOT are linear)."""
-    s = {"NOT": 0, "AND": 0, "XOR": 0, "OR": 0, "XADD": 0}
+    s = {"NOT": 0, "AND": 0, "XOR": 0, "OR": 0, "XADD": 0, "NAND": 0}
     for op, *_ in c.gates:
         s[op] += 1
     # One product per distinct (kind, A, B) after value numbering: an HA's XOR
@@ -326,7 +352,7 @@ def stats(c):
             seen[key] = (o, 0)
         canon[o] = seen[key]
         if op != "XADD":
-            pairs.add(("OR" if op == "OR" else "HA", canon[A], canon[B]))
+            pairs.add((op if op in ("OR", "NAND") else "HA", canon[A], canon[B]))
     s["products"] = len(pairs)
     s["depth"] = max((c.depth[o] for _, _, _, o in c.gates), default=0)
     return s

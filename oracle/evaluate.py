@@ -17,6 +17,7 @@ TRUTH = {
     "XOR": lambda a, b: a ^ b,
     "OR": lambda a, b: a | b,
     "XADD": lambda a, b: _exclusive_sum(a, b),
+    "NAND": lambda a, b: 1 - (a & b),
 }
 
 

@@ -19,6 +19,7 @@ from .native import SfftError, check, lib, sfft_params, sfft_plan_info
 PLAN_ALLOW_NOISY = 1
 PLAN_INT_KERNEL = 2
 PLAN_XCARRY = 8   # circuit variant: exclusive-carry full adders (sfft.h SFFT_PLAN_XCARRY)
+PLAN_NAND = 16    # circuit variant: every gate built of NAND gates (sfft.h SFFT_PLAN_NAND)
 KERNEL_AUTO, KERNEL_INT, KERNEL_TC = 0, 1, 2
 
 __all__ = ["Params", "Keys", "Plan", "keygen", "encrypt_bits", "encrypt_bits_device", "decrypt",
@@ -132,23 +133,27 @@ def gather_dec_rows(params, d_ct, n_ct, d_rows, stream=None):
                                      _stream(stream)))
 
 
-def min_ell(N1, N2, F, f, n=1, chi=1, xcarry=False):
-    return int(lib().sfft_min_ell(N1, N2, F, f, n, chi, PLAN_XCARRY if xcarry else 0))
+def _variant(xcarry, nand):
+    return (PLAN_XCARRY if xcarry else 0) | (PLAN_NAND if nand else 0)
 
 
-def circuit_info(params, N1, N2, F, f, xcarry=False):
+def min_ell(N1, N2, F, f, n=1, chi=1, xcarry=False, nand=False):
+    return int(lib().sfft_min_ell(N1, N2, F, f, n, chi, _variant(xcarry, nand)))
+
+
+def circuit_info(params, N1, N2, F, f, xcarry=False, nand=False):
     """Host-only statistics of the compiled FFT circuit (sfft_circuit_info)."""
     info = sfft_plan_info()
-    check(lib().sfft_circuit_info(ctypes.byref(params), N1, N2, F, f, PLAN_XCARRY if xcarry else 0,
+    check(lib().sfft_circuit_info(ctypes.byref(params), N1, N2, F, f, _variant(xcarry, nand),
                                   ctypes.byref(info)))
     return {k: getattr(info, k) for k, _ in sfft_plan_info._fields_}
 
 
-def program_eval_plain(params, N1, N2, F, f, in_bits, xcarry=False):
+def program_eval_plain(params, N1, N2, F, f, in_bits, xcarry=False, nand=False):
     """Host-only plaintext run of the compiled device program (sfft_program_eval_plain)."""
     in_bits = np.ascontiguousarray(in_bits, dtype=np.uint8)
     out = np.zeros(len(in_bits), dtype=np.uint8)
-    check(lib().sfft_program_eval_plain(ctypes.byref(params), N1, N2, F, f, PLAN_XCARRY if xcarry else 0,
+    check(lib().sfft_program_eval_plain(ctypes.byref(params), N1, N2, F, f, _variant(xcarry, nand),
                                         in_bits.ctypes.data_as(native.c_u8_p),
                                         out.ctypes.data_as(native.c_u8_p)))
     return out

@@ -200,8 +200,7 @@ uint64_t sfft_launch_count(void) { return g_launches.load(std::memory_order_rela
 uint32_t sfft_min_ell(uint32_t N1, uint32_t N2, uint32_t F, uint32_t f, uint32_t n, uint32_t chi,
                       uint32_t flags) {
   Circuit c;
-  c.xcarry = (flags & SFFT_PLAN_XCARRY) != 0;
-  if (!build_fft(&c, N1, N2, F, f)) return 0;
+  if (!c.set_variant(flags) || !build_fft(&c, N1, N2, F, f)) return 0;
   for (uint32_t ell = 32; ell <= 8192; ell += 32) {
     sfft_params p{n, ell, (n + 1) * ell, chi};
     Shape s;
@@ -219,7 +218,8 @@ int sfft_plan_create(const sfft_params* p, uint32_t N1, uint32_t N2, uint32_t F,
   if (!pl) return fail(SFFT_ENOMEM, "host allocation failed");
   int rc = make_shape(p, &pl->s, false);
   if (rc) return rc;
-  pl->circuit.xcarry = (flags & SFFT_PLAN_XCARRY) != 0;
+  if (!pl->circuit.set_variant(flags))
+    return fail(SFFT_EINVAL, "SFFT_PLAN_XCARRY and SFFT_PLAN_NAND are exclusive");
   if (!build_fft(&pl->circuit, N1, N2, F, f))
     return fail(SFFT_EINVAL, "N1, N2 must be powers of two, 2 <= F <= 48, f < F");
   compile(pl->circuit, pl->s, &pl->prog);

@@ -158,7 +158,8 @@ int sfft_batch_create(const sfft_params* p, const sfft_request* reqs, uint32_t c
   uint64_t in = 0, outp = 0, scr = 0;
   for (uint32_t r = 0; r < count; r++) {
     Circuit c;
-    c.xcarry = (flags & SFFT_PLAN_XCARRY) != 0;
+    if (!c.set_variant(flags))
+      return fail(SFFT_EINVAL, "SFFT_PLAN_XCARRY and SFFT_PLAN_NAND are exclusive");
     if (!build_fft(&c, reqs[r].N1, reqs[r].N2, reqs[r].F, reqs[r].f))
       return fail(SFFT_EINVAL, "request " + std::to_string(r) + ": invalid FFT shape");
     Program prog;

@@ -8,6 +8,12 @@ namespace sfft {
 
 // ------------------------------------------------------------------ circuit
 
+bool Circuit::set_variant(uint32_t flags) {
+  xcarry = (flags & SFFT_PLAN_XCARRY) != 0;
+  nand = (flags & SFFT_PLAN_NAND) != 0;
+  return !(xcarry && nand);
+}
+
 uint32_t Circuit::new_node(uint32_t d, int32_t prod) {
   if (depth.empty()) {  // node 0: the constant zero
     depth.push_back(0);
@@ -26,7 +32,33 @@ uint32_t Circuit::new_input() {
 
 Sig Circuit::NOT(Sig a) {
   if (sig_node(a) != 0) n_not++;
+  if (nand && sig_node(a) != 0) return NAND(a, a);
   return a ^ SIG_ONE;
+}
+
+Sig Circuit::NAND(Sig a, Sig b) {
+  uint32_t d = 1 + std::max(dep(a), dep(b));
+  Product p;
+  if (dep(b) > dep(a)) {
+    p.a = b;
+    p.b = a;
+  } else {
+    p.a = a;
+    p.b = b;
+  }
+  p.is_or = false;
+  p.is_add = false;
+  p.is_nand = true;
+  p.out_and = 0;
+  const uint64_t key = ((uint64_t)p.a << 32) | p.b;
+  auto hit = memo_nand.find(key);
+  if (hit != memo_nand.end()) return products[hit->second].out_xor;
+  int32_t id = (int32_t)products.size();
+  memo_nand[key] = id;
+  products.push_back(p);
+  uint32_t n = new_node(d, id);
+  products[id].out_xor = n;
+  return n;
 }
 
 void Circuit::HA(Sig a, Sig b, Sig* s, Sig* c) {
@@ -44,6 +76,16 @@ void Circuit::HA(Sig a, Sig b, Sig* s, Sig* c) {
     *c = k ? x : SIG_ZERO;
     return;
   }
+  if (nand) {  // the sequence is explicit: argument evaluation order is unspecified
+    const Sig t = NAND(a, b);
+    const Sig u = NAND(a, t);
+    const Sig v = NAND(b, t);
+    *s = NAND(u, v);
+    *c = NAND(t, t);
+    n_xor++;
+    n_and++;
+    return;
+  }
   uint32_t d = 1 + std::max(dep(a), dep(b));
   Product p;
   if (dep(b) > dep(a)) {
@@ -55,6 +97,7 @@ void Circuit::HA(Sig a, Sig b, Sig* s, Sig* c) {
   }
   p.is_or = false;
   p.is_add = false;
+  p.is_nand = false;
   const uint64_t key = ((uint64_t)p.a << 32) | p.b;
   auto hit = memo_ha.find(key);
   if (hit != memo_ha.end()) {
@@ -79,6 +122,12 @@ Sig Circuit::OR(Sig a, Sig b) {
   if (a == SIG_ONE || b == SIG_ONE) return SIG_ONE;
   if (a == SIG_ZERO) return b;
   if (b == SIG_ZERO) return a;
+  if (nand) {
+    n_or++;
+    const Sig na = NOT(a);
+    const Sig nb = NOT(b);
+    return NAND(na, nb);
+  }
   uint32_t d = 1 + std::max(dep(a), dep(b));
   Product p;
   if (dep(b) > dep(a)) {
@@ -90,6 +139,7 @@ Sig Circuit::OR(Sig a, Sig b) {
   }
   p.is_or = true;
   p.is_add = false;
+  p.is_nand = false;
   p.out_and = 0;
   const uint64_t key = ((uint64_t)p.a << 32) | p.b;
   auto hit = memo_or.find(key);
@@ -118,6 +168,7 @@ Sig Circuit::XADD(Sig a, Sig b) {
   }
   p.is_or = false;
   p.is_add = true;
+  p.is_nand = false;
   p.out_and = 0;
   const uint64_t key = ((uint64_t)p.a << 32) | p.b;
   auto hit = memo_add.find(key);
@@ -370,6 +421,7 @@ constexpr Code kXor = {0, 1, 1, -2};
 constexpr Code kAnd = {0, 0, 0, 1};
 constexpr Code kOr = {0, 1, 1, -1};
 constexpr Code kAdd = {0, 1, 1, 0};
+constexpr Code kNand = {1, 0, 0, -1};
 
 // Liveness: which products and nodes reach an output.
 void liveness(const Circuit& c, std::vector<char>* live_node, std::vector<char>* live_prod) {
@@ -410,6 +462,8 @@ uint32_t noise_bits(const Circuit& c, const Shape& s) {
     };
     if (g.is_add) {
       apply(g.out_xor, kAdd);
+    } else if (g.is_nand) {
+      apply(g.out_xor, kNand);
     } else if (g.is_or) {
       apply(g.out_xor, kOr);
     } else {
@@ -537,10 +591,10 @@ void compile(const Circuit& c, const Shape& s, Program* prog) {
         d.a = home[sig_node(g.a)];
         d.b = home[sig_node(g.b)];
         uint16_t k0, k1 = 0;
-        if (g.is_add) {
+        if (g.is_add || g.is_nand) {
           d.o0 = ln[g.out_xor] ? home[g.out_xor] : REF_NONE;
           d.o1 = REF_NONE;
-          k0 = adjusted(kAdd, negA, negB);
+          k0 = adjusted(g.is_add ? kAdd : kNand, negA, negB);
         } else if (g.is_or) {
           d.o0 = ln[g.out_xor] ? home[g.out_xor] : REF_NONE;
           d.o1 = REF_NONE;

@@ -27,6 +27,12 @@
 // forces the other carry to 0). For the operand rule it is linear (depth =
 // max of its inputs); on the device it runs after the products of its
 // schedule level.
+//
+// NAND-only variant (Circuit::nand, the paper's literal construction, Lemma
+// 4): constants fold first as above; every remaining gate is made of GSW NAND
+// gates (1, 0, 0, -1), one product each: NOT a = NAND(a, a), AND = NOT(NAND),
+// OR = NAND(NOT a, NOT b), and a half adder t = NAND(a, b), XOR =
+// NAND(NAND(a, t), NAND(b, t)), AND = NAND(t, t). No complement bits.
 #pragma once
 
 #include <cstdint>
@@ -50,6 +56,7 @@ struct Product {
   uint32_t out_and;  // node of the AND output (HA only); 0 = none
   bool is_or;
   bool is_add;       // linear exclusive sum (XADD): no ciphertext product
+  bool is_nand;      // GSW NAND gate (NAND-only variant)
 };
 
 struct Circuit {
@@ -60,9 +67,14 @@ struct Circuit {
   std::vector<Sig> outputs;        // output signals in ciphertext order
   uint64_t n_and = 0, n_xor = 0, n_or = 0, n_not = 0, n_xadd = 0;   // logical gates before pruning
   bool xcarry = false;             // full-adder carry as XADD instead of OR
+  bool nand = false;               // every gate made of NAND gates
   // Common subexpressions: identical (kind, A, B) gates give identical
   // ciphertexts, so each is computed once (bit-exact).
-  std::unordered_map<uint64_t, int32_t> memo_ha, memo_or, memo_add;
+  std::unordered_map<uint64_t, int32_t> memo_ha, memo_or, memo_add, memo_nand;
+
+  // Selects the variant from plan flags (SFFT_PLAN_XCARRY, SFFT_PLAN_NAND);
+  // false if both are set.
+  bool set_variant(uint32_t flags);
 
   uint32_t new_node(uint32_t d, int32_t prod);
   uint32_t new_input();
@@ -72,6 +84,7 @@ struct Circuit {
   void HA(Sig a, Sig b, Sig* s, Sig* c);
   Sig OR(Sig a, Sig b);
   Sig XADD(Sig a, Sig b);
+  Sig NAND(Sig a, Sig b);   // one GSW NAND gate on two non-constant signals
   void FA(Sig a, Sig b, Sig c, Sig* s, Sig* co);
   std::vector<Sig> ADD(const std::vector<Sig>& x, const std::vector<Sig>& y, Sig cin);
   std::vector<Sig> SUB(const std::vector<Sig>& x, const std::vector<Sig>& y);

@@ -21,7 +21,8 @@ int build(const sfft_params* p, uint32_t N1, uint32_t N2, uint32_t F, uint32_t f
           Shape* s, Circuit* c, Program* prog) {
   int rc = make_shape(p, s, false);
   if (rc) return rc;
-  c->xcarry = (flags & SFFT_PLAN_XCARRY) != 0;
+  if (!c->set_variant(flags))
+    return fail(SFFT_EINVAL, "SFFT_PLAN_XCARRY and SFFT_PLAN_NAND are exclusive");
   if (!build_fft(c, N1, N2, F, f))
     return fail(SFFT_EINVAL, "N1, N2 must be powers of two, 2 <= F <= 48, f < F");
   compile(*c, *s, prog);

@@ -126,7 +126,7 @@ struct sfft_server {
   int* err = nullptr;
   cudaStream_t stream = nullptr;
   bool tc = false;
-  bool xcarry = false;             // exclusive-carry full adders in every circuit
+  uint32_t variant = 0;            // circuit variant flags of every request
 
   std::map<sfft::Shape4, std::unique_ptr<sfft::Program>> programs;
   std::mutex mu;
@@ -376,7 +376,9 @@ int sfft_server_create(const sfft_params* p, uint64_t hbm_budget_bytes, uint32_t
   int rc = make_shape(p, &sv->s, false);
   if (rc) return rc;
   sv->max_active = max_active ? max_active : 64;
-  sv->xcarry = (flags & SFFT_PLAN_XCARRY) != 0;
+  sv->variant = flags & (SFFT_PLAN_XCARRY | SFFT_PLAN_NAND);
+  if (!Circuit().set_variant(sv->variant))
+    return fail(SFFT_EINVAL, "SFFT_PLAN_XCARRY and SFFT_PLAN_NAND are exclusive");
   const uint64_t ctb = sv->s.ctw * 4;
   KArgs k = make_args(sv->s);
   sv->tc = tc_supported(k);
@@ -421,7 +423,7 @@ int sfft_server_submit(sfft_server* sv, const sfft_request* req, const uint32_t*
   auto it = sv->programs.find(shape);
   if (it == sv->programs.end()) {
     Circuit c;
-    c.xcarry = sv->xcarry;
+    c.set_variant(sv->variant);
     if (!build_fft(&c, req->N1, req->N2, req->F, req->f))
       return fail(SFFT_EINVAL, "invalid FFT shape");
     std::unique_ptr<Program> prog(new Program);

@@ -186,6 +186,49 @@ def test_fft_exclusive_carry_variant_bit_exact(flags):
     assert [gsw.decrypt(ko, ct) for ct in got] == evaluate.eval_plain(c, bits)
 
 
+@pytest.mark.parametrize("pset,N1,N2,F,f,flags", [
+    ("P1", 2, 1, 4, 1, 0), ("P1", 2, 1, 4, 1, sf.PLAN_INT_KERNEL), ("P0", 4, 4, 8, 3, 0)])
+def test_fft_nand_variant_bit_exact(pset, N1, N2, F, f, flags):
+    """The NAND-only circuit (every gate a GSW NAND product; Lemma 4): noisy
+    chi = 1 at its own smallest ell (tensor-core and integer kernels), and a
+    2-D transform at the toy parameters, through the plan and the graph-replayed
+    batch."""
+    ell = sf.min_ell(N1, N2, F, f, n=1, chi=1, nand=True) if pset == "P1" else None
+    sp = sf.param_set(pset, ell)
+    p = gsw.Params(sp.n, sp.ell, sp.m, sp.chi)
+    re_, im_ = (signal_1d(N1, -1, 1, 7) if N2 == 1 else image_2d(N1, N2, 7))
+    keys = sf.keygen(sp, 7)
+    n_in = N1 * N2 * 2 * F
+    d_in = torch.zeros((n_in, sf.ct_words(sp)), dtype=torch.int32, device="cuda")
+    sf.encrypt_bits_device(sp, dev(keys.public()), re_, im_, F, f, 4, d_in)
+    plan, out = _run_plan(sp, N1, N2, F, f, d_in, flags | sf.PLAN_NAND)
+    assert plan.info["gates_xor"] > 0 and plan.info["gates_xadd"] == 0
+    got = host(out, (n_in, p.Ng, p.n + 1, p.L))
+    ko = gsw.Keys(p, 7)
+    c = circuit.fft_circuit(N1, N2, F, f, nand=True)
+    assert plan.info["products"] == circuit.stats(c)["products"]
+    cts, bits = [], []
+    for k in range(N1 * N2):
+        for part, x in enumerate((re_[k], im_[k])):
+            for b, bit in enumerate(fx.to_bits(fx.quantize(x, F, f), F)):
+                cts.append(gsw.encrypt(ko, bit, 4, (2 * k + part) * F + b))
+                bits.append(bit)
+    want = evaluate.eval_encrypted(c, p, cts)
+    assert np.array_equal(got, want)
+    assert [gsw.decrypt(ko, ct) for ct in got] == evaluate.eval_plain(c, bits)
+
+    batch = sf.Batch(sp, [(N1, N2, F, f)], flags | sf.PLAN_NAND)
+    bi = batch.info
+    d_out = torch.zeros((bi["outputs"], bi["ct_words"]), dtype=torch.int32, device="cuda")
+    scratch = torch.empty(max(1, bi["scratch_bytes"] // 4), dtype=torch.int32, device="cuda")
+    stream = torch.cuda.Stream()
+    for _ in range(2):   # capture, then replay
+        batch.eval(d_in, d_out, scratch, stream)
+    batch.check(stream)
+    torch.cuda.synchronize()
+    assert np.array_equal(host(d_out, (n_in, p.Ng, p.n + 1, p.L)), want)
+
+
 def test_fft_2d_toy_parameters_bit_exact():
     N1, N2, F, f = 4, 4, 8, 3
     sp = sf.param_set("P0")

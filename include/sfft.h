@@ -168,10 +168,48 @@ typedef struct sfft_plan_info {
  * and a larger ell; decrypts to the same words. Exclusive with
  * SFFT_PLAN_XCARRY (EINVAL). */
 #define SFFT_PLAN_NAND 16u
+/* Variant (not the paper's, which multiplies by plaintext twiddles and notes
+ * in Sec. 4 that a plaintext constant's bits show through the Wallace tree):
+ * the FFT takes its twiddles as encrypted words and multiplies with the
+ * encrypted-operand Wallace multiplier (every partial product an AND of two
+ * ciphertexts). Inputs: the signal as without the flag, then one table of
+ * M/2 complex words W_M^k = floor(cos(2 pi k / M) 2^f) + i floor(-sin(2 pi k /
+ * M) 2^f), M = max(N1, N2), as samples N1 N2 + k (sfft_twiddles gives the
+ * values; encrypt them with the signal in one sfft_encrypt_bits call).
+ * Requires f <= F - 2 (W_M^0 = 2^f must fit a signed F-bit word). Same output
+ * words as the plaintext-twiddle circuit. Combines with either gate variant. */
+#define SFFT_PLAN_ENC_TWIDDLE 32u
 int sfft_plan_create(const sfft_params* p, uint32_t N1, uint32_t N2, uint32_t F, uint32_t f,
                      uint32_t flags, sfft_plan** out);
 int sfft_plan_info_get(const sfft_plan* plan, sfft_plan_info* info);
 void sfft_plan_free(sfft_plan* plan);
+
+/* Word circuits: count independent operations on pairs of encrypted F-bit
+ * two's-complement words (x, y), evaluated like an FFT plan (sfft_eval_fft and
+ * sfft_eval_fft_host take any plan). Word k's x is input (2k) F + b, its y
+ * input (2k + 1) F + b (the layout of sfft_encrypt_bits with re = x, im = y);
+ * its result is output k F + b. Ops: (x + y) mod 2^F and (x - y) mod 2^F
+ * (Sec. 4, Lemma 7), and the fixed-point product of two ciphertext words,
+ * floor(x y / 2^f) mod 2^F, by the encrypted-operand Wallace multiplier
+ * (partial products AND(x_ext[c - i], y_ext[i]) over T = f + F sign-extended
+ * bits, Lemma 8's Wallace stages, Lemma 9's middle bits [f, f + F)). flags:
+ * as sfft_plan_create (SFFT_PLAN_ENC_TWIDDLE has no effect). EINVAL unless
+ * 1 <= count <= 2^24, 2 <= F <= 48, f < F. */
+#define SFFT_WORD_ADD 1u
+#define SFFT_WORD_SUB 2u
+#define SFFT_WORD_MUL 3u
+int sfft_word_plan_create(const sfft_params* p, uint32_t op, uint64_t count, uint32_t F,
+                          uint32_t f, uint32_t flags, sfft_plan** out);
+
+/* Smallest ell of a word circuit (as sfft_min_ell; independent of count). */
+uint32_t sfft_word_min_ell(uint32_t op, uint32_t F, uint32_t f, uint32_t n, uint32_t chi,
+                           uint32_t flags);
+
+/* Quantised twiddles W_M^k, k < M/2 (M a power of two >= 2): h_wr[k] =
+ * floor(cos(2 pi k / M) 2^f), h_wi[k] = floor(-sin(2 pi k / M) 2^f), fp64
+ * (Sec. 4's truncation read as floor). The client encrypts them for
+ * SFFT_PLAN_ENC_TWIDDLE. h_wr, h_wi: M/2 entries each, caller-owned. */
+int sfft_twiddles(uint32_t M, uint32_t f, int64_t* h_wr, int64_t* h_wi);
 
 /* Step 4 on the server, plain level-by-level form: one kernel launch per
  * level, every product of the level evaluated in parallel. d_in holds
@@ -206,6 +244,13 @@ int sfft_circuit_info(const sfft_params* p, uint32_t N1, uint32_t N2, uint32_t F
 int sfft_program_eval_plain(const sfft_params* p, uint32_t N1, uint32_t N2, uint32_t F,
                             uint32_t f, uint32_t flags, const uint8_t* h_in_bits,
                             uint8_t* h_out_bits);
+
+/* The same two host-only hooks for word circuits (sfft_word_plan_create). */
+int sfft_word_circuit_info(const sfft_params* p, uint32_t op, uint64_t count, uint32_t F,
+                           uint32_t f, uint32_t flags, sfft_plan_info* info);
+int sfft_word_program_eval_plain(const sfft_params* p, uint32_t op, uint64_t count, uint32_t F,
+                                 uint32_t f, uint32_t flags, const uint8_t* h_in_bits,
+                                 uint8_t* h_out_bits);
 
 /* sfft_eval_fft without any allocation (the paper has no counterpart; this
  * is a library service). For callers that must not call cudaMalloc while

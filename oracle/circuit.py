@@ -50,9 +50,20 @@ NAND(a, a), AND = NOT(NAND(a, b)), OR = NAND(NOT a, NOT b), XOR =
 NAND(NAND(a, t), NAND(b, t)) with t = NAND(a, b); a half adder shares t
 between its XOR and its AND = NAND(t, t).
 
+Encrypted-operand multiplier (``MULE``, a variant; the paper multiplies by
+plaintext constants and notes in Sec. 4 that the constant's bits show through
+the Wallace tree): both words are sign-extended to T = f + F bits and every
+row i < T is present, column c >= i receiving AND(x_ext[c-i], y_ext[i]); the
+same Wallace stages and final ADD_T as MUL; result bits [f, f+F). Closed form:
+floor(x y / 2^f) mod 2^F. With ``enc_twiddle`` the FFT takes its twiddles as
+encrypted words (inputs after the signal): one table W_M^k, k < M/2, M the
+largest transform length, and a length-n transform uses entry t M/n for its
+W_n^t (the same floor of the same real number).
+
 Wires are non-negative ints; the trivial constants are ZERO = -1, ONE = -2.
 Input wire number (k * 2 + part) * F + bit holds bit ``bit`` of the real
-(part 0) or imaginary (part 1) word of sample k.
+(part 0) or imaginary (part 1) word of sample k; with ``enc_twiddle`` sample
+N1 N2 + k holds the twiddle W_M^k (real part Wr, imaginary part Wi).
 
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 """
@@ -187,6 +198,23 @@ class Circuit:
             if (w_bits >> i) & 1:
                 for c in range(i, T):
                     cols[c].append(x_ext[c - i])
+        return self._wallace(cols)[f:f + F]
+
+    def MULE(self, x, y, f):
+        """Fixed-point product of two encrypted words (AND partial products)."""
+        F = len(x)
+        T = f + F
+        x_ext = [x[min(j, F - 1)] for j in range(T)]
+        y_ext = [y[min(i, F - 1)] for i in range(T)]
+        cols = [[] for _ in range(T)]
+        for i in range(T):
+            for c in range(i, T):
+                cols[c].append(self.AND(x_ext[c - i], y_ext[i]))
+        return self._wallace(cols)[f:f + F]
+
+    def _wallace(self, cols):
+        """Wallace stages on column lists, then ADD_T of the two rows (T bits)."""
+        T = len(cols)
         while max(len(col) for col in cols) > 2:
             sums = [[] for _ in range(T)]
             passed = [[] for _ in range(T)]
@@ -208,14 +236,15 @@ class Circuit:
             cols = [sums[c] + passed[c] + carries[c] for c in range(T)]
         row0 = [col[0] if len(col) >= 1 else ZERO for col in cols]
         row1 = [col[1] if len(col) >= 2 else ZERO for col in cols]
-        prod = self.ADD(row0, row1, ZERO)
-        return prod[f:f + F]
+        return self.ADD(row0, row1, ZERO)
 
     # -- butterfly and FFT (Sec. 4, Lemma 3) -------------------------------
     def BUTTERFLY(self, u, x, W, f):
+        """W = (Wr, Wi): plaintext ints (MUL) or encrypted words (MULE)."""
         (ur, ui), (xr, xi), (Wr, Wi) = u, x, W
-        tr = self.SUB(self.MUL(xr, Wr, f), self.MUL(xi, Wi, f))
-        ti = self.ADD(self.MUL(xi, Wr, f), self.MUL(xr, Wi, f))
+        mul = self.MULE if isinstance(Wr, list) else self.MUL
+        tr = self.SUB(mul(xr, Wr, f), mul(xi, Wi, f))
+        ti = self.ADD(mul(xi, Wr, f), mul(xr, Wi, f))
         top = (self.ADD(ur, tr), self.ADD(ui, ti))
         bot = (self.SUB(ur, tr), self.SUB(ui, ti))
         return top, bot
@@ -268,16 +297,20 @@ def twiddles(N, f):
     return tw
 
 
-def fft_circuit(N1, N2, F, f, xcarry=False, nand=False):
+def fft_circuit(N1, N2, F, f, xcarry=False, nand=False, enc_twiddle=False):
     """Circuit of a 1-D (N2 == 1) or row-column 2-D encrypted FFT.
 
     1-D: N1 samples. 2-D: an N1 x N2 image, sample k = r * N2 + c; all row
     FFTs (length N2) first, then all column FFTs (length N1). ``xcarry``
-    selects the exclusive-carry full adder.
+    selects the exclusive-carry full adder, ``nand`` the NAND-only gates,
+    ``enc_twiddle`` encrypted twiddle inputs (needs f <= F - 2 so that
+    W_M^0 = 2^f fits a signed F-bit word).
     """
     for n in (N1, N2):
         if n < 1 or n & (n - 1):
             raise ValueError("FFT sizes must be powers of two")
+    if enc_twiddle and f > F - 2:
+        raise ValueError("encrypted twiddles need f <= F - 2")
     c = Circuit(xcarry, nand)
     count = N1 * N2
     samples = []
@@ -285,15 +318,28 @@ def fft_circuit(N1, N2, F, f, xcarry=False, nand=False):
         re = [c.new_input() for _ in range(F)]
         im = [c.new_input() for _ in range(F)]
         samples.append((re, im))
-    if N2 == 1:
-        out = c.FFT(samples, twiddles(N1, f), f) if N1 > 1 else samples
+    M = max(N1, N2)
+    if enc_twiddle:
+        table = []
+        for k in range(M // 2):
+            wr = [c.new_input() for _ in range(F)]
+            wi = [c.new_input() for _ in range(F)]
+            table.append((wr, wi))
+
+        def tw_of(n):
+            return [table[t * (M // n)] for t in range(n // 2)]
     else:
-        rows = [c.FFT(samples[r * N2:(r + 1) * N2], twiddles(N2, f), f) if N2 > 1
+        def tw_of(n):
+            return twiddles(n, f)
+    if N2 == 1:
+        out = c.FFT(samples, tw_of(N1), f) if N1 > 1 else samples
+    else:
+        rows = [c.FFT(samples[r * N2:(r + 1) * N2], tw_of(N2), f) if N2 > 1
                 else samples[r * N2:(r + 1) * N2] for r in range(N1)]
         grid = [x for row in rows for x in row]
         out = list(grid)
         if N1 > 1:
-            tw = twiddles(N1, f)
+            tw = tw_of(N1)
             for col in range(N2):
                 res = c.FFT([grid[r * N2 + col] for r in range(N1)], tw, f)
                 for r in range(N1):
@@ -308,7 +354,8 @@ def fft_circuit(N1, N2, F, f, xcarry=False, nand=False):
 def word_circuit(kind, F, f=0, w=None, xcarry=False, nand=False):
     """Small circuits over two input words (x, y) for the arithmetic pins.
 
-    kind: 'add', 'sub' (x op y), 'mul' (x times plaintext w, fixed point f).
+    kind: 'add', 'sub' (x op y), 'mul' (x times plaintext w, fixed point f),
+    'mule' (x times the encrypted y, fixed point f).
     """
     c = Circuit(xcarry, nand)
     x = [c.new_input() for _ in range(F)]
@@ -319,6 +366,8 @@ def word_circuit(kind, F, f=0, w=None, xcarry=False, nand=False):
         out = c.SUB(x, y)
     elif kind == "mul":
         out = c.MUL(x, w, f)
+    elif kind == "mule":
+        out = c.MULE(x, y, f)
     else:
         raise ValueError(kind)
     c.outputs = list(out)

@@ -20,10 +20,13 @@ PLAN_ALLOW_NOISY = 1
 PLAN_INT_KERNEL = 2
 PLAN_XCARRY = 8   # circuit variant: exclusive-carry full adders (sfft.h SFFT_PLAN_XCARRY)
 PLAN_NAND = 16    # circuit variant: every gate built of NAND gates (sfft.h SFFT_PLAN_NAND)
+PLAN_ENC_TWIDDLE = 32   # FFT twiddles as encrypted inputs (sfft.h SFFT_PLAN_ENC_TWIDDLE)
+WORD_ADD, WORD_SUB, WORD_MUL = 1, 2, 3   # word circuits (sfft.h SFFT_WORD_*)
 KERNEL_AUTO, KERNEL_INT, KERNEL_TC = 0, 1, 2
 
 __all__ = ["Params", "Keys", "Plan", "keygen", "encrypt_bits", "encrypt_bits_device", "decrypt",
-           "gather_dec_rows", "min_ell", "gate_level", "ct_words", "SfftError", "version"]
+           "gather_dec_rows", "min_ell", "gate_level", "ct_words", "SfftError", "version",
+           "word_min_ell", "word_circuit_info", "twiddles"]
 
 PARAM_SETS = {
     # toy, noise-free (chi = 0): exact decryption at any depth; insecure by construction
@@ -133,30 +136,69 @@ def gather_dec_rows(params, d_ct, n_ct, d_rows, stream=None):
                                      _stream(stream)))
 
 
-def _variant(xcarry, nand):
-    return (PLAN_XCARRY if xcarry else 0) | (PLAN_NAND if nand else 0)
+def _variant(xcarry, nand, enc_twiddle=False):
+    return ((PLAN_XCARRY if xcarry else 0) | (PLAN_NAND if nand else 0)
+            | (PLAN_ENC_TWIDDLE if enc_twiddle else 0))
 
 
-def min_ell(N1, N2, F, f, n=1, chi=1, xcarry=False, nand=False):
-    return int(lib().sfft_min_ell(N1, N2, F, f, n, chi, _variant(xcarry, nand)))
-
-
-def circuit_info(params, N1, N2, F, f, xcarry=False, nand=False):
-    """Host-only statistics of the compiled FFT circuit (sfft_circuit_info)."""
-    info = sfft_plan_info()
-    check(lib().sfft_circuit_info(ctypes.byref(params), N1, N2, F, f, _variant(xcarry, nand),
-                                  ctypes.byref(info)))
+def _info_dict(info):
     return {k: getattr(info, k) for k, _ in sfft_plan_info._fields_}
 
 
-def program_eval_plain(params, N1, N2, F, f, in_bits, xcarry=False, nand=False):
+def min_ell(N1, N2, F, f, n=1, chi=1, xcarry=False, nand=False, enc_twiddle=False):
+    return int(lib().sfft_min_ell(N1, N2, F, f, n, chi, _variant(xcarry, nand, enc_twiddle)))
+
+
+def circuit_info(params, N1, N2, F, f, xcarry=False, nand=False, enc_twiddle=False):
+    """Host-only statistics of the compiled FFT circuit (sfft_circuit_info)."""
+    info = sfft_plan_info()
+    check(lib().sfft_circuit_info(ctypes.byref(params), N1, N2, F, f,
+                                  _variant(xcarry, nand, enc_twiddle), ctypes.byref(info)))
+    return _info_dict(info)
+
+
+def program_eval_plain(params, N1, N2, F, f, in_bits, xcarry=False, nand=False, enc_twiddle=False):
     """Host-only plaintext run of the compiled device program (sfft_program_eval_plain)."""
+    flags = _variant(xcarry, nand, enc_twiddle)
     in_bits = np.ascontiguousarray(in_bits, dtype=np.uint8)
-    out = np.zeros(len(in_bits), dtype=np.uint8)
-    check(lib().sfft_program_eval_plain(ctypes.byref(params), N1, N2, F, f, _variant(xcarry, nand),
+    out = np.zeros(circuit_info(params, N1, N2, F, f, xcarry, nand, enc_twiddle)["outputs"],
+                   dtype=np.uint8)
+    check(lib().sfft_program_eval_plain(ctypes.byref(params), N1, N2, F, f, flags,
                                         in_bits.ctypes.data_as(native.c_u8_p),
                                         out.ctypes.data_as(native.c_u8_p)))
     return out
+
+
+def word_min_ell(op, F, f, n=1, chi=1, xcarry=False, nand=False):
+    return int(lib().sfft_word_min_ell(op, F, f, n, chi, _variant(xcarry, nand)))
+
+
+def word_circuit_info(params, op, count, F, f, xcarry=False, nand=False):
+    """Host-only statistics of a word circuit (sfft_word_circuit_info)."""
+    info = sfft_plan_info()
+    check(lib().sfft_word_circuit_info(ctypes.byref(params), op, count, F, f,
+                                       _variant(xcarry, nand), ctypes.byref(info)))
+    return _info_dict(info)
+
+
+def word_program_eval_plain(params, op, count, F, f, in_bits, xcarry=False, nand=False):
+    """Host-only plaintext run of a word circuit's device program."""
+    in_bits = np.ascontiguousarray(in_bits, dtype=np.uint8)
+    out = np.zeros(count * F, dtype=np.uint8)
+    check(lib().sfft_word_program_eval_plain(ctypes.byref(params), op, count, F, f,
+                                             _variant(xcarry, nand),
+                                             in_bits.ctypes.data_as(native.c_u8_p),
+                                             out.ctypes.data_as(native.c_u8_p)))
+    return out
+
+
+def twiddles(M, f):
+    """Quantised twiddles W_M^k, k < M/2, as two int64 arrays (sfft_twiddles)."""
+    wr = np.zeros(M // 2, dtype=np.int64)
+    wi = np.zeros(M // 2, dtype=np.int64)
+    check(lib().sfft_twiddles(M, f, wr.ctypes.data_as(native.c_i64_p),
+                              wi.ctypes.data_as(native.c_i64_p)))
+    return wr, wi
 
 
 class Plan:
@@ -171,6 +213,22 @@ class Plan:
         info = sfft_plan_info()
         check(lib().sfft_plan_info_get(h, ctypes.byref(info)))
         self.info = {k: getattr(info, k) for k, _ in sfft_plan_info._fields_}
+
+    @classmethod
+    def words(cls, params, op, count, F, f, flags=0):
+        """count word operations (sfft_word_plan_create); evaluated like an FFT plan."""
+        self = cls.__new__(cls)
+        self.params = params
+        self.N1 = self.N2 = None
+        self.F, self.f = F, f
+        h = ctypes.c_void_p()
+        check(lib().sfft_word_plan_create(ctypes.byref(params), op, count, F, f, flags,
+                                          ctypes.byref(h)))
+        self._h = h
+        info = sfft_plan_info()
+        check(lib().sfft_plan_info_get(h, ctypes.byref(info)))
+        self.info = _info_dict(info)
+        return self
 
     def eval_fft(self, d_in, d_out, d_scratch, stream=None):
         nbytes = 0 if d_scratch is None else d_scratch.numel() * d_scratch.element_size()

@@ -191,16 +191,11 @@ void free_device_program(DeviceProgram* dp) {
 
 using namespace sfft;
 
-extern "C" {
+namespace {
 
-const char* sfft_version(void) { return "sfft-gb300 0.1 (sm_103a)"; }
-
-uint64_t sfft_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
-
-uint32_t sfft_min_ell(uint32_t N1, uint32_t N2, uint32_t F, uint32_t f, uint32_t n, uint32_t chi,
-                      uint32_t flags) {
+uint32_t min_ell_of(const CircuitSpec& spec, uint32_t n, uint32_t chi, uint32_t flags) {
   Circuit c;
-  if (!c.set_variant(flags) || !build_fft(&c, N1, N2, F, f)) return 0;
+  if (build_circuit(&c, spec, flags)) return 0;
   for (uint32_t ell = 32; ell <= 8192; ell += 32) {
     sfft_params p{n, ell, (n + 1) * ell, chi};
     Shape s;
@@ -210,18 +205,14 @@ uint32_t sfft_min_ell(uint32_t N1, uint32_t N2, uint32_t F, uint32_t f, uint32_t
   return 0;
 }
 
-int sfft_plan_create(const sfft_params* p, uint32_t N1, uint32_t N2, uint32_t F, uint32_t f,
-                     uint32_t flags, sfft_plan** out) {
+int plan_create(const sfft_params* p, const CircuitSpec& spec, uint32_t flags, sfft_plan** out) {
   if (!out) return fail(SFFT_EINVAL, "out is NULL");
   *out = nullptr;
   std::unique_ptr<sfft_plan> pl(new (std::nothrow) sfft_plan);
   if (!pl) return fail(SFFT_ENOMEM, "host allocation failed");
   int rc = make_shape(p, &pl->s, false);
   if (rc) return rc;
-  if (!pl->circuit.set_variant(flags))
-    return fail(SFFT_EINVAL, "SFFT_PLAN_XCARRY and SFFT_PLAN_NAND are exclusive");
-  if (!build_fft(&pl->circuit, N1, N2, F, f))
-    return fail(SFFT_EINVAL, "N1, N2 must be powers of two, 2 <= F <= 48, f < F");
+  if ((rc = build_circuit(&pl->circuit, spec, flags))) return rc;
   compile(pl->circuit, pl->s, &pl->prog);
   if (!pl->prog.noise_ok && !(flags & SFFT_PLAN_ALLOW_NOISY))
     return fail(SFFT_EPARAM, "static noise bound reaches q/4: raise ell (see sfft_min_ell)");
@@ -229,10 +220,7 @@ int sfft_plan_create(const sfft_params* p, uint32_t N1, uint32_t N2, uint32_t F,
     free_device_program(&pl->dev);
     return rc;
   }
-  pl->N1 = N1;
-  pl->N2 = N2;
-  pl->F = F;
-  pl->f = f;
+  pl->spec = spec;
   pl->dev.kernel = (flags & SFFT_PLAN_INT_KERNEL) ? KERNEL_INT : KERNEL_AUTO;
   pl->dev.max_width = pl->prog.max_width;
   pl->dev.tc = pl->dev.kernel != KERNEL_INT && tc_supported(make_args(pl->s));
@@ -240,6 +228,54 @@ int sfft_plan_create(const sfft_params* p, uint32_t N1, uint32_t N2, uint32_t F,
                                          pl->dev.tc, &pl->dev.bx_off);
   *out = pl.release();
   return SFFT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sfft_version(void) { return "sfft-gb300 0.1 (sm_103a)"; }
+
+uint64_t sfft_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+uint32_t sfft_min_ell(uint32_t N1, uint32_t N2, uint32_t F, uint32_t f, uint32_t n, uint32_t chi,
+                      uint32_t flags) {
+  CircuitSpec spec;
+  spec.N1 = N1;
+  spec.N2 = N2;
+  spec.F = F;
+  spec.f = f;
+  return min_ell_of(spec, n, chi, flags);
+}
+
+uint32_t sfft_word_min_ell(uint32_t op, uint32_t F, uint32_t f, uint32_t n, uint32_t chi,
+                           uint32_t flags) {
+  CircuitSpec spec;
+  spec.op = op;
+  spec.count = 1;
+  spec.F = F;
+  spec.f = f;
+  return min_ell_of(spec, n, chi, flags);
+}
+
+int sfft_plan_create(const sfft_params* p, uint32_t N1, uint32_t N2, uint32_t F, uint32_t f,
+                     uint32_t flags, sfft_plan** out) {
+  CircuitSpec spec;
+  spec.N1 = N1;
+  spec.N2 = N2;
+  spec.F = F;
+  spec.f = f;
+  return plan_create(p, spec, flags, out);
+}
+
+int sfft_word_plan_create(const sfft_params* p, uint32_t op, uint64_t count, uint32_t F,
+                          uint32_t f, uint32_t flags, sfft_plan** out) {
+  CircuitSpec spec;
+  spec.op = op;
+  spec.count = count;
+  spec.F = F;
+  spec.f = f;
+  return plan_create(p, spec, flags, out);
 }
 
 int sfft_plan_info_get(const sfft_plan* pl, sfft_plan_info* info) {

@@ -11,6 +11,7 @@ namespace sfft {
 bool Circuit::set_variant(uint32_t flags) {
   xcarry = (flags & SFFT_PLAN_XCARRY) != 0;
   nand = (flags & SFFT_PLAN_NAND) != 0;
+  enc_twiddle = (flags & SFFT_PLAN_ENC_TWIDDLE) != 0;
   return !(xcarry && nand);
 }
 
@@ -34,6 +35,22 @@ Sig Circuit::NOT(Sig a) {
   if (sig_node(a) != 0) n_not++;
   if (nand && sig_node(a) != 0) return NAND(a, a);
   return a ^ SIG_ONE;
+}
+
+Sig Circuit::AND(Sig a, Sig b) {
+  if (a == SIG_ZERO || b == SIG_ZERO) return SIG_ZERO;
+  if (a == SIG_ONE) return b;
+  if (b == SIG_ONE) return a;
+  if (nand) {
+    n_and++;
+    const Sig t = NAND(a, b);
+    return NOT(t);
+  }
+  Sig s, c;
+  const uint64_t xors = n_xor;
+  HA(a, b, &s, &c);   // the XOR output stays unused (pruned)
+  n_xor = xors;
+  return c;
 }
 
 Sig Circuit::NAND(Sig a, Sig b) {
@@ -217,6 +234,27 @@ std::vector<Sig> Circuit::MUL(const std::vector<Sig>& x, int64_t w, uint32_t f) 
   for (uint32_t i = 0; i < T; i++)
     if ((wb >> i) & 1)
       for (uint32_t c = i; c < T; c++) col[c].push_back(xe[c - i]);
+  std::vector<Sig> prod = wallace(std::move(col));
+  return std::vector<Sig>(prod.begin() + f, prod.begin() + f + F);
+}
+
+std::vector<Sig> Circuit::MULE(const std::vector<Sig>& x, const std::vector<Sig>& y, uint32_t f) {
+  const uint32_t F = (uint32_t)x.size();
+  const uint32_t T = f + F;
+  std::vector<Sig> xe(T), ye(T);
+  for (uint32_t j = 0; j < T; j++) {
+    xe[j] = x[std::min(j, F - 1)];
+    ye[j] = y[std::min(j, F - 1)];
+  }
+  std::vector<std::vector<Sig>> col(T);
+  for (uint32_t i = 0; i < T; i++)
+    for (uint32_t c = i; c < T; c++) col[c].push_back(AND(xe[c - i], ye[i]));
+  std::vector<Sig> prod = wallace(std::move(col));
+  return std::vector<Sig>(prod.begin() + f, prod.begin() + f + F);
+}
+
+std::vector<Sig> Circuit::wallace(std::vector<std::vector<Sig>> col) {
+  const uint32_t T = (uint32_t)col.size();
   auto tallest = [&]() {
     size_t h = 0;
     for (auto& v : col) h = std::max(h, v.size());
@@ -258,8 +296,7 @@ std::vector<Sig> Circuit::MUL(const std::vector<Sig>& x, int64_t w, uint32_t f) 
     r0[c] = col[c].size() >= 1 ? col[c][0] : SIG_ZERO;
     r1[c] = col[c].size() >= 2 ? col[c][1] : SIG_ZERO;
   }
-  std::vector<Sig> prod = ADD(r0, r1, SIG_ZERO);
-  return std::vector<Sig>(prod.begin() + f, prod.begin() + f + F);
+  return ADD(r0, r1, SIG_ZERO);
 }
 
 void twiddles(uint32_t N, uint32_t f, std::vector<int64_t>* wr, std::vector<int64_t>* wi) {
@@ -287,9 +324,25 @@ uint32_t bitrev(uint32_t i, uint32_t bits) {
   return r;
 }
 
-void butterfly(Circuit* c, Cplx* u, Cplx* x, int64_t wr, int64_t wi, uint32_t f) {
-  Word tr = c->SUB(c->MUL(x->first, wr, f), c->MUL(x->second, wi, f));
-  Word ti = c->ADD(c->MUL(x->second, wr, f), c->MUL(x->first, wi, f), SIG_ZERO);
+// Twiddle of a butterfly: a plaintext pair (MUL) or an encrypted pair (MULE).
+struct Twiddle {
+  int64_t wr = 0, wi = 0;
+  const Cplx* enc = nullptr;
+};
+
+Word mul_tw(Circuit* c, const Word& x, const Twiddle& w, bool real, uint32_t f) {
+  if (w.enc) return c->MULE(x, real ? w.enc->first : w.enc->second, f);
+  return c->MUL(x, real ? w.wr : w.wi, f);
+}
+
+void butterfly(Circuit* c, Cplx* u, Cplx* x, const Twiddle& w, uint32_t f) {
+  // operands in the order t_r = xr Wr - xi Wi, t_i = xi Wr + xr Wi
+  Word p0 = mul_tw(c, x->first, w, true, f);
+  Word p1 = mul_tw(c, x->second, w, false, f);
+  Word tr = c->SUB(p0, p1);
+  Word p2 = mul_tw(c, x->second, w, true, f);
+  Word p3 = mul_tw(c, x->first, w, false, f);
+  Word ti = c->ADD(p2, p3, SIG_ZERO);
   Word top_r = c->ADD(u->first, tr, SIG_ZERO);
   Word top_i = c->ADD(u->second, ti, SIG_ZERO);
   Word bot_r = c->SUB(u->first, tr);
@@ -298,20 +351,31 @@ void butterfly(Circuit* c, Cplx* u, Cplx* x, int64_t wr, int64_t wi, uint32_t f)
   *x = Cplx(bot_r, bot_i);
 }
 
-std::vector<Cplx> fft(Circuit* c, const std::vector<Cplx>& in, uint32_t f) {
+// table: encrypted twiddles W_M^k (k < M/2) or empty for plaintext constants
+std::vector<Cplx> fft(Circuit* c, const std::vector<Cplx>& in, uint32_t f,
+                      const std::vector<Cplx>& table) {
   const uint32_t N = (uint32_t)in.size();
   uint32_t logN = 0;
   while ((1u << logN) < N) logN++;
-  std::vector<int64_t> wr, wi;
-  twiddles(N, f, &wr, &wi);
+  std::vector<Twiddle> tw(N / 2);
+  if (table.empty()) {
+    std::vector<int64_t> wr, wi;
+    twiddles(N, f, &wr, &wi);
+    for (uint32_t t = 0; t < N / 2; t++) {
+      tw[t].wr = wr[t];
+      tw[t].wi = wi[t];
+    }
+  } else {
+    const uint32_t M = 2 * (uint32_t)table.size();
+    for (uint32_t t = 0; t < N / 2; t++) tw[t].enc = &table[t * (M / N)];
+  }
   std::vector<Cplx> a(N);
   for (uint32_t i = 0; i < N; i++) a[i] = in[bitrev(i, logN)];
   for (uint32_t m = 2; m <= N; m *= 2) {
     uint32_t h = m / 2;
     for (uint32_t k = 0; k < N; k += m)
       for (uint32_t j = 0; j < h; j++) {
-        uint32_t t = j * (N / m);
-        butterfly(c, &a[k + j], &a[k + j + h], wr[t], wi[t], f);
+        butterfly(c, &a[k + j], &a[k + j + h], tw[j * (N / m)], f);
       }
   }
   return a;
@@ -323,22 +387,27 @@ bool pow2(uint32_t n) { return n >= 1 && (n & (n - 1)) == 0; }
 
 bool build_fft(Circuit* c, uint32_t N1, uint32_t N2, uint32_t F, uint32_t f) {
   if (!pow2(N1) || !pow2(N2) || F < 2 || F > 48 || f >= F) return false;
+  if (c->enc_twiddle && f + 2 > F) return false;   // W^0 = 2^f must fit a signed word
   const uint32_t count = N1 * N2;
-  std::vector<Cplx> s(count);
-  for (uint32_t k = 0; k < count; k++) {
+  auto input_word = [&]() {
     Word re(F), im(F);
     for (uint32_t b = 0; b < F; b++) re[b] = c->new_input();
     for (uint32_t b = 0; b < F; b++) im[b] = c->new_input();
-    s[k] = Cplx(re, im);
-  }
+    return Cplx(re, im);
+  };
+  std::vector<Cplx> s(count);
+  for (uint32_t k = 0; k < count; k++) s[k] = input_word();
+  std::vector<Cplx> table;
+  if (c->enc_twiddle)
+    for (uint32_t k = 0; k < std::max(N1, N2) / 2; k++) table.push_back(input_word());
   std::vector<Cplx> out;
   if (N2 == 1) {
-    out = N1 > 1 ? fft(c, s, f) : s;
+    out = N1 > 1 ? fft(c, s, f, table) : s;
   } else {
     std::vector<Cplx> grid(count);
     for (uint32_t r = 0; r < N1; r++) {
       std::vector<Cplx> row(s.begin() + r * N2, s.begin() + (r + 1) * N2);
-      std::vector<Cplx> res = fft(c, row, f);
+      std::vector<Cplx> res = N2 > 1 ? fft(c, row, f, table) : row;
       for (uint32_t j = 0; j < N2; j++) grid[r * N2 + j] = res[j];
     }
     out = grid;
@@ -346,7 +415,7 @@ bool build_fft(Circuit* c, uint32_t N1, uint32_t N2, uint32_t F, uint32_t f) {
       for (uint32_t col = 0; col < N2; col++) {
         std::vector<Cplx> v(N1);
         for (uint32_t r = 0; r < N1; r++) v[r] = grid[r * N2 + col];
-        std::vector<Cplx> res = fft(c, v, f);
+        std::vector<Cplx> res = fft(c, v, f, table);
         for (uint32_t r = 0; r < N1; r++) out[r * N2 + col] = res[r];
       }
   }
@@ -355,6 +424,37 @@ bool build_fft(Circuit* c, uint32_t N1, uint32_t N2, uint32_t F, uint32_t f) {
     c->outputs.insert(c->outputs.end(), z.second.begin(), z.second.end());
   }
   return true;
+}
+
+bool build_words(Circuit* c, uint32_t op, uint64_t count, uint32_t F, uint32_t f) {
+  if (count == 0 || count > (1ull << 24) || F < 2 || F > 48 || f >= F) return false;
+  if (op != SFFT_WORD_ADD && op != SFFT_WORD_SUB && op != SFFT_WORD_MUL) return false;
+  for (uint64_t k = 0; k < count; k++) {
+    Word x(F), y(F);
+    for (uint32_t b = 0; b < F; b++) x[b] = c->new_input();
+    for (uint32_t b = 0; b < F; b++) y[b] = c->new_input();
+    Word r = op == SFFT_WORD_ADD ? c->ADD(x, y, SIG_ZERO)
+           : op == SFFT_WORD_SUB ? c->SUB(x, y)
+                                 : c->MULE(x, y, f);
+    c->outputs.insert(c->outputs.end(), r.begin(), r.end());
+  }
+  return true;
+}
+
+int build_circuit(Circuit* c, const CircuitSpec& spec, uint32_t flags) {
+  if (!c->set_variant(flags))
+    return fail(SFFT_EINVAL, "SFFT_PLAN_XCARRY and SFFT_PLAN_NAND are exclusive");
+  if (spec.op == 0) {
+    if (!build_fft(c, spec.N1, spec.N2, spec.F, spec.f))
+      return fail(SFFT_EINVAL,
+                  "N1, N2 must be powers of two, 2 <= F <= 48, f < F (f <= F - 2 with "
+                  "encrypted twiddles)");
+    return SFFT_OK;
+  }
+  if (!build_words(c, spec.op, spec.count, spec.F, spec.f))
+    return fail(SFFT_EINVAL, "word op must be SFFT_WORD_ADD/SUB/MUL, 1 <= count <= 2^24, "
+                             "2 <= F <= 48, f < F");
+  return SFFT_OK;
 }
 
 // ------------------------------------------------------------ noise bound

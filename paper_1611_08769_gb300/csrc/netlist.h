@@ -28,6 +28,14 @@
 // max of its inputs); on the device it runs after the products of its
 // schedule level.
 //
+// Encrypted-operand multiplier (MULE, a variant: the paper multiplies by
+// plaintext constants, whose bits show through the Wallace tree, Sec. 4):
+// both words sign-extended to T = f + F bits, every row i < T present, column
+// c >= i receiving AND(x_ext[c-i], y_ext[i]); the same Wallace stages and
+// final ADD_T as MUL; bits [f, f+F). With Circuit::enc_twiddle the FFT takes
+// one table of encrypted twiddles W_M^k, k < M/2, M = max(N1, N2), as inputs
+// after the signal; a length-n transform uses entry t M/n for W_n^t.
+//
 // NAND-only variant (Circuit::nand, the paper's literal construction, Lemma
 // 4): constants fold first as above; every remaining gate is made of GSW NAND
 // gates (1, 0, 0, -1), one product each: NOT a = NAND(a, a), AND = NOT(NAND),
@@ -68,12 +76,13 @@ struct Circuit {
   uint64_t n_and = 0, n_xor = 0, n_or = 0, n_not = 0, n_xadd = 0;   // logical gates before pruning
   bool xcarry = false;             // full-adder carry as XADD instead of OR
   bool nand = false;               // every gate made of NAND gates
+  bool enc_twiddle = false;        // FFT twiddles are encrypted inputs (MULE)
   // Common subexpressions: identical (kind, A, B) gates give identical
   // ciphertexts, so each is computed once (bit-exact).
   std::unordered_map<uint64_t, int32_t> memo_ha, memo_or, memo_add, memo_nand;
 
-  // Selects the variant from plan flags (SFFT_PLAN_XCARRY, SFFT_PLAN_NAND);
-  // false if both are set.
+  // Selects the variant from plan flags (SFFT_PLAN_XCARRY, SFFT_PLAN_NAND,
+  // SFFT_PLAN_ENC_TWIDDLE); false if both gate variants are set.
   bool set_variant(uint32_t flags);
 
   uint32_t new_node(uint32_t d, int32_t prod);
@@ -81,6 +90,7 @@ struct Circuit {
   uint32_t dep(Sig s) const { return depth[sig_node(s)]; }
 
   Sig NOT(Sig a);
+  Sig AND(Sig a, Sig b);    // the AND output of a half adder (NAND-only: NOT(NAND))
   void HA(Sig a, Sig b, Sig* s, Sig* c);
   Sig OR(Sig a, Sig b);
   Sig XADD(Sig a, Sig b);
@@ -89,11 +99,31 @@ struct Circuit {
   std::vector<Sig> ADD(const std::vector<Sig>& x, const std::vector<Sig>& y, Sig cin);
   std::vector<Sig> SUB(const std::vector<Sig>& x, const std::vector<Sig>& y);
   std::vector<Sig> MUL(const std::vector<Sig>& x, int64_t w, uint32_t f);
+  std::vector<Sig> MULE(const std::vector<Sig>& x, const std::vector<Sig>& y, uint32_t f);
+  // Wallace stages on column lists, then ADD_T of the two rows (T = columns).
+  std::vector<Sig> wallace(std::vector<std::vector<Sig>> col);
 };
 
 // Builds the circuit of a 1-D (N2 == 1) or 2-D FFT. Throws nothing; returns
-// false on invalid sizes.
+// false on invalid sizes (and f > F - 2 with encrypted twiddles).
 bool build_fft(Circuit* c, uint32_t N1, uint32_t N2, uint32_t F, uint32_t f);
+
+// count independent word operations (SFFT_WORD_ADD / SUB / MUL) on pairs of
+// F-bit words: word k's x at inputs (2k) F + b, y at (2k + 1) F + b, result
+// at outputs k F + b. false on invalid sizes.
+bool build_words(Circuit* c, uint32_t op, uint64_t count, uint32_t F, uint32_t f);
+
+// What a plan evaluates: an FFT (op 0) or count word operations (SFFT_WORD_*).
+struct CircuitSpec {
+  uint32_t op = 0;
+  uint32_t N1 = 1, N2 = 1;
+  uint64_t count = 0;
+  uint32_t F = 0, f = 0;
+};
+
+// Selects the variant from flags and builds the circuit; SFFT_OK or the
+// error (recorded as the last error).
+int build_circuit(Circuit* c, const CircuitSpec& spec, uint32_t flags);
 
 // Quantised twiddles W_N^k = exp(-2 pi i k / N), k < N/2, floor to 2^-f.
 void twiddles(uint32_t N, uint32_t f, std::vector<int64_t>* wr, std::vector<int64_t>* wi);

@@ -17,31 +17,42 @@ using namespace sfft;
 
 namespace {
 
-int build(const sfft_params* p, uint32_t N1, uint32_t N2, uint32_t F, uint32_t f, uint32_t flags,
-          Shape* s, Circuit* c, Program* prog) {
+int build(const sfft_params* p, const CircuitSpec& spec, uint32_t flags, Shape* s, Circuit* c,
+          Program* prog) {
   int rc = make_shape(p, s, false);
   if (rc) return rc;
-  if (!c->set_variant(flags))
-    return fail(SFFT_EINVAL, "SFFT_PLAN_XCARRY and SFFT_PLAN_NAND are exclusive");
-  if (!build_fft(c, N1, N2, F, f))
-    return fail(SFFT_EINVAL, "N1, N2 must be powers of two, 2 <= F <= 48, f < F");
+  if ((rc = build_circuit(c, spec, flags))) return rc;
   compile(*c, *s, prog);
   return SFFT_OK;
 }
 
+CircuitSpec fft_spec(uint32_t N1, uint32_t N2, uint32_t F, uint32_t f) {
+  CircuitSpec sp;
+  sp.N1 = N1;
+  sp.N2 = N2;
+  sp.F = F;
+  sp.f = f;
+  return sp;
+}
+
+CircuitSpec word_spec(uint32_t op, uint64_t count, uint32_t F, uint32_t f) {
+  CircuitSpec sp;
+  sp.op = op;
+  sp.count = count;
+  sp.F = F;
+  sp.f = f;
+  return sp;
+}
+
 int nib(uint32_t code, int k) { return (int)((int32_t)(code << (28 - 4 * k)) >> 28); }
 
-}  // namespace
-
-extern "C" {
-
-int sfft_circuit_info(const sfft_params* p, uint32_t N1, uint32_t N2, uint32_t F, uint32_t f,
-                      uint32_t flags, sfft_plan_info* info) {
+int circuit_info(const sfft_params* p, const CircuitSpec& spec, uint32_t flags,
+                 sfft_plan_info* info) {
   if (!info) return fail(SFFT_EINVAL, "info is NULL");
   Shape s;
   Circuit c;
   Program prog;
-  int rc = build(p, N1, N2, F, f, flags, &s, &c, &prog);
+  int rc = build(p, spec, flags, &s, &c, &prog);
   if (rc) return rc;
   std::memset(info, 0, sizeof(*info));
   info->inputs = prog.n_inputs;
@@ -80,13 +91,13 @@ int sfft_circuit_info(const sfft_params* p, uint32_t N1, uint32_t N2, uint32_t F
   return SFFT_OK;
 }
 
-int sfft_program_eval_plain(const sfft_params* p, uint32_t N1, uint32_t N2, uint32_t F,
-                            uint32_t f, uint32_t flags, const uint8_t* h_in_bits, uint8_t* h_out_bits) {
+int program_eval_plain(const sfft_params* p, const CircuitSpec& spec, uint32_t flags,
+                       const uint8_t* h_in_bits, uint8_t* h_out_bits) {
   if (!h_in_bits || !h_out_bits) return fail(SFFT_EINVAL, "null argument");
   Shape s;
   Circuit c;
   Program prog;
-  int rc = build(p, N1, N2, F, f, flags, &s, &c, &prog);
+  int rc = build(p, spec, flags, &s, &c, &prog);
   if (rc) return rc;
   std::vector<int> reg[3];
   reg[REG_SCRATCH].assign(prog.scratch_slots, -1);
@@ -129,6 +140,41 @@ int sfft_program_eval_plain(const sfft_params* p, uint32_t N1, uint32_t N2, uint
     if (reg[REG_OUT][o] < 0) return fail(SFFT_EINVAL, "output never written");
     h_out_bits[o] = (uint8_t)reg[REG_OUT][o];
   }
+  return SFFT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sfft_circuit_info(const sfft_params* p, uint32_t N1, uint32_t N2, uint32_t F, uint32_t f,
+                      uint32_t flags, sfft_plan_info* info) {
+  return circuit_info(p, fft_spec(N1, N2, F, f), flags, info);
+}
+
+int sfft_program_eval_plain(const sfft_params* p, uint32_t N1, uint32_t N2, uint32_t F,
+                            uint32_t f, uint32_t flags, const uint8_t* h_in_bits, uint8_t* h_out_bits) {
+  return program_eval_plain(p, fft_spec(N1, N2, F, f), flags, h_in_bits, h_out_bits);
+}
+
+int sfft_word_circuit_info(const sfft_params* p, uint32_t op, uint64_t count, uint32_t F,
+                           uint32_t f, uint32_t flags, sfft_plan_info* info) {
+  return circuit_info(p, word_spec(op, count, F, f), flags, info);
+}
+
+int sfft_word_program_eval_plain(const sfft_params* p, uint32_t op, uint64_t count, uint32_t F,
+                                 uint32_t f, uint32_t flags, const uint8_t* h_in_bits,
+                                 uint8_t* h_out_bits) {
+  return program_eval_plain(p, word_spec(op, count, F, f), flags, h_in_bits, h_out_bits);
+}
+
+int sfft_twiddles(uint32_t M, uint32_t f, int64_t* h_wr, int64_t* h_wi) {
+  if (M < 2 || (M & (M - 1)) || f > 62) return fail(SFFT_EINVAL, "M must be a power of two >= 2, f <= 62");
+  if (!h_wr || !h_wi) return fail(SFFT_EINVAL, "null argument");
+  std::vector<int64_t> wr, wi;
+  twiddles(M, f, &wr, &wi);
+  std::memcpy(h_wr, wr.data(), wr.size() * sizeof(int64_t));
+  std::memcpy(h_wi, wi.data(), wi.size() * sizeof(int64_t));
   return SFFT_OK;
 }
 

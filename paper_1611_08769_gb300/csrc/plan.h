@@ -80,5 +80,5 @@ struct sfft_plan {
   sfft::Program prog;
   sfft::DeviceProgram dev;
   sfft::Timer timer;
-  uint32_t N1, N2, F, f;
+  sfft::CircuitSpec spec;        // what the plan evaluates (FFT or word operations)
 };

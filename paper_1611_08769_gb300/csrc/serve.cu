@@ -376,7 +376,7 @@ int sfft_server_create(const sfft_params* p, uint64_t hbm_budget_bytes, uint32_t
   int rc = make_shape(p, &sv->s, false);
   if (rc) return rc;
   sv->max_active = max_active ? max_active : 64;
-  sv->variant = flags & (SFFT_PLAN_XCARRY | SFFT_PLAN_NAND);
+  sv->variant = flags & (SFFT_PLAN_XCARRY | SFFT_PLAN_NAND | SFFT_PLAN_ENC_TWIDDLE);
   if (!Circuit().set_variant(sv->variant))
     return fail(SFFT_EINVAL, "SFFT_PLAN_XCARRY and SFFT_PLAN_NAND are exclusive");
   const uint64_t ctb = sv->s.ctw * 4;

@@ -18,6 +18,8 @@ circuit     canonical gate netlist: HA, FA, ADD, SUB, Wallace MUL, butterfly, FF
 fixedpoint  quantisation, twiddles, closed-form integer FFT, FP64 DFT, Thm 2 bound
 noise       static worst-case noise bound and the measured noise of a ciphertext
 evaluate    plaintext and encrypted evaluation of a circuit
+refresh     ciphertext refresh by homomorphic decryption (bootstrapping key,
+            truncated phase sum, refresh circuit, closed form)
 
 Parity status: every function here is pinned by a ``-m "not gpu"`` test
 against something other than itself (see tests/test_oracle_*.py); none is

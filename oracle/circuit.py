@@ -159,6 +159,11 @@ class Circuit:
             return a
         return self._emit("XADD", a, b, max(self.d(a), self.d(b)))
 
+    def SEL(self, a, beta):
+        """beta * a for a public bit beta: a linear gate that is never folded
+        (its structure must not depend on beta; refresh circuits)."""
+        return self._emit("SEL1" if beta else "SEL0", a, None, self.d(a))
+
     # -- adders (Lemmas 5-7) ---------------------------------------------
     def HA(self, a, b):
         if self.nand and a not in (ZERO, ONE) and b not in (ZERO, ONE):
@@ -377,8 +382,8 @@ def word_circuit(kind, F, f=0, w=None, xcarry=False, nand=False):
 
 def stats(c):
     """Counts of each gate kind and of ciphertext products (AND/XOR/OR;
-    XADD and NOT are linear)."""
-    s = {"NOT": 0, "AND": 0, "XOR": 0, "OR": 0, "XADD": 0, "NAND": 0}
+    XADD, NOT and SEL are linear)."""
+    s = {"NOT": 0, "AND": 0, "XOR": 0, "OR": 0, "XADD": 0, "NAND": 0, "SEL0": 0, "SEL1": 0}
     for op, *_ in c.gates:
         s[op] += 1
     # One product per distinct (kind, A, B) after value numbering: an HA's XOR
@@ -394,6 +399,9 @@ def stats(c):
         if op == "NOT":
             base, neg = canon[a]
             canon[o] = (base, 1 - neg)
+            continue
+        if op in ("SEL0", "SEL1"):    # distinct wires whatever their source
+            canon[o] = (o, 0)
             continue
         A, B = (b, a) if c.d(b) > c.d(a) else (a, b)
         key = (op, canon[A], canon[B])

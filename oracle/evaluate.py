@@ -18,6 +18,8 @@ TRUTH = {
     "OR": lambda a, b: a | b,
     "XADD": lambda a, b: _exclusive_sum(a, b),
     "NAND": lambda a, b: 1 - (a & b),
+    "SEL1": lambda a, b: a,
+    "SEL0": lambda a, b: 0,
 }
 
 

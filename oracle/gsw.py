@@ -51,6 +51,10 @@ GATE_CODES = {
     # a + b for two bits that are never both 1 (the carries of a full adder):
     # linear, no product; equals OR on every input it is applied to
     "XADD": (0, 1, 1, 0),
+    # beta C for a public bit beta (refresh: a bootstrapping-key ciphertext
+    # selected by a bit of the refreshed ciphertext); linear
+    "SEL1": (0, 1, 0, 0),
+    "SEL0": (0, 0, 0, 0),
 }
 
 

@@ -14,7 +14,13 @@ fft16x16_image_noisy (2-D row-column FFT of a 16 x 16 image, 10.6 words),
 batch256_p2 (256 independent 1-D FFTs, N in {16..128}, F in {16, 24}, four
 client key sets, one graph-replayed level-merged batch; noise-free ell 128),
 fft64_16bit_xcarry (the default workload built with exclusive-carry full
-adders, a circuit variant: fewer products, its own smaller ell).
+adders, a circuit variant: fewer products, its own smaller ell),
+fft8_8bit_nand (8-point 8-bit FFT built from NAND gates only, the paper's
+literal gate construction, at its own smallest ell), fft64_16bit_enctw_xcarry
+(the default workload with encrypted twiddles and the encrypted-operand
+multiplier, exclusive-carry adders), refresh32_noisy (refresh by homomorphic
+decryption of 32 ciphertexts at the default workload's ell; metric:
+refreshed ciphertexts/s).
 
 Keys beyond the base contract:
   roofline      the gate-product kernel against its peak (tensor or ALU)
@@ -54,6 +60,14 @@ CONFIGS = {
     # circuit variant: exclusive-carry full adders (linear carry gates, smaller ell)
     "fft64_16bit_xcarry": dict(kind="fft", N1=64, N2=1, F=16, f=8, lo=-8.0, hi=8.0, pset="P1",
                                xcarry=True),
+    # the paper's literal NAND-only gates
+    "fft8_8bit_nand": dict(kind="fft", N1=8, N2=1, F=8, f=4, lo=-1.0, hi=1.0, pset="P1",
+                           nand=True),
+    # encrypted twiddles (encrypted-operand Wallace multiplier), exclusive-carry adders
+    "fft64_16bit_enctw_xcarry": dict(kind="fft", N1=64, N2=1, F=16, f=8, lo=-8.0, hi=8.0,
+                                     pset="P1", xcarry=True, enc_twiddle=True),
+    # refresh of 32 ciphertexts at the ell of the 64-point 16-bit workload
+    "refresh32_noisy": dict(kind="refresh", count=32, pset="P1", ell_of=(64, 1, 16, 8)),
     "batch256_p2": dict(kind="batch", count=256, pset="P2", key_sets=4),
     "serve_p2": dict(kind="serve", pset="P2", key_sets=8, requests=400, calib=48),
 }
@@ -179,15 +193,36 @@ def roofline(params, gate_kernel, gate_ms, launches, gates_timed, tc_columns=0):
             "peak_source": "derived: 152 SMs x 128 INT32 lanes x 2.07 GHz"}
 
 
-def xcarry_of(cfg):
-    return bool(CONFIGS[cfg].get("xcarry", False))
+def variant_of(cfg):
+    """Circuit variant switches of a config (keyword arguments of min_ell and
+    the oracle's fft_circuit)."""
+    c = CONFIGS[cfg]
+    return {k: bool(c.get(k, False)) for k in ("xcarry", "nand", "enc_twiddle")}
 
 
-def params_for(sf, pset, dims_list, xcarry=False):
+def flags_of(sf, cfg):
+    v = variant_of(cfg)
+    return ((sf.PLAN_XCARRY if v["xcarry"] else 0) | (sf.PLAN_NAND if v["nand"] else 0)
+            | (sf.PLAN_ENC_TWIDDLE if v["enc_twiddle"] else 0))
+
+
+def params_for(sf, pset, dims_list, variant=None):
     if pset == "P1":
-        ell = max(sf.min_ell(*d, n=1, chi=1, xcarry=xcarry) for d in dims_list)
+        ell = max(sf.min_ell(*d, n=1, chi=1, **(variant or {})) for d in dims_list)
         return sf.param_set("P1", ell)
     return sf.param_set(pset)
+
+
+def fft_inputs(sf, dims, re_, im_, enc_twiddle):
+    """(re, im) values encrypted for one request: the signal, then (with
+    encrypted twiddles) the twiddle table W_M^k, M = max(N1, N2), as exact
+    fixed-point values."""
+    N1, N2, F, f = dims
+    if not enc_twiddle:
+        return list(re_), list(im_)
+    wr, wi = sf.twiddles(max(N1, N2), f)
+    return (list(re_) + [w / 2 ** f for w in wr.tolist()],
+            list(im_) + [w / 2 ** f for w in wi.tolist()])
 
 
 def fft_workload(cfg):
@@ -196,7 +231,7 @@ def fft_workload(cfg):
     from synthetic import image_2d, signal_1d
     c = CONFIGS[cfg]
     dims = (c["N1"], c["N2"], c["F"], c["f"])
-    params = params_for(sf, c["pset"], [dims], xcarry_of(cfg))
+    params = params_for(sf, c["pset"], [dims], variant_of(cfg))
     if c["N2"] == 1:
         re_, im_ = signal_1d(c["N1"], c["lo"], c["hi"], seed=0)
     else:
@@ -223,6 +258,13 @@ def serve_workload(cfg):
                                      for r in trace]
 
 
+def refresh_workload(cfg):
+    """(params, count): the refresh config's parameters and batch size."""
+    import paper_1611_08769_gb300 as sf
+    c = CONFIGS[cfg]
+    return sf.param_set("P1", sf.min_ell(*c["ell_of"], n=1, chi=1)), c["count"]
+
+
 def workload(cfg):
     kind = CONFIGS[cfg]["kind"]
     if kind == "batch":
@@ -232,15 +274,11 @@ def workload(cfg):
     return fft_workload(cfg)
 
 
-def cpu_oracle_sample(params, items, budget_s, xcarry=False):
-    """Oracle on a bounded prefix of the first request's circuit.
-
-    Returns (FFTs/s, gates/s, description). FFT time is the per-gate time
-    times the mean oracle gate count of the workload's distinct FFT shapes."""
-    from oracle import circuit, fixedpoint as fx, gsw
-    p = gsw.Params(params.n, params.ell, params.m, params.chi)
-    (N1, N2, F, f), re_, im_, _, _ = items[0]
-    c = circuit.fft_circuit(N1, N2, F, f, xcarry=xcarry)
+def oracle_gate_prefix(c, p, input_bit, budget_s):
+    """Times the oracle's gates of circuit c in order until budget_s of gate
+    time is spent. Inputs are encrypted on first use (untimed); input_bit(w)
+    gives the plaintext bit of input wire w. Returns (gates done, seconds)."""
+    from oracle import circuit, gsw
     keys = gsw.Keys(p, 0)
     cts = {}
     zero, one = gsw.zero_ct(p), gsw.one_ct(p)
@@ -250,11 +288,8 @@ def cpu_oracle_sample(params, items, budget_s, xcarry=False):
             return zero
         if w == circuit.ONE:
             return one
-        if w not in cts:   # inputs (wires 0 .. 2F N - 1) are encrypted on first use, untimed
-            sample, rem = divmod(w, 2 * F)
-            part, bit = divmod(rem, F)
-            x = re_[sample] if part == 0 else im_[sample]
-            cts[w] = gsw.encrypt(keys, fx.to_bits(fx.quantize(x, F, f), F)[bit], 0, w)
+        if w not in cts:
+            cts[w] = gsw.encrypt(keys, input_bit(w), 0, w)
         return cts[w]
 
     done, dt = 0, 0.0
@@ -267,52 +302,216 @@ def cpu_oracle_sample(params, items, budget_s, xcarry=False):
         done += 1
         if dt > budget_s:
             break
+    return done, dt
+
+
+def cpu_oracle_sample(params, items, budget_s, variant=None):
+    """Oracle on a bounded prefix of the first request's circuit.
+
+    Returns (FFTs/s, gates/s, description). FFT time is the per-gate time
+    times the mean oracle gate count of the workload's distinct FFT shapes."""
+    import paper_1611_08769_gb300 as sf
+    from oracle import circuit, fixedpoint as fx, gsw
+    variant = variant or {}
+    p = gsw.Params(params.n, params.ell, params.m, params.chi)
+    (N1, N2, F, f), re_, im_, _, _ = items[0]
+    c = circuit.fft_circuit(N1, N2, F, f, **variant)
+    re_all, im_all = fft_inputs(sf, (N1, N2, F, f), re_, im_, variant.get("enc_twiddle", False))
+
+    def input_bit(w):   # wire (sample * 2 + part) * F + bit, twiddles after the signal
+        sample, rem = divmod(w, 2 * F)
+        part, bit = divmod(rem, F)
+        x = re_all[sample] if part == 0 else im_all[sample]
+        return fx.to_bits(fx.quantize(x, F, f), F)[bit]
+
+    done, dt = oracle_gate_prefix(c, p, input_bit, budget_s)
     per_gate = dt / done
     shapes = sorted({d for d, *_ in items})
-    sizes = {d: (len(c.gates) if d == (N1, N2, F, f) else len(circuit.fft_circuit(*d, xcarry=xcarry).gates))
-             for d in shapes}
+    sizes = {d: (len(c.gates) if d == (N1, N2, F, f) else
+                 len(circuit.fft_circuit(*d, **variant).gates)) for d in shapes}
     mean_gates = sum(sizes[d] for d, *_ in items) / len(items)
     fft_s = per_gate * mean_gates
-    detail = (f"first {done} of {len(c.gates)} oracle gates (AND/XOR/OR/NOT evaluated separately) "
+    detail = (f"first {done} of {len(c.gates)} oracle gates (each logical gate evaluated separately) "
               f"of the {N1}x{N2} F={F} circuit at the same parameters, {dt:.1f} s; FFT time "
               f"extrapolated to {fft_s:.1f} s from the mean oracle gate count {mean_gates:.0f}")
     return 1.0 / fft_s, done / dt, detail
 
 
+def cpu_refresh_sample(params, count, budget_s, xcarry=False):
+    """Oracle on a bounded prefix of one refresh circuit (the worst-case
+    selection: every key ciphertext selected). Returns (refreshes/s, gates/s,
+    description); the time per refresh is extrapolated from the per-gate time."""
+    from oracle import gsw, refresh
+    p = gsw.Params(params.n, params.ell, params.m, params.chi)
+    c = refresh.refresh_circuit(p, [None], xcarry=xcarry)
+    done, dt = oracle_gate_prefix(c, p, lambda w: w % 2, budget_s)
+    per = dt / done * len(c.gates)
+    detail = (f"first {done} of {len(c.gates)} oracle gates of one refresh circuit (every key "
+              f"ciphertext selected) at the same parameters, {dt:.1f} s; time per refreshed "
+              f"ciphertext extrapolated to {per:.1f} s")
+    return 1.0 / per, done / dt, detail
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    params, items = workload(args.config)
     budget = max(1.0, args.cpu_seconds / max(1, args.steps + args.warmup))
     vals = []
     detail = ""
+    if CONFIGS[args.config]["kind"] == "refresh":
+        params, count = refresh_workload(args.config)
+        metric, unit = "refreshed ciphertexts/s", "ct/s"
+        cfg = refresh_config_json(args.config, params, count)
+        sample = lambda: cpu_refresh_sample(params, count, budget,  # noqa: E731
+                                            variant_of(args.config)["xcarry"])
+    else:
+        params, items = workload(args.config)
+        metric, unit = "encrypted FFTs/s", "FFT/s"
+        cfg = config_json(args.config, params, items)
+        sample = lambda: cpu_oracle_sample(params, items, budget,  # noqa: E731
+                                           variant_of(args.config))
     for s in range(args.warmup + args.steps):
-        fps, gps, detail = cpu_oracle_sample(params, items, budget, xcarry_of(args.config))
+        fps, gps, detail = sample()
         if s >= args.warmup:
             vals.append(fps)
     v = statistics.mean(vals)
-    line = {"impl": "reference", "metric": "encrypted FFTs/s", "value": v, "unit": "FFT/s",
+    line = {"impl": "reference", "metric": metric, "value": v, "unit": unit,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 / v, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": config_json(args.config, params, items),
-            "cpu_baseline": {"value": v, "unit": "FFT/s", "cores": os.cpu_count(), "kind": "oracle",
+            "config": cfg,
+            "cpu_baseline": {"value": v, "unit": unit, "cores": os.cpu_count(), "kind": "oracle",
                              "sample": detail},
-            "e2e": {"value": v, "unit": "FFT/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "e2e": {"value": v, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+CIRCUIT_NOTES = {
+    "xcarry": "exclusive-carry full adders (variant; carries are linear gates)",
+    "nand": "every gate built of GSW NAND gates (the paper's literal construction)",
+    "enc_twiddle": "twiddles encrypted (inputs after the signal), encrypted-operand multiplier",
+}
 
 
 def config_json(cfg, params, items):
     out = {"workload": cfg, "n": params.n, "ell": params.ell, "m": params.m, "chi": params.chi,
            "requests": len(items)}
-    if xcarry_of(cfg):
-        out["circuit"] = "exclusive-carry full adders (variant; carries are linear gates)"
+    notes = [CIRCUIT_NOTES[k] for k, on in variant_of(cfg).items() if on]
+    if notes:
+        out["circuit"] = "; ".join(notes)
     if len(items) == 1:
         (N1, N2, F, f), *_ = items[0]
         out.update({"N1": N1, "N2": N2, "F": F, "f": f})
     else:
         out["key_sets"] = len({it[3] for it in items})
     return out
+
+
+def refresh_config_json(cfg, params, count):
+    out = {"workload": cfg, "n": params.n, "ell": params.ell, "m": params.m, "chi": params.chi,
+           "refreshed_per_step": count,
+           "circuit": "homomorphic decryption of row ell - 1: Wallace sum of the top "
+                      "ceil(log2(n ell + 1)) + 3 bits of n ell + 1 selected key ciphertexts"}
+    notes = [CIRCUIT_NOTES[k] for k, on in variant_of(cfg).items() if on]
+    if notes:
+        out["circuit"] += "; " + "; ".join(notes)
+    return out
+
+
+def run_refresh(args):
+    """Refresh of `count` ciphertexts per step (rank 0; replicas elsewhere)."""
+    import torch
+
+    import paper_1611_08769_gb300 as sf
+    from paper_1611_08769_gb300 import build as sfbuild
+    sfbuild.build()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank = int(os.environ.get("RANK", "0"))
+    torch.cuda.set_device(local)
+    params, count = refresh_workload(args.config)
+    flags = (sf.PLAN_INT_KERNEL if args.kernel == "int" else 0) | flags_of(sf, args.config)
+    cw = sf.ct_words(params)
+    keys = sf.keygen(params, 3000)
+    pub = torch.from_numpy(keys.public().view(np.int32)).cuda()
+    kb = keys.key_bits()
+    d_bk = torch.empty((len(kb), cw), dtype=torch.int32, device="cuda")
+    sf.encrypt_raw_bits_device(params, pub, kb, 11, d_bk)
+    rng = np.random.default_rng(12)
+    src_bits = rng.integers(0, 2, size=count).astype(np.uint8)
+    d_src = torch.empty((count, cw), dtype=torch.int32, device="cuda")
+    sf.encrypt_raw_bits_device(params, pub, src_bits, 13, d_src)
+    plan = sf.Plan.refresher(params, count, flags)
+    info = plan.info
+    d_out = torch.empty((count, cw), dtype=torch.int32, device="cuda")
+    scratch = torch.empty(max(1, info["scratch_bytes"] // 4), dtype=torch.int32, device="cuda")
+    stream = torch.cuda.Stream()
+    run = lambda: plan.refresh(d_bk, d_src, d_out, scratch, stream)  # noqa: E731
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            run()
+        plan.check(stream)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n0 = sf.lib().sfft_launch_count()
+        with ClockSampler(local) as clk:
+            ev0.record(stream)
+            for _ in range(args.steps):
+                run()
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        launches_timed = sf.lib().sfft_launch_count() - n0
+        ms = ev0.elapsed_time(ev1) / args.steps
+        plan.check(stream)
+        plan.set_timing(True)
+        run()
+        gate_ms, launches, gates_timed = plan.timing()
+        plan.set_timing(False)
+        # end to end: sources from pinned host memory, refreshed ciphertexts back
+        h_src = d_src.cpu().pin_memory()
+        h_out = torch.empty((count, cw), dtype=torch.int32).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            d_src.copy_(h_src, non_blocking=True)
+            run()
+            h_out.copy_(d_out, non_blocking=True)
+            stream.synchronize()
+        e2e_ms = (time.perf_counter() - t0) * 1000.0 / args.steps
+    # the refreshed bits decrypt to the sources
+    rows = d_out.view(count, -1)[:, (params.ell - 1) * (params.n + 1) * params.ell // 32:
+                                 params.ell * (params.n + 1) * params.ell // 32]
+    raw = sf.decrypt(keys, rows.cpu().numpy().view(np.uint32), (params.n + 1) * params.ell // 32,
+                     count // 4, 2, 0)[2]   # 2-bit words: ciphertext i is bit i % 2 of word i // 2
+    ok = [(int(raw[i // 2]) >> (i % 2)) & 1 for i in range(count // 4 * 4)] == \
+        [int(b) for b in src_bits[:count // 4 * 4]]
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        v, gps, detail = cpu_refresh_sample(params, count, args.cpu_seconds,
+                                            variant_of(args.config)["xcarry"])
+        cpu = {"value": v, "unit": "ct/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": detail, "gates_per_s": gps}
+    if rank != 0:
+        return
+    cfg = refresh_config_json(args.config, params, count)
+    cfg.update({"products_per_step": info["products"], "levels": info["levels"],
+                "l2": f"bootstrapping key {len(kb) * cw * 4 / 1e9:.2f} GB (> L2 129 MB)",
+                "sources": "fresh encryptions of seeded random bits",
+                "decrypts_to_sources": ok})
+    line = {
+        "metric": "refreshed ciphertexts/s", "value": count * 1000.0 / ms, "unit": "ct/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic", "config": cfg,
+        "gates_per_s": info["products"] * 1000.0 / ms,
+        "roofline": roofline(params, info["gate_kernel"], gate_ms, launches, gates_timed,
+                             info["tc_columns"]),
+        "cpu_baseline": cpu,
+        "e2e": {"value": count * 1000.0 / e2e_ms, "unit": "ct/s",
+                "h2d_bytes_per_step": count * cw * 4, "d2h_bytes_per_step": count * cw * 4},
+        "gpu_launches": launches_timed,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
 
 
 def run_gates(args):
@@ -449,6 +648,8 @@ def main():
         return run_gates(args)
     if CONFIGS[args.config]["kind"] == "serve":
         return run_serve(args) if rank == 0 else None
+    if CONFIGS[args.config]["kind"] == "refresh":
+        return run_refresh(args)
 
     import torch
     import torch.distributed as dist
@@ -461,9 +662,8 @@ def main():
     torch.cuda.set_device(local)
     sfbuild.build()
     params, items = workload(args.config)
-    flags = sf.PLAN_INT_KERNEL if args.kernel == "int" else 0
-    if xcarry_of(args.config):
-        flags |= sf.PLAN_XCARRY
+    flags = (sf.PLAN_INT_KERNEL if args.kernel == "int" else 0) | flags_of(sf, args.config)
+    enc_tw = variant_of(args.config)["enc_twiddle"]
     cw = sf.ct_words(params)
     reqs = [d for d, *_ in items]
 
@@ -474,8 +674,9 @@ def main():
     info = batch.info
     d_in = torch.empty((info["inputs"], cw), dtype=torch.int32, device="cuda")
     for r, ((N1, N2, F, f), re_, im_, ks, seed) in enumerate(items):
-        n = N1 * N2 * 2 * F
-        sf.encrypt_bits_device(params, pubs[ks], re_, im_, F, f, seed,
+        re_all, im_all = fft_inputs(sf, (N1, N2, F, f), re_, im_, enc_tw)
+        n = len(re_all) * 2 * F
+        sf.encrypt_bits_device(params, pubs[ks], re_all, im_all, F, f, seed,
                                d_in[batch.in_off[r]:batch.in_off[r] + n])
     d_out = torch.empty((info["outputs"], cw), dtype=torch.int32, device="cuda")
     scratch = torch.empty(max(1, info["scratch_bytes"] // 4), dtype=torch.int32, device="cuda")
@@ -559,7 +760,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        fps, gps, detail = cpu_oracle_sample(params, items, args.cpu_seconds, xcarry_of(args.config))
+        fps, gps, detail = cpu_oracle_sample(params, items, args.cpu_seconds, variant_of(args.config))
         cpu = {"value": fps, "unit": "FFT/s", "cores": os.cpu_count(), "kind": "oracle",
                "sample": detail, "gates_per_s": gps}
 

@@ -101,6 +101,18 @@ int sfft_encrypt_bits_device(const sfft_params* p, const uint32_t* d_pub,
                              uint32_t F, uint32_t f, uint64_t enc_seed,
                              uint32_t* d_ct_out, void* stream);
 
+/* GPU encryption of count arbitrary bits h_bits[c] in {0, 1} (EINVAL
+ * otherwise) as ciphertext index c under enc_seed (the randomness layout of
+ * sfft_encrypt_bits_device). Used for bootstrapping keys (sfft_key_bits). */
+int sfft_encrypt_raw_bits_device(const sfft_params* p, const uint32_t* d_pub,
+                                 const uint8_t* h_bits, uint64_t count, uint64_t enc_seed,
+                                 uint32_t* d_ct_out, void* stream);
+
+/* The bits a bootstrapping key encrypts (client side; sfft_refresh): h_bits[0]
+ * = 1 (s_0 = 1), then bit b of s_j = -t_j mod q at 1 + (j - 1) ell + b, for
+ * j = 1..n, b < ell. cap >= n ell + 1 bytes (EINVAL otherwise). */
+int sfft_key_bits(const sfft_keys* k, uint8_t* h_bits, uint64_t cap);
+
 /* Step 6, Dec (GSW'13; Lemma 2): x = <C'_{ell-1}, s> mod q, bit = [q/4 <= x
  * < 3q/4], words reassembled LSB first, value = signed word / 2^f.
  * h_rows points at row ell-1 of ciphertext 0; ciphertext j's row is
@@ -184,6 +196,34 @@ int sfft_plan_create(const sfft_params* p, uint32_t N1, uint32_t N2, uint32_t F,
 int sfft_plan_info_get(const sfft_plan* plan, sfft_plan_info* info);
 void sfft_plan_free(sfft_plan* plan);
 
+/* Refresh (bootstrapping; Sec. 5 closes by pointing at refreshing, without a
+ * construction): count ciphertexts are decrypted homomorphically under a
+ * bootstrapping key, giving fresh-noise encryptions of the same bits. Row
+ * ell - 1 of a ciphertext, c = (c_0..c_n), has phase x = <c, s> = sum_r K_r
+ * sigma_r (mod q) with sigma_0 = 1, K_0 = c_0, and sigma_{j,b} = bit b of
+ * s_j, K_{j,b} = c_j 2^b mod q. The circuit sums the top p = ceil(log2(n ell
+ * + 1)) + 3 bits of every K_r (Lemma 8's Wallace stages, Lemma 7's ripple
+ * adder, mod 2^p) and outputs [the top two bits of the sum differ]: the
+ * decryption of c whenever its phase noise lies in [-q/8, q/4). Every term
+ * is a bootstrapping-key ciphertext selected by a bit of c (a linear gate
+ * beta C): the gate program is fixed, and each run patches the selected
+ * gates' coefficients from the source ciphertexts on the device.
+ * sfft_refresh_plan_create: inputs n ell + 1 (the bootstrapping key, i.e.
+ * encryptions of sfft_key_bits), outputs count; EPARAM if the output's static
+ * noise bound reaches q/8 (it could not be refreshed again) unless
+ * SFFT_PLAN_ALLOW_NOISY. flags: SFFT_PLAN_INT_KERNEL and the gate variants. */
+int sfft_refresh_plan_create(const sfft_params* p, uint64_t count, uint32_t flags,
+                             sfft_plan** out);
+/* Smallest ell (multiple of 32, m = Ng) whose refresh output bound stays
+ * below q/8; 0 if none up to 8192. */
+uint32_t sfft_refresh_min_ell(uint32_t n, uint32_t chi, uint32_t flags);
+/* d_bk: the n ell + 1 bootstrapping-key ciphertexts; d_src: the count
+ * ciphertexts to refresh (only their rows ell - 1 are read); d_out: count
+ * refreshed ciphertexts; scratch as sfft_eval_fft. One run at a time per plan
+ * (the run rewrites the plan's gate coefficients). */
+int sfft_refresh(sfft_plan* plan, const uint32_t* d_bk, const uint32_t* d_src, uint32_t* d_out,
+                 uint32_t* d_scratch, uint64_t scratch_bytes, void* stream);
+
 /* Word circuits: count independent operations on pairs of encrypted F-bit
  * two's-complement words (x, y), evaluated like an FFT plan (sfft_eval_fft and
  * sfft_eval_fft_host take any plan). Word k's x is input (2k) F + b, its y
@@ -243,6 +283,16 @@ int sfft_circuit_info(const sfft_params* p, uint32_t N1, uint32_t N2, uint32_t F
  * h_out_bits: info.outputs bytes. */
 int sfft_program_eval_plain(const sfft_params* p, uint32_t N1, uint32_t N2, uint32_t F,
                             uint32_t f, uint32_t flags, const uint8_t* h_in_bits,
+                            uint8_t* h_out_bits);
+
+/* Host-only hooks of a refresh program: statistics, and a plaintext run with
+ * key bits h_key_bits (n ell + 1 bytes) and the rows ell - 1 of the count
+ * refreshed ciphertexts h_rows ((n + 1) ell / 32 words each), writing count
+ * bits. */
+int sfft_refresh_circuit_info(const sfft_params* p, uint64_t count, uint32_t flags,
+                              sfft_plan_info* info);
+int sfft_refresh_eval_plain(const sfft_params* p, uint64_t count, uint32_t flags,
+                            const uint8_t* h_key_bits, const uint32_t* h_rows,
                             uint8_t* h_out_bits);
 
 /* The same two host-only hooks for word circuits (sfft_word_plan_create). */

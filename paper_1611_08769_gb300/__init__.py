@@ -26,7 +26,8 @@ KERNEL_AUTO, KERNEL_INT, KERNEL_TC = 0, 1, 2
 
 __all__ = ["Params", "Keys", "Plan", "keygen", "encrypt_bits", "encrypt_bits_device", "decrypt",
            "gather_dec_rows", "min_ell", "gate_level", "ct_words", "SfftError", "version",
-           "word_min_ell", "word_circuit_info", "twiddles"]
+           "word_min_ell", "word_circuit_info", "twiddles", "refresh_min_ell",
+           "refresh_circuit_info", "refresh_eval_plain", "encrypt_raw_bits_device"]
 
 PARAM_SETS = {
     # toy, noise-free (chi = 0): exact decryption at any depth; insecure by construction
@@ -86,6 +87,13 @@ class Keys:
         check(lib().sfft_keys_public(self._h, out.ctypes.data_as(native.c_u32_p), out.size))
         return out
 
+    def key_bits(self):
+        """The n ell + 1 bits a bootstrapping key encrypts (sfft_key_bits)."""
+        p = self.params
+        out = np.zeros(p.n * p.ell + 1, dtype=np.uint8)
+        check(lib().sfft_key_bits(self._h, out.ctypes.data_as(native.c_u8_p), out.size))
+        return out
+
     def __del__(self):
         h = getattr(self, "_h", None)
         if h is not None and h.value:
@@ -117,6 +125,14 @@ def encrypt_bits_device(params, d_pub, re, im, F, f, enc_seed, d_out, stream=Non
         ctypes.byref(params), _dptr(d_pub), re.ctypes.data_as(native.c_double_p),
         None if im is None else im.ctypes.data_as(native.c_double_p), len(re), F, f, enc_seed,
         _dptr(d_out), _stream(stream)))
+
+
+def encrypt_raw_bits_device(params, d_pub, bits, enc_seed, d_out, stream=None):
+    """GPU encryption of arbitrary bits, ciphertext c = bits[c] (sfft_encrypt_raw_bits_device)."""
+    bits = np.ascontiguousarray(bits, dtype=np.uint8)
+    check(lib().sfft_encrypt_raw_bits_device(ctypes.byref(params), _dptr(d_pub),
+                                             bits.ctypes.data_as(native.c_u8_p), bits.size,
+                                             enc_seed, _dptr(d_out), _stream(stream)))
 
 
 def decrypt(keys, rows, row_stride_words, count, F, f):
@@ -192,6 +208,32 @@ def word_program_eval_plain(params, op, count, F, f, in_bits, xcarry=False, nand
     return out
 
 
+def refresh_min_ell(n=1, chi=1, xcarry=False, nand=False):
+    return int(lib().sfft_refresh_min_ell(n, chi, _variant(xcarry, nand)))
+
+
+def refresh_circuit_info(params, count, xcarry=False, nand=False):
+    """Host-only statistics of a refresh program (sfft_refresh_circuit_info)."""
+    info = sfft_plan_info()
+    check(lib().sfft_refresh_circuit_info(ctypes.byref(params), count, _variant(xcarry, nand),
+                                          ctypes.byref(info)))
+    return _info_dict(info)
+
+
+def refresh_eval_plain(params, key_bits, rows, xcarry=False, nand=False):
+    """Host-only plaintext run of a refresh program: rows = (count, (n+1) ell/32)
+    uint32 rows ell - 1 of the refreshed ciphertexts; returns count bits."""
+    rows = np.ascontiguousarray(rows, dtype=np.uint32)
+    count = rows.shape[0]
+    key_bits = np.ascontiguousarray(key_bits, dtype=np.uint8)
+    out = np.zeros(count, dtype=np.uint8)
+    check(lib().sfft_refresh_eval_plain(ctypes.byref(params), count, _variant(xcarry, nand),
+                                        key_bits.ctypes.data_as(native.c_u8_p),
+                                        rows.ctypes.data_as(native.c_u32_p),
+                                        out.ctypes.data_as(native.c_u8_p)))
+    return out
+
+
 def twiddles(M, f):
     """Quantised twiddles W_M^k, k < M/2, as two int64 arrays (sfft_twiddles)."""
     wr = np.zeros(M // 2, dtype=np.int64)
@@ -229,6 +271,25 @@ class Plan:
         check(lib().sfft_plan_info_get(h, ctypes.byref(info)))
         self.info = _info_dict(info)
         return self
+
+    @classmethod
+    def refresher(cls, params, count, flags=0):
+        """Refresh of count ciphertexts (sfft_refresh_plan_create); run with refresh()."""
+        self = cls.__new__(cls)
+        self.params = params
+        self.N1 = self.N2 = self.F = self.f = None
+        h = ctypes.c_void_p()
+        check(lib().sfft_refresh_plan_create(ctypes.byref(params), count, flags, ctypes.byref(h)))
+        self._h = h
+        info = sfft_plan_info()
+        check(lib().sfft_plan_info_get(h, ctypes.byref(info)))
+        self.info = _info_dict(info)
+        return self
+
+    def refresh(self, d_bk, d_src, d_out, d_scratch, stream=None):
+        nbytes = 0 if d_scratch is None else d_scratch.numel() * d_scratch.element_size()
+        check(lib().sfft_refresh(self._h, _dptr(d_bk), _dptr(d_src), _dptr(d_out),
+                                 _dptr(d_scratch), nbytes, _stream(stream)))
 
     def eval_fft(self, d_in, d_out, d_scratch, stream=None):
         nbytes = 0 if d_scratch is None else d_scratch.numel() * d_scratch.element_size()

@@ -155,6 +155,11 @@ int make_device_program(const Program& p, DeviceProgram* dp) {
   if ((rc = upload(p.fix.data(), p.fix.size() * sizeof(FixDesc), &ptr))) return rc;
   dp->fix = (FixDesc*)ptr;
   dp->n_fix = p.fix.size();
+  if (!p.patch.empty()) {
+    if ((rc = upload(p.patch.data(), p.patch.size() * sizeof(PatchDesc), &ptr))) return rc;
+    dp->patch = (PatchDesc*)ptr;
+    dp->n_patch = p.patch.size();
+  }
   dp->level_off = p.level_off;
   dp->lin_start = p.lin_start;
   dp->scratch_slots = p.scratch_slots;
@@ -180,7 +185,10 @@ void free_device_program(DeviceProgram* dp) {
   cudaFree(dp->desc);
   cudaFree(dp->aux);
   cudaFree(dp->fix);
+  cudaFree(dp->patch);
   cudaFree(dp->err);
+  dp->patch = nullptr;
+  dp->n_patch = 0;
   dp->err = nullptr;
   dp->desc = nullptr;
   dp->aux = nullptr;
@@ -214,8 +222,13 @@ int plan_create(const sfft_params* p, const CircuitSpec& spec, uint32_t flags, s
   if (rc) return rc;
   if ((rc = build_circuit(&pl->circuit, spec, flags))) return rc;
   compile(pl->circuit, pl->s, &pl->prog);
-  if (!pl->prog.noise_ok && !(flags & SFFT_PLAN_ALLOW_NOISY))
+  if (spec.op == kOpRefresh) {   // refreshed outputs must be refreshable again
+    if (pl->prog.noise_bits > pl->s.ell - 3 && !(flags & SFFT_PLAN_ALLOW_NOISY))
+      return fail(SFFT_EPARAM, "refresh output bound reaches q/8: raise ell "
+                               "(see sfft_refresh_min_ell)");
+  } else if (!pl->prog.noise_ok && !(flags & SFFT_PLAN_ALLOW_NOISY)) {
     return fail(SFFT_EPARAM, "static noise bound reaches q/4: raise ell (see sfft_min_ell)");
+  }
   if ((rc = make_device_program(pl->prog, &pl->dev))) {
     free_device_program(&pl->dev);
     return rc;
@@ -311,8 +324,56 @@ void sfft_plan_free(sfft_plan* pl) {
 int sfft_eval_fft(sfft_plan* pl, const uint32_t* d_in, uint32_t* d_out, uint32_t* d_scratch,
                   uint64_t scratch_bytes, void* stream) {
   if (!pl) return fail(SFFT_EINVAL, "plan is NULL");
+  if (pl->dev.n_patch) return fail(SFFT_EINVAL, "a refresh plan runs through sfft_refresh");
   return run_program(pl->s, pl->dev, d_in, d_out, d_scratch, scratch_bytes, (cudaStream_t)stream,
                      &pl->timer);
+}
+
+int sfft_refresh_plan_create(const sfft_params* p, uint64_t count, uint32_t flags,
+                             sfft_plan** out) {
+  CircuitSpec spec;
+  spec.op = kOpRefresh;
+  spec.count = count;
+  spec.n = p ? p->n : 0;
+  spec.ell = p ? p->ell : 0;
+  return plan_create(p, spec, flags, out);
+}
+
+uint32_t sfft_refresh_min_ell(uint32_t n, uint32_t chi, uint32_t flags) {
+  for (uint32_t ell = 32; ell <= 8192; ell += 32) {
+    sfft_params p{n, ell, (n + 1) * ell, chi};
+    Shape s;
+    if (make_shape(&p, &s, false)) return 0;
+    CircuitSpec spec;
+    spec.op = kOpRefresh;
+    spec.count = 1;
+    spec.n = n;
+    spec.ell = ell;
+    Circuit c;
+    if (build_circuit(&c, spec, flags)) {
+      set_error("");
+      continue;   // ell too small for the p-bit sum
+    }
+    if (noise_bits(c, s) <= ell - 3) return ell;
+  }
+  return 0;
+}
+
+int sfft_refresh(sfft_plan* pl, const uint32_t* d_bk, const uint32_t* d_src, uint32_t* d_out,
+                 uint32_t* d_scratch, uint64_t scratch_bytes, void* stream) {
+  if (!pl || !d_src) return fail(SFFT_EINVAL, "null argument");
+  if (pl->spec.op != kOpRefresh) return fail(SFFT_EINVAL, "not a refresh plan");
+  cudaStream_t st = (cudaStream_t)stream;
+  const uint64_t n = pl->dev.n_patch;
+  if (n) {
+    k_patch_codes<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+        pl->dev.patch, n, pl->dev.aux, d_src, pl->s.ctw, (pl->s.ell - 1) * pl->s.W, pl->s.L,
+        pl->s.ell);
+    count_launches(1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "code patch launch");
+  }
+  return run_program(pl->s, pl->dev, d_bk, d_out, d_scratch, scratch_bytes, st, &pl->timer);
 }
 
 int sfft_plan_set_timing(sfft_plan* pl, int on) {
@@ -337,6 +398,7 @@ int sfft_eval_fft_host(sfft_plan* pl, const uint32_t* h_in, uint32_t* h_out, uin
                        uint32_t* d_out, uint32_t* d_scratch, uint64_t scratch_bytes,
                        void* stream) {
   if (!pl || !h_in || !h_out) return fail(SFFT_EINVAL, "null argument");
+  if (pl->dev.n_patch) return fail(SFFT_EINVAL, "a refresh plan runs through sfft_refresh");
   cudaStream_t st = (cudaStream_t)stream;
   const uint64_t in_b = pl->prog.n_inputs * pl->s.ctw * 4, out_b = pl->prog.n_outputs * pl->s.ctw * 4;
   cudaError_t e = cudaMemcpyAsync(d_in, h_in, in_b, cudaMemcpyHostToDevice, st);
@@ -414,13 +476,25 @@ int sfft_gate_level(const sfft_params* p, const uint32_t* d_a, const uint32_t* d
 int sfft_encrypt_bits_device(const sfft_params* p, const uint32_t* d_pub, const double* h_re,
                              const double* h_im, uint64_t count, uint32_t F, uint32_t f,
                              uint64_t enc_seed, uint32_t* d_ct_out, void* stream) {
-  Shape s;
-  int rc = make_shape(p, &s, true);
-  if (rc) return rc;
-  if (!d_pub || !h_re || !d_ct_out) return fail(SFFT_EINVAL, "null argument");
+  if (!h_re) return fail(SFFT_EINVAL, "null argument");
   if (F < 2 || F > 48 || f >= F) return fail(SFFT_EPARAM, "need 2 <= F <= 48 and f < F");
   std::vector<uint8_t> bits;
   encode_signal(h_re, h_im, count, F, f, &bits);
+  return sfft_encrypt_raw_bits_device(p, d_pub, bits.data(), bits.size(), enc_seed, d_ct_out,
+                                      stream);
+}
+
+int sfft_encrypt_raw_bits_device(const sfft_params* p, const uint32_t* d_pub,
+                                 const uint8_t* h_bits, uint64_t count, uint64_t enc_seed,
+                                 uint32_t* d_ct_out, void* stream) {
+  Shape s;
+  int rc = make_shape(p, &s, true);
+  if (rc) return rc;
+  if (!d_pub || !h_bits || !d_ct_out) return fail(SFFT_EINVAL, "null argument");
+  if (count == 0) return SFFT_OK;
+  std::vector<uint8_t> bits(h_bits, h_bits + count);
+  for (uint8_t& b : bits)
+    if (b > 1) return fail(SFFT_EINVAL, "bits must be 0 or 1");
   const uint64_t n = bits.size();
   std::vector<GateDesc> desc(n);
   std::vector<GateAux> aux(n);

@@ -53,6 +53,15 @@ inline uint16_t pack_code(int c0, int c1, int c2, int c3) {
   return (uint16_t)(((c0 & 15)) | ((c1 & 15) << 4) | ((c2 & 15) << 8) | ((c3 & 15) << 12));
 }
 
+// Code patch of a refresh program: gate `gate` takes a selected operand
+// beta * C (beta a public bit of a refreshed ciphertext), so its coefficients
+// become (c0, c1 bA, c2 bB, c3 bA bB) for both output codes of `code`. bA is
+// bit a_pos % ell of element a_pos / ell of row ell - 1 of source ciphertext
+// a_ct (1 when a_ct == REF_NONE); bB likewise.
+struct PatchDesc {
+  uint32_t gate, code, a_ct, a_pos, b_ct, b_pos, pad0, pad1;
+};
+
 // Output fix-up: materialises an output that is not written by a gate
 // (an alias of another wire, a complemented wire, or a trivial constant).
 //   kind 0: copy src; 1: P - src; 2: zero matrix; 3: P

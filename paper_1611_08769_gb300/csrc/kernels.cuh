@@ -168,6 +168,33 @@ __global__ void k_linear(KArgs a, uint32_t blocks_per_gate) {
   }
 }
 
+// Code patches of a refresh program (PatchDesc), one thread per patch: each
+// selector bit is read from row ell - 1 of its refreshed ciphertext in src.
+__device__ __forceinline__ int src_bit(const uint32_t* src, uint64_t ctw, uint32_t row_word0,
+                                       uint32_t L, uint32_t ell, uint32_t ct, uint32_t pos) {
+  if (ct == REF_NONE) return 1;
+  const uint32_t j = pos / ell, b = pos % ell;
+  return (src[(uint64_t)ct * ctw + row_word0 + j * L + b / 32] >> (b % 32)) & 1;
+}
+
+__global__ void k_patch_codes(const PatchDesc* pd, uint64_t n, GateAux* aux, const uint32_t* src,
+                              uint64_t ctw, uint32_t row_word0, uint32_t L, uint32_t ell) {
+  const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const PatchDesc d = pd[t];
+  const int ba = src_bit(src, ctw, row_word0, L, ell, d.a_ct, d.a_pos);
+  const int bb = src_bit(src, ctw, row_word0, L, ell, d.b_ct, d.b_pos);
+  uint32_t out = 0;
+  for (int h = 0; h < 2; h++) {
+    const uint32_t k = (d.code >> (16 * h)) & 0xFFFFu;
+    const int c0 = nib(k, 0), c1 = nib(k, 1) * ba, c2 = nib(k, 2) * bb, c3 = nib(k, 3) * ba * bb;
+    const uint32_t packed = (uint32_t)(c0 & 15) | ((uint32_t)(c1 & 15) << 4) |
+                            ((uint32_t)(c2 & 15) << 8) | ((uint32_t)(c3 & 15) << 12);
+    out |= packed << (16 * h);
+  }
+  aux[d.gate].code = out;
+}
+
 // Row ell-1 of each ciphertext (what decryption reads).
 __global__ void k_gather_rows(const uint32_t* ct, uint64_t n, uint64_t ctw, uint32_t W,
                               uint32_t row, uint32_t* out) {

@@ -37,6 +37,13 @@ Sig Circuit::NOT(Sig a) {
   return a ^ SIG_ONE;
 }
 
+Sig Circuit::SEL(uint32_t input, uint32_t src_ct, uint32_t src_pos) {
+  const uint32_t node = new_node(0, -1);
+  vin_of[node] = (uint32_t)vin.size();
+  vin.push_back(VInput{input, src_ct, src_pos});
+  return node;
+}
+
 Sig Circuit::AND(Sig a, Sig b) {
   if (a == SIG_ZERO || b == SIG_ZERO) return SIG_ZERO;
   if (a == SIG_ONE) return b;
@@ -441,9 +448,40 @@ bool build_words(Circuit* c, uint32_t op, uint64_t count, uint32_t F, uint32_t f
   return true;
 }
 
+bool build_refresh(Circuit* c, uint32_t n, uint32_t ell, uint64_t count) {
+  const uint64_t rows = (uint64_t)n * ell + 1;
+  uint32_t pb = 0;
+  while ((1ull << pb) < rows) pb++;
+  pb += 3;
+  if (n == 0 || count == 0 || count > (1u << 20) || pb > ell) return false;
+  const uint32_t tau = ell - pb;
+  std::vector<uint32_t> bk(rows);
+  for (uint64_t r = 0; r < rows; r++) bk[r] = c->new_input();
+  for (uint64_t i = 0; i < count; i++) {
+    std::vector<std::vector<Sig>> col(pb);
+    for (uint32_t k = 0; k < pb; k++) {
+      col[k].push_back(c->SEL(0, (uint32_t)i, tau + k));
+      for (uint32_t j = 1; j <= n; j++)
+        for (uint32_t b = 0; b <= tau + k && b < ell; b++)
+          col[k].push_back(c->SEL(1 + (j - 1) * ell + b, (uint32_t)i, j * ell + tau + k - b));
+    }
+    std::vector<Sig> S = c->wallace(std::move(col));
+    Sig s, cy;
+    c->HA(S[pb - 1], S[pb - 2], &s, &cy);
+    c->outputs.push_back(s);
+  }
+  return true;
+}
+
 int build_circuit(Circuit* c, const CircuitSpec& spec, uint32_t flags) {
   if (!c->set_variant(flags))
     return fail(SFFT_EINVAL, "SFFT_PLAN_XCARRY and SFFT_PLAN_NAND are exclusive");
+  if (spec.op == kOpRefresh) {
+    if (!build_refresh(c, spec.n, spec.ell, spec.count))
+      return fail(SFFT_EINVAL, "refresh needs n >= 1, 1 <= count <= 2^20 and ell >= "
+                               "ceil(log2(n ell + 1)) + 3");
+    return SFFT_OK;
+  }
   if (spec.op == 0) {
     if (!build_fft(c, spec.N1, spec.N2, spec.F, spec.f))
       return fail(SFFT_EINVAL,
@@ -547,6 +585,7 @@ uint32_t noise_bits(const Circuit& c, const Shape& s) {
   std::vector<Big> E(c.depth.size());
   Big fresh = Big::of((uint64_t)s.m * s.chi);
   for (uint32_t n : c.inputs) E[n] = fresh;
+  for (const auto& kv : c.vin_of) E[kv.first] = fresh;   // worst case: selected
   uint32_t best = fresh.bits();
   for (size_t p = 0; p < c.products.size(); p++) {
     if (!lp[p]) continue;
@@ -632,6 +671,7 @@ void compile(const Circuit& c, const Shape& s, Program* prog) {
     last[nb] = std::max(last[nb], lev);
   }
   for (size_t i = 0; i < c.inputs.size(); i++) home[c.inputs[i]] = make_ref(REG_IN, (uint32_t)i);
+  for (const auto& kv : c.vin_of) home[kv.first] = make_ref(REG_IN, c.vin[kv.second].input);
 
   // Outputs: a gate-produced, uncomplemented node lives directly in its first
   // output slot; everything else is materialised by a fix-up after the last
@@ -664,6 +704,7 @@ void compile(const Circuit& c, const Shape& s, Program* prog) {
   uint32_t next_slot = 0;
   prog->desc.clear();
   prog->aux.clear();
+  prog->patch.clear();
   prog->level_off.assign(1, 0);
   prog->lin_start.clear();
   prog->max_width = 0;
@@ -707,6 +748,22 @@ void compile(const Circuit& c, const Shape& s, Program* prog) {
         }
         x.code = (uint32_t)k0 | ((uint32_t)k1 << 16);
         x.flags = (negA && !g.is_add) ? 1u : 0u;   // complement A before BitDecomp (products only)
+        auto va = c.vin_of.find(sig_node(g.a)), vb = c.vin_of.find(sig_node(g.b));
+        if (va != c.vin_of.end() || vb != c.vin_of.end()) {
+          PatchDesc pd{};
+          pd.gate = (uint32_t)prog->desc.size();
+          pd.code = x.code;
+          pd.a_ct = pd.b_ct = REF_NONE;
+          if (va != c.vin_of.end()) {
+            pd.a_ct = c.vin[va->second].src_ct;
+            pd.a_pos = c.vin[va->second].src_pos;
+          }
+          if (vb != c.vin_of.end()) {
+            pd.b_ct = c.vin[vb->second].src_ct;
+            pd.b_pos = c.vin[vb->second].src_pos;
+          }
+          prog->patch.push_back(pd);
+        }
         prog->desc.push_back(d);
         prog->aux.push_back(x);
       }

@@ -67,6 +67,13 @@ struct Product {
   bool is_nand;      // GSW NAND gate (NAND-only variant)
 };
 
+// A selected bootstrapping-key wire of a refresh circuit: beta * input, with
+// beta read at run time from a refreshed ciphertext (src_ct, bit src_pos of
+// its row ell - 1, counted over the row's n + 1 elements of ell bits).
+struct VInput {
+  uint32_t input, src_ct, src_pos;
+};
+
 struct Circuit {
   std::vector<uint32_t> depth;     // per node; node 0 = constant zero
   std::vector<int32_t> producer;   // per node: product index or -1 (input/const)
@@ -80,6 +87,8 @@ struct Circuit {
   // Common subexpressions: identical (kind, A, B) gates give identical
   // ciphertexts, so each is computed once (bit-exact).
   std::unordered_map<uint64_t, int32_t> memo_ha, memo_or, memo_add, memo_nand;
+  std::vector<VInput> vin;                          // selected inputs (refresh)
+  std::unordered_map<uint32_t, uint32_t> vin_of;    // node -> index into vin
 
   // Selects the variant from plan flags (SFFT_PLAN_XCARRY, SFFT_PLAN_NAND,
   // SFFT_PLAN_ENC_TWIDDLE); false if both gate variants are set.
@@ -95,6 +104,9 @@ struct Circuit {
   Sig OR(Sig a, Sig b);
   Sig XADD(Sig a, Sig b);
   Sig NAND(Sig a, Sig b);   // one GSW NAND gate on two non-constant signals
+  // beta * inputs[input] with beta a run-time bit of a refreshed ciphertext:
+  // a depth-0 leaf, never folded, never shared.
+  Sig SEL(uint32_t input, uint32_t src_ct, uint32_t src_pos);
   void FA(Sig a, Sig b, Sig c, Sig* s, Sig* co);
   std::vector<Sig> ADD(const std::vector<Sig>& x, const std::vector<Sig>& y, Sig cin);
   std::vector<Sig> SUB(const std::vector<Sig>& x, const std::vector<Sig>& y);
@@ -113,12 +125,25 @@ bool build_fft(Circuit* c, uint32_t N1, uint32_t N2, uint32_t F, uint32_t f);
 // at outputs k F + b. false on invalid sizes.
 bool build_words(Circuit* c, uint32_t op, uint64_t count, uint32_t F, uint32_t f);
 
-// What a plan evaluates: an FFT (op 0) or count word operations (SFFT_WORD_*).
+// Refresh of count ciphertexts by homomorphic decryption of row ell - 1:
+// inputs are the bootstrapping key (encryptions of sigma_0 = 1 and of bit b
+// of s_j = -t_j mod q, j = 1..n, in that order); for each refreshed
+// ciphertext i the p-bit sum S = sum_r K'_r sigma_r (mod 2^p), p =
+// ceil(log2(n ell + 1)) + 3, K'_r = floor(K_r / 2^(ell - p)), K_0 = c_0,
+// K_{j,b} = c_j 2^b mod q: column k gets SEL(sigma_r) selected by bit k of
+// K'_r (bit ell - p + k - b of c_j, left out where that index is negative),
+// Wallace stages and ADD_p; output i = XOR(S_{p-1}, S_{p-2}).
+bool build_refresh(Circuit* c, uint32_t n, uint32_t ell, uint64_t count);
+constexpr uint32_t kOpRefresh = 0x100;
+
+// What a plan evaluates: an FFT (op 0), count word operations (SFFT_WORD_*)
+// or count refreshes (kOpRefresh, at parameters n, ell).
 struct CircuitSpec {
   uint32_t op = 0;
   uint32_t N1 = 1, N2 = 1;
   uint64_t count = 0;
   uint32_t F = 0, f = 0;
+  uint32_t n = 0, ell = 0;
 };
 
 // Selects the variant from flags and builds the circuit; SFFT_OK or the
@@ -137,6 +162,7 @@ struct Program {
   std::vector<uint64_t> level_off;
   std::vector<uint64_t> lin_start;
   std::vector<FixDesc> fix;        // output fix-ups
+  std::vector<PatchDesc> patch;    // gates with selected operands (refresh)
   uint64_t n_inputs = 0, n_outputs = 0, scratch_slots = 0, products = 0;
   uint64_t max_width = 0;
   uint32_t noise_bits = 0;

@@ -17,6 +17,8 @@ using namespace sfft;
 
 namespace {
 
+int nib(uint32_t code, int k) { return (int)((int32_t)(code << (28 - 4 * k)) >> 28); }
+
 int build(const sfft_params* p, const CircuitSpec& spec, uint32_t flags, Shape* s, Circuit* c,
           Program* prog) {
   int rc = make_shape(p, s, false);
@@ -35,6 +37,32 @@ CircuitSpec fft_spec(uint32_t N1, uint32_t N2, uint32_t F, uint32_t f) {
   return sp;
 }
 
+CircuitSpec refresh_spec(const sfft_params* p, uint64_t count) {
+  CircuitSpec sp;
+  sp.op = kOpRefresh;
+  sp.count = count;
+  sp.n = p ? p->n : 0;
+  sp.ell = p ? p->ell : 0;
+  return sp;
+}
+
+// Bit pos (over the row's n + 1 elements of ell bits) of a public row given
+// as (n + 1) L words.
+int row_bit(const uint32_t* row, const Shape& s, uint32_t pos) {
+  const uint32_t j = pos / s.ell, b = pos % s.ell;
+  return (row[j * s.L + b / 32] >> (b % 32)) & 1;
+}
+
+uint32_t patched(uint32_t code, int ba, int bb) {
+  uint32_t out = 0;
+  for (int h = 0; h < 2; h++) {
+    const uint32_t k = (code >> (16 * h)) & 0xFFFFu;
+    const int c0 = nib(k, 0), c1 = nib(k, 1), c2 = nib(k, 2), c3 = nib(k, 3);
+    out |= (uint32_t)pack_code(c0, c1 * ba, c2 * bb, c3 * ba * bb) << (16 * h);
+  }
+  return out;
+}
+
 CircuitSpec word_spec(uint32_t op, uint64_t count, uint32_t F, uint32_t f) {
   CircuitSpec sp;
   sp.op = op;
@@ -44,7 +72,6 @@ CircuitSpec word_spec(uint32_t op, uint64_t count, uint32_t F, uint32_t f) {
   return sp;
 }
 
-int nib(uint32_t code, int k) { return (int)((int32_t)(code << (28 - 4 * k)) >> 28); }
 
 int circuit_info(const sfft_params* p, const CircuitSpec& spec, uint32_t flags,
                  sfft_plan_info* info) {
@@ -91,14 +118,23 @@ int circuit_info(const sfft_params* p, const CircuitSpec& spec, uint32_t flags,
   return SFFT_OK;
 }
 
+// h_rows: row ell - 1 of every refreshed ciphertext ((n + 1) L words each),
+// for the code patches of a refresh program; NULL otherwise.
 int program_eval_plain(const sfft_params* p, const CircuitSpec& spec, uint32_t flags,
-                       const uint8_t* h_in_bits, uint8_t* h_out_bits) {
+                       const uint8_t* h_in_bits, uint8_t* h_out_bits,
+                       const uint32_t* h_rows = nullptr) {
   if (!h_in_bits || !h_out_bits) return fail(SFFT_EINVAL, "null argument");
   Shape s;
   Circuit c;
   Program prog;
   int rc = build(p, spec, flags, &s, &c, &prog);
   if (rc) return rc;
+  if (!prog.patch.empty() && !h_rows) return fail(SFFT_EINVAL, "refresh rows are NULL");
+  for (const PatchDesc& pd : prog.patch) {
+    const int ba = pd.a_ct == REF_NONE ? 1 : row_bit(h_rows + (uint64_t)pd.a_ct * s.W, s, pd.a_pos);
+    const int bb = pd.b_ct == REF_NONE ? 1 : row_bit(h_rows + (uint64_t)pd.b_ct * s.W, s, pd.b_pos);
+    prog.aux[pd.gate].code = patched(pd.code, ba, bb);
+  }
   std::vector<int> reg[3];
   reg[REG_SCRATCH].assign(prog.scratch_slots, -1);
   reg[REG_IN].assign(h_in_bits, h_in_bits + prog.n_inputs);
@@ -166,6 +202,18 @@ int sfft_word_program_eval_plain(const sfft_params* p, uint32_t op, uint64_t cou
                                  uint32_t f, uint32_t flags, const uint8_t* h_in_bits,
                                  uint8_t* h_out_bits) {
   return program_eval_plain(p, word_spec(op, count, F, f), flags, h_in_bits, h_out_bits);
+}
+
+int sfft_refresh_circuit_info(const sfft_params* p, uint64_t count, uint32_t flags,
+                              sfft_plan_info* info) {
+  return circuit_info(p, refresh_spec(p, count), flags, info);
+}
+
+int sfft_refresh_eval_plain(const sfft_params* p, uint64_t count, uint32_t flags,
+                            const uint8_t* h_key_bits, const uint32_t* h_rows,
+                            uint8_t* h_out_bits) {
+  if (!h_rows) return fail(SFFT_EINVAL, "null argument");
+  return program_eval_plain(p, refresh_spec(p, count), flags, h_key_bits, h_out_bits, h_rows);
 }
 
 int sfft_twiddles(uint32_t M, uint32_t f, int64_t* h_wr, int64_t* h_wi) {

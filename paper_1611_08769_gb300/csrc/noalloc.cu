@@ -54,6 +54,7 @@ int scratch_on_current_device(uint32_t** out) {
 extern "C" int sfft_eval_fft_noalloc(sfft_plan* pl, const uint32_t* d_in, uint32_t* d_out,
                                      void* stream) {
   if (!pl) return sfft::fail(SFFT_EINVAL, "plan is NULL");
+  if (pl->dev.n_patch) return sfft::fail(SFFT_EINVAL, "a refresh plan runs through sfft_refresh");
   const uint64_t need = pl->dev.scratch_bytes;
   if (need > kNoAllocScratchBytes)
     return sfft::fail(SFFT_EINVAL, "plan needs " + std::to_string(need) +

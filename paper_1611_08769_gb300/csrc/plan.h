@@ -17,6 +17,8 @@ struct DeviceProgram {
   GateAux* aux = nullptr;
   FixDesc* fix = nullptr;
   uint64_t n_fix = 0;
+  PatchDesc* patch = nullptr;    // refresh programs: code patches applied before each run
+  uint64_t n_patch = 0;
   std::vector<uint64_t> level_off;
   std::vector<uint64_t> lin_start;   // per level: first linear gate (after its products)
   uint64_t scratch_slots = 0;

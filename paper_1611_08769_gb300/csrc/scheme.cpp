@@ -178,6 +178,18 @@ int sfft_keys_public(const sfft_keys* k, uint32_t* h_out, uint64_t cap_words) {
   return SFFT_OK;
 }
 
+int sfft_key_bits(const sfft_keys* K, uint8_t* h_bits, uint64_t cap) {
+  if (!K || !h_bits) return fail(SFFT_EINVAL, "null argument");
+  const Shape& s = K->k.s;
+  const uint64_t rows = (uint64_t)s.n * s.ell + 1;
+  if (cap < rows) return fail(SFFT_EINVAL, "output too small: n ell + 1 bytes needed");
+  h_bits[0] = 1;
+  for (uint32_t j = 1; j <= s.n; j++)
+    for (uint32_t b = 0; b < s.ell; b++)
+      h_bits[1 + (uint64_t)(j - 1) * s.ell + b] = (K->k.sk[j][b / 32] >> (b % 32)) & 1;
+  return SFFT_OK;
+}
+
 int sfft_encrypt_bits(const sfft_keys* K, const double* h_re, const double* h_im, uint64_t count,
                       uint32_t F, uint32_t f, uint64_t enc_seed, uint32_t* h_ct_out) {
   if (!K || !h_re || !h_ct_out) return fail(SFFT_EINVAL, "null argument");

@@ -67,6 +67,14 @@ SIGNATURES = {
     "sfft_word_program_eval_plain": (c_i32, [P(sfft_params), c_u32, c_u64, c_u32, c_u32, c_u32,
                                              c_u8_p, c_u8_p]),
     "sfft_twiddles": (c_i32, [c_u32, c_u32, c_i64_p, c_i64_p]),
+    "sfft_encrypt_raw_bits_device": (c_i32, [P(sfft_params), c_void_p, c_u8_p, c_u64, c_u64,
+                                             c_void_p, c_void_p]),
+    "sfft_key_bits": (c_i32, [c_void_p, c_u8_p, c_u64]),
+    "sfft_refresh_plan_create": (c_i32, [P(sfft_params), c_u64, c_u32, P(c_void_p)]),
+    "sfft_refresh_min_ell": (c_u32, [c_u32, c_u32, c_u32]),
+    "sfft_refresh": (c_i32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_u64, c_void_p]),
+    "sfft_refresh_circuit_info": (c_i32, [P(sfft_params), c_u64, c_u32, P(sfft_plan_info)]),
+    "sfft_refresh_eval_plain": (c_i32, [P(sfft_params), c_u64, c_u32, c_u8_p, c_u32_p, c_u8_p]),
     "sfft_gate_level": (c_i32, [P(sfft_params), c_void_p, c_void_p, c_void_p, c_void_p, c_u16_p,
                                 c_u16_p, c_u8_p, c_u64, c_u32, c_void_p]),
     "sfft_plan_check": (c_i32, [c_void_p, c_void_p]),

@@ -144,3 +144,41 @@ def test_min_ell_is_smallest_with_output_below_q_over_8():
             p = gsw.Params(1, e, 2 * e, 1)
             b = noise.max_bound(refresh.refresh_circuit(p, [None], xcarry=xcarry), p)
             assert (b < p.q // 8) == (e == ell)
+
+
+# ----------------------------------------------------------- native vs oracle
+
+@pytest.mark.parametrize("n,ell,xcarry", [(1, 64, False), (1, 64, True), (2, 64, False),
+                                          (1, 224, False)])
+def test_native_refresh_program_matches_oracle(n, ell, xcarry):
+    import paper_1611_08769_gb300 as sf
+    sp = sf.Params(n, ell, (n + 1) * ell, 1)
+    p = gsw.Params(n, ell, (n + 1) * ell, 1)
+    count = 4
+    rng = random.Random(n * 1000 + ell)
+    keys = sf.keygen(sp, 6)
+    ko = gsw.Keys(p, 6)
+    kb = keys.key_bits()
+    assert list(kb) == refresh.key_bits(ko)
+    rows = [[rng.randrange(p.q) for _ in range(n + 1)] for _ in range(count - 2)]
+    for mu in (0, 1):   # phases on the decision edges
+        rows.append(_row_with_phase(p, ko, (mu * p.q // 2 - p.q // 8) % p.q, rng))
+    c = refresh.refresh_circuit(p, rows, xcarry=xcarry)
+    worst = refresh.refresh_circuit(p, [None] * count, xcarry=xcarry)
+    info = sf.refresh_circuit_info(sp, count, xcarry=xcarry)
+    st = circuit.stats(c)
+    assert info["inputs"] == n * ell + 1 and info["outputs"] == count
+    assert info["products"] == st["products"] == circuit.stats(worst)["products"]
+    assert info["levels"] == st["depth"]
+    assert info["noise_bits"] == noise.max_bound(worst, p).bit_length()
+    h_rows = np.array([gsw.to_limbs(np.array(r, dtype=object), p.L).reshape(-1) for r in rows],
+                      dtype=np.uint32)
+    got = sf.refresh_eval_plain(sp, kb, h_rows, xcarry=xcarry)
+    assert list(got) == evaluate.eval_plain(c, list(kb))
+    assert list(got) == [refresh.refreshed_bit(p, r, [int(v) for v in kb]) for r in rows]
+
+
+def test_native_refresh_min_ell_matches_oracle():
+    import paper_1611_08769_gb300 as sf
+    for xcarry in (False, True):
+        assert sf.refresh_min_ell(1, 1, xcarry=xcarry) == refresh.min_ell(1, 1, xcarry=xcarry)

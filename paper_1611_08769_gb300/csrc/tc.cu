@@ -317,7 +317,9 @@ struct TcShape {
 // a.bx_shared). Output slice (j, kb) lives at a.bx + (j kblocks + kb) btile.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kExpandThreads) k_expand_b(KArgs a, TcShape t) {
-  extern __shared__ uint32_t raw[];   // kBK rows x W words
+  // raw: the step's kBK source rows (W words each); then one 32-row x 128-byte
+  // staging block per warp
+  extern __shared__ __align__(16) uint32_t raw[];
   const uint32_t W = a.W, L = a.L;
   const uint64_t job = blockIdx.x / t.kblocks;
   const uint32_t kb = blockIdx.x % t.kblocks;
@@ -325,38 +327,62 @@ __global__ void __launch_bounds__(kExpandThreads) k_expand_b(KArgs a, TcShape t)
   const uint32_t* B = ct_ptr(a, a.desc[job].b);
   const uint32_t k0 = kb * kBK;
   const uint32_t krows = (a.Ng - k0) < (uint32_t)kBK ? (a.Ng - k0) : (uint32_t)kBK;
-  const uint32_t* src = B + (uint64_t)k0 * W;
-  for (uint32_t e = threadIdx.x; e < (uint32_t)kBK * W; e += kExpandThreads)
-    raw[e] = e < krows * W ? __ldg(src + e) : 0u;
+  // rows are contiguous in the ciphertext and krows W is a multiple of 4
+  // (Ng and so krows are multiples of 64): 16-byte loads
+  const uint4* src = reinterpret_cast<const uint4*>(B + (uint64_t)k0 * W);
+  uint4* raw4 = reinterpret_cast<uint4*>(raw);
+  const uint32_t nvec = krows * W / 4u;
+  for (uint32_t i = threadIdx.x; i < nvec; i += kExpandThreads) raw4[i] = __ldg(src + i);
+  for (uint32_t i = krows * W + threadIdx.x; i < (uint32_t)kBK * W; i += kExpandThreads) raw[i] = 0u;
   __syncthreads();
-  uint4* dst = (uint4*)(a.bx + (job * t.kblocks + kb) * (uint64_t)t.btile);
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  uint32_t* stage = raw + kBK * W + warp * 1024u;
+  uint4* stage4 = reinterpret_cast<uint4*>(stage);
+  uint4* dst = reinterpret_cast<uint4*>(a.bx + (job * t.kblocks + kb) * (uint64_t)t.btile);
   const uint32_t mask = (1u << t.dw) - 1u;
   // The step's image is two atoms (K values 0..63, 64..127 of the step), each
-  // ndpad rows of 128 bytes. 16-byte unit uu of an atom: row n = uu / 8,
-  // stored position p = uu % 8 holds K chunk c = p ^ (n & 7); row n is digit
-  // d = n % dpad of element e = n / dpad: bits dw d .. dw d + dw - 1 of the
-  // element (zero past ell).
-  for (uint32_t u = threadIdx.x; u < 2u * t.ndpad * 8u; u += kExpandThreads) {
-    const uint32_t atom = u >= t.ndpad * 8u ? 1u : 0u, uu = u - atom * t.ndpad * 8u;
-    const uint32_t n = uu >> 3, c = (uu & 7u) ^ (n & 7u);
-    const uint32_t e = n / t.dpad, d = n - e * t.dpad;
-    uint4 v = make_uint4(0, 0, 0, 0);
-    if (d < t.D) {
-      const uint32_t bit = d * t.dw, wl = bit >> 5, sh = bit & 31u;
-      const bool hi = wl + 1 < L;   // the digit may continue in the element's next limb
-      const uint32_t* rp = raw + (atom * 64u + c * 8u) * W + e * L + wl;
+  // ndpad rows of 128 bytes, atom 1 right after atom 0: image row g = atom
+  // ndpad + n. Row n is digit d = n % dpad of element e = n / dpad (bits dw d
+  // .. dw d + dw - 1, zero past ell); its 16-byte position p holds K chunk
+  // c = p ^ (n & 7). A warp makes 32 consecutive image rows, lane = row: for
+  // each chunk all lanes read the same source row (no bank conflicts), and
+  // each lane stores its chunk at position c ^ (n & 7) of its staging row
+  // (the eight lanes of a quarter warp hit eight distinct positions); the
+  // block then leaves as 512 contiguous bytes per warp instruction.
+  for (uint32_t base = warp * 32u; base < 2u * t.ndpad; base += (kExpandThreads / 32) * 32u) {
+    const uint32_t g = base + lane;
+    const bool in_img = g < 2u * t.ndpad;
+    const uint32_t atom = g >= t.ndpad ? 1u : 0u;
+    const uint32_t n = g - atom * t.ndpad;
+    uint32_t e = 0;
+    while ((e + 1) * t.dpad <= n) e++;
+    const uint32_t d = n - e * t.dpad;
+    const bool valid = in_img && d < t.D;
+    const uint32_t bit = d * t.dw, wl = valid ? bit >> 5 : 0u, sh = bit & 31u;
+    const bool hi = wl + 1 < L;   // the digit may continue in the element's next limb
+    const uint32_t* rp = raw + atom * 64u * W + (valid ? e * L + wl : 0u);
+#pragma unroll 2
+    for (uint32_t c = 0; c < 8; c++) {
       uint32_t h[8];
 #pragma unroll
       for (int q = 0; q < 8; q++) {
-        const uint32_t dig = __funnelshift_r(rp[q * W], hi ? rp[q * W + 1] : 0u, sh) & mask;
+        const uint32_t* r = rp + (c * 8u + q) * W;
+        const uint32_t dig = __funnelshift_r(r[0], hi ? r[1] : 0u, sh) & mask;
         h[q] = __half_as_ushort(__uint2half_rn(dig));
       }
-      v.x = h[0] | (h[1] << 16);
-      v.y = h[2] | (h[3] << 16);
-      v.z = h[4] | (h[5] << 16);
-      v.w = h[6] | (h[7] << 16);
+      uint4 v = make_uint4(0, 0, 0, 0);
+      if (valid) {
+        v.x = h[0] | (h[1] << 16);
+        v.y = h[2] | (h[3] << 16);
+        v.z = h[4] | (h[5] << 16);
+        v.w = h[6] | (h[7] << 16);
+      }
+      stage4[lane * 8u + (c ^ (n & 7u))] = v;
     }
-    dst[u] = v;
+    __syncwarp();
+    const uint32_t rows = (2u * t.ndpad - base) < 32u ? (2u * t.ndpad - base) : 32u;
+    for (uint32_t i = lane; i < rows * 8u; i += 32u) dst[base * 8u + i] = stage4[i];
+    __syncwarp();
   }
 }
 
@@ -890,6 +916,11 @@ uint64_t tc_bx_bytes(const KArgs& a, uint64_t gates) {
   return (gates < c ? gates : c) * tc_bx_bytes_per_gate(a);
 }
 
+// k_expand_b: the step's source rows, then a 4 KB staging block per warp.
+uint32_t expand_smem_bytes(const KArgs& a) {
+  return kBK * a.W * 4u + (kExpandThreads / 32) * 4096u;
+}
+
 int launch_gates_tc(const KArgs& a, cudaStream_t st) {
   if (a.n == 0) return SFFT_OK;
   TcShape t{};
@@ -912,7 +943,7 @@ int launch_gates_tc(const KArgs& a, cudaStream_t st) {
     ca.n = (a.n - c0) < chunk ? (a.n - c0) : chunk;
     KArgs ea = ca;
     ea.n = a.bx_shared ? 1 : ca.n;
-    k_expand_b<<<(unsigned)(ea.n * t.kblocks), kExpandThreads, kBK * a.W * 4u, st>>>(ea, t);
+    k_expand_b<<<(unsigned)(ea.n * t.kblocks), kExpandThreads, expand_smem_bytes(a), st>>>(ea, t);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "B expansion launch");
     // persistent: one CTA per SM (or per item, if fewer)

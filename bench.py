@@ -142,6 +142,23 @@ class ClockSampler:
                 "samples": len(self.samples)}
 
 
+def max_over_ranks(x, world, device):
+    """The largest of every rank's x (the slowest replica times the job)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank, ms, world):
+    """Whole-job units per second: every rank runs its own replica of the
+    workload in ms (the maximum over ranks)."""
+    return world * units_per_rank * 1000.0 / ms
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -709,11 +726,8 @@ def main():
         with ClockSampler(local) as clk:
             ms = timed(run_b, args.steps)
         batch.check(stream)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    fft_per_s = world * len(items) * 1000.0 / ms
+    ms = max_over_ranks(ms, world, "cuda")
+    fft_per_s = replica_throughput(len(items), ms, world)
 
     # kernel timing (per-launch events; graph replay is bypassed while timing)
     batch.set_timing(True)
@@ -754,10 +768,7 @@ def main():
             batch.eval_host(h_in, h_out, d_in, d_out, scratch, stream)
         e2e_ms = (time.perf_counter() - t0) * 1000.0 / args.steps
         barrier()
-    if world > 1:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e2e_ms, world, "cuda")
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

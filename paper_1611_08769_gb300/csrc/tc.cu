@@ -37,6 +37,8 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <map>
+#include <mutex>
 
 #include "common.h"
 #include "kargs.h"
@@ -49,7 +51,8 @@ namespace {
 
 constexpr int kThreads = 512;
 constexpr int kTileM = 128;
-constexpr int kBK = 128;                       // K elements per step: two 64-wide swizzle atoms
+constexpr int kBK = 128;                       // K elements per step: 64-wide swizzle atoms
+constexpr uint32_t kAtoms = kBK / 64;          // atoms per step
 constexpr uint32_t kSpinLimit = 1u << 26;
 constexpr uint64_t kWaitNs = 2000000000ull;    // bound of any single mbarrier wait
 constexpr uint32_t kMaxSmem = 232448;          // 227 KB opt-in per CTA
@@ -127,6 +130,17 @@ __device__ __forceinline__ void cp_async4(uint32_t* dst, const uint32_t* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
 
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+// Waits until at most one committed group (the most recent) is in flight.
+__device__ __forceinline__ void cp_async_wait_prev() {
+  asm volatile("cp.async.wait_group 1;" ::: "memory");
+}
+
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
 }
@@ -195,6 +209,27 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
   " @e tcgen05.mma.cta_group::1.kind::f16 [%1], [a5], y5, %7, t;\n"                             \
   " @e tcgen05.mma.cta_group::1.kind::f16 [%1], [a6], y6, %7, t;\n"                             \
   " @e tcgen05.mma.cta_group::1.kind::f16 [%1], [a7], y7, %7, t;\n"
+// The same for a 64-wide K step (one atom, four K=16 steps).
+#define SFFT_MMA_PROLOGUE1                                                                       \
+  "{\n .reg .pred e, e3, p, t;\n .reg .b32 a1, a2, a3;\n"                                        \
+  " .reg .b64 o1, x0, x1, x2, x3, y0, y1, y2, y3;\n"                                            \
+  " elect.sync _|e, 0xffffffff;\n"                                                               \
+  " setp.ne.b32 p, %8, 0;\n"                                                                     \
+  " setp.eq.b32 t, %8, %8;\n"                                                                    \
+  " setp.ne.and.b32 e3, %11, 0, e;\n"                                                            \
+  " add.u32 a1, %2, 8;\n add.u32 a2, %2, 16;\n add.u32 a3, %2, 24;\n"                            \
+  " cvt.u64.u32 o1, %5;\n"                                                                       \
+  " mov.b64 x0, %3;\n add.u64 x1, x0, 2;\n add.u64 x2, x0, 4;\n add.u64 x3, x0, 6;\n"          \
+  " @e tcgen05.mma.cta_group::1.kind::f16 [%0], [%2], x0, %6, p;\n"                             \
+  " @e tcgen05.mma.cta_group::1.kind::f16 [%0], [a1], x1, %6, t;\n"                             \
+  " @e tcgen05.mma.cta_group::1.kind::f16 [%0], [a2], x2, %6, t;\n"                             \
+  " @e tcgen05.mma.cta_group::1.kind::f16 [%0], [a3], x3, %6, t;\n"
+#define SFFT_MMA_SECOND1                                                                         \
+  " add.u64 y0, x0, o1;\n add.u64 y1, x1, o1;\n add.u64 y2, x2, o1;\n add.u64 y3, x3, o1;\n"    \
+  " @e tcgen05.mma.cta_group::1.kind::f16 [%1], [%2], y0, %7, p;\n"                             \
+  " @e tcgen05.mma.cta_group::1.kind::f16 [%1], [a1], y1, %7, t;\n"                             \
+  " @e tcgen05.mma.cta_group::1.kind::f16 [%1], [a2], y2, %7, t;\n"                             \
+  " @e tcgen05.mma.cta_group::1.kind::f16 [%1], [a3], y3, %7, t;\n"
 #define SFFT_MMA_COMMITS                                                                         \
   " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%9];\n"           \
   " @e3 tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%10];\n}\n"
@@ -203,6 +238,19 @@ template <bool TWO>
 __device__ __forceinline__ void mma_step(uint32_t d0, uint32_t d1, uint32_t at, uint64_t b0, uint32_t aoff,
                                          uint32_t boff1, uint32_t id0, uint32_t id1, uint32_t acc,
                                          uint64_t* fb, uint64_t* fd, uint32_t last) {
+  if (kAtoms == 1) {
+    if (TWO)
+      asm volatile(SFFT_MMA_PROLOGUE1 SFFT_MMA_SECOND1 SFFT_MMA_COMMITS ::"r"(d0), "r"(d1), "r"(at),
+                   "l"(b0), "r"(aoff), "r"(boff1), "r"(id0), "r"(id1), "r"(acc), "r"(smem_u32(fb)),
+                   "r"(smem_u32(fd)), "r"(last)
+                   : "memory");
+    else
+      asm volatile(SFFT_MMA_PROLOGUE1 SFFT_MMA_COMMITS ::"r"(d0), "r"(d1), "r"(at), "l"(b0), "r"(aoff),
+                   "r"(boff1), "r"(id0), "r"(id1), "r"(acc), "r"(smem_u32(fb)), "r"(smem_u32(fd)),
+                   "r"(last)
+                   : "memory");
+    return;
+  }
   if (TWO)
     asm volatile(SFFT_MMA_PROLOGUE SFFT_MMA_SECOND SFFT_MMA_COMMITS ::"r"(d0), "r"(d1), "r"(at), "l"(b0),
                  "r"(aoff), "r"(boff1), "r"(id0), "r"(id1), "r"(acc), "r"(smem_u32(fb)), "r"(smem_u32(fd)),
@@ -215,6 +263,8 @@ __device__ __forceinline__ void mma_step(uint32_t d0, uint32_t d1, uint32_t at, 
 }
 #undef SFFT_MMA_PROLOGUE
 #undef SFFT_MMA_SECOND
+#undef SFFT_MMA_PROLOGUE1
+#undef SFFT_MMA_SECOND1
 #undef SFFT_MMA_COMMITS
 
 // Commit -> bar from the elected lane of the calling warp (the lane that
@@ -316,74 +366,95 @@ struct TcShape {
 // Job j expands the B operand of gate j (job 0 for every gate when
 // a.bx_shared). Output slice (j, kb) lives at a.bx + (j kblocks + kb) btile.
 // ---------------------------------------------------------------------------
+// Persistent: CTA b takes the jobs (gate, K step) b, b + grid, ...; the next
+// job's source rows stream into the second buffer (16-byte async copies)
+// while the current one is expanded, so that every SM keeps loads in flight.
 __global__ void __launch_bounds__(kExpandThreads) k_expand_b(KArgs a, TcShape t) {
-  // raw: the step's kBK source rows (W words each); then one 32-row x 128-byte
-  // staging block per warp
+  // two buffers of a step's kBK source rows (W words each); then one 32-row x
+  // 128-byte staging block per warp
   extern __shared__ __align__(16) uint32_t raw[];
   const uint32_t W = a.W, L = a.L;
-  const uint64_t job = blockIdx.x / t.kblocks;
-  const uint32_t kb = blockIdx.x % t.kblocks;
-  if (job >= a.n) return;
-  const uint32_t* B = ct_ptr(a, a.desc[job].b);
-  const uint32_t k0 = kb * kBK;
-  const uint32_t krows = (a.Ng - k0) < (uint32_t)kBK ? (a.Ng - k0) : (uint32_t)kBK;
-  // rows are contiguous in the ciphertext and krows W is a multiple of 4
-  // (Ng and so krows are multiples of 64): 16-byte loads
-  const uint4* src = reinterpret_cast<const uint4*>(B + (uint64_t)k0 * W);
-  uint4* raw4 = reinterpret_cast<uint4*>(raw);
-  const uint32_t nvec = krows * W / 4u;
-  for (uint32_t i = threadIdx.x; i < nvec; i += kExpandThreads) raw4[i] = __ldg(src + i);
-  for (uint32_t i = krows * W + threadIdx.x; i < (uint32_t)kBK * W; i += kExpandThreads) raw[i] = 0u;
-  __syncthreads();
-  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-  uint32_t* stage = raw + kBK * W + warp * 1024u;
+  const uint64_t jobs = a.n * t.kblocks;
+  const uint32_t buf_words = kBK * W;
+  uint32_t* stage = raw + 2u * buf_words + (threadIdx.x >> 5) * 1024u;
   uint4* stage4 = reinterpret_cast<uint4*>(stage);
-  uint4* dst = reinterpret_cast<uint4*>(a.bx + (job * t.kblocks + kb) * (uint64_t)t.btile);
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   const uint32_t mask = (1u << t.dw) - 1u;
-  // The step's image is two atoms (K values 0..63, 64..127 of the step), each
-  // ndpad rows of 128 bytes, atom 1 right after atom 0: image row g = atom
-  // ndpad + n. Row n is digit d = n % dpad of element e = n / dpad (bits dw d
-  // .. dw d + dw - 1, zero past ell); its 16-byte position p holds K chunk
-  // c = p ^ (n & 7). A warp makes 32 consecutive image rows, lane = row: for
-  // each chunk all lanes read the same source row (no bank conflicts), and
-  // each lane stores its chunk at position c ^ (n & 7) of its staging row
-  // (the eight lanes of a quarter warp hit eight distinct positions); the
-  // block then leaves as 512 contiguous bytes per warp instruction.
-  for (uint32_t base = warp * 32u; base < 2u * t.ndpad; base += (kExpandThreads / 32) * 32u) {
-    const uint32_t g = base + lane;
-    const bool in_img = g < 2u * t.ndpad;
-    const uint32_t atom = g >= t.ndpad ? 1u : 0u;
-    const uint32_t n = g - atom * t.ndpad;
-    uint32_t e = 0;
-    while ((e + 1) * t.dpad <= n) e++;
-    const uint32_t d = n - e * t.dpad;
-    const bool valid = in_img && d < t.D;
-    const uint32_t bit = d * t.dw, wl = valid ? bit >> 5 : 0u, sh = bit & 31u;
-    const bool hi = wl + 1 < L;   // the digit may continue in the element's next limb
-    const uint32_t* rp = raw + atom * 64u * W + (valid ? e * L + wl : 0u);
+  // rows are contiguous in the ciphertext and krows W is a multiple of 4
+  // (Ng and so krows are multiples of 64): 16-byte copies
+  auto rows_of = [&](uint64_t job) {
+    const uint32_t k0 = (uint32_t)(job % t.kblocks) * kBK;
+    return (a.Ng - k0) < (uint32_t)kBK ? (a.Ng - k0) : (uint32_t)kBK;
+  };
+  auto prefetch = [&](uint64_t job, uint32_t* buf) {
+    const uint32_t k0 = (uint32_t)(job % t.kblocks) * kBK;
+    const uint4* src = reinterpret_cast<const uint4*>(ct_ptr(a, a.desc[job / t.kblocks].b) +
+                                                      (uint64_t)k0 * W);
+    uint4* dst4 = reinterpret_cast<uint4*>(buf);
+    const uint32_t nvec = rows_of(job) * W / 4u;
+    for (uint32_t i = threadIdx.x; i < nvec; i += kExpandThreads) cp_async16(dst4 + i, src + i);
+  };
+  uint32_t it = 0;
+  if (blockIdx.x < jobs) prefetch(blockIdx.x, raw);
+  cp_async_commit();
+  for (uint64_t job = blockIdx.x; job < jobs; job += gridDim.x, it++) {
+    uint32_t* cur = raw + (it & 1u) * buf_words;
+    const uint64_t nxt = job + gridDim.x;
+    if (nxt < jobs) prefetch(nxt, raw + ((it + 1) & 1u) * buf_words);
+    cp_async_commit();
+    cp_async_wait_prev();   // this job's rows have landed (this thread's copies)
+    const uint32_t krows = rows_of(job);
+    for (uint32_t i = krows * W + threadIdx.x; i < buf_words; i += kExpandThreads) cur[i] = 0u;
+    __syncthreads();        // every thread's copies and zero rows are visible
+    uint4* dst = reinterpret_cast<uint4*>(a.bx + job * (uint64_t)t.btile);
+    // The step's image is kAtoms atoms (K values 0..63, 64..127 of the step),
+    // each ndpad rows of 128 bytes, one after the other: image row g = atom
+    // ndpad + n. Row n is digit d = n % dpad of element e = n / dpad (bits
+    // dw d .. dw d + dw - 1, zero past ell); its 16-byte position p holds K
+    // chunk c = p ^ (n & 7). A warp makes 32 consecutive image rows, lane =
+    // row: for each chunk all lanes read the same source row (no bank
+    // conflicts), and each lane stores its chunk at position c ^ (n & 7) of
+    // its staging row (the eight lanes of a quarter warp hit eight distinct
+    // positions); the block then leaves as 512 contiguous bytes per warp
+    // instruction.
+    for (uint32_t base = warp * 32u; base < kAtoms * t.ndpad; base += (kExpandThreads / 32) * 32u) {
+      const uint32_t g = base + lane;
+      const bool in_img = g < kAtoms * t.ndpad;
+      const uint32_t atom = g >= t.ndpad ? 1u : 0u;
+      const uint32_t n = g - atom * t.ndpad;
+      uint32_t e = 0;
+      while ((e + 1) * t.dpad <= n) e++;
+      const uint32_t d = n - e * t.dpad;
+      const bool valid = in_img && d < t.D;
+      const uint32_t bit = d * t.dw, wl = valid ? bit >> 5 : 0u, sh = bit & 31u;
+      const bool hi = wl + 1 < L;   // the digit may continue in the element's next limb
+      const uint32_t* rp = cur + atom * 64u * W + (valid ? e * L + wl : 0u);
 #pragma unroll 2
-    for (uint32_t c = 0; c < 8; c++) {
-      uint32_t h[8];
+      for (uint32_t c = 0; c < 8; c++) {
+        uint32_t h[8];
 #pragma unroll
-      for (int q = 0; q < 8; q++) {
-        const uint32_t* r = rp + (c * 8u + q) * W;
-        const uint32_t dig = __funnelshift_r(r[0], hi ? r[1] : 0u, sh) & mask;
-        h[q] = __half_as_ushort(__uint2half_rn(dig));
+        for (int q = 0; q < 8; q++) {
+          const uint32_t* r = rp + (c * 8u + q) * W;
+          const uint32_t dig = __funnelshift_r(r[0], hi ? r[1] : 0u, sh) & mask;
+          h[q] = __half_as_ushort(__uint2half_rn(dig));
+        }
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (valid) {
+          v.x = h[0] | (h[1] << 16);
+          v.y = h[2] | (h[3] << 16);
+          v.z = h[4] | (h[5] << 16);
+          v.w = h[6] | (h[7] << 16);
+        }
+        stage4[lane * 8u + (c ^ (n & 7u))] = v;
       }
-      uint4 v = make_uint4(0, 0, 0, 0);
-      if (valid) {
-        v.x = h[0] | (h[1] << 16);
-        v.y = h[2] | (h[3] << 16);
-        v.z = h[4] | (h[5] << 16);
-        v.w = h[6] | (h[7] << 16);
-      }
-      stage4[lane * 8u + (c ^ (n & 7u))] = v;
+      __syncwarp();
+      const uint32_t rows = (kAtoms * t.ndpad - base) < 32u ? (kAtoms * t.ndpad - base) : 32u;
+      for (uint32_t i = lane; i < rows * 8u; i += 32u) dst[base * 8u + i] = stage4[i];
+      __syncwarp();
     }
-    __syncwarp();
-    const uint32_t rows = (2u * t.ndpad - base) < 32u ? (2u * t.ndpad - base) : 32u;
-    for (uint32_t i = lane; i < rows * 8u; i += 32u) dst[base * 8u + i] = stage4[i];
-    __syncwarp();
+    __syncthreads();        // the buffer is refilled two jobs later
   }
+  cp_async_wait_all();
 }
 
 // ---------------------------------------------------------------------------
@@ -425,7 +496,7 @@ __global__ void __launch_bounds__(kExpandThreads) k_expand_b(KArgs a, TcShape t)
 //   warps 8..15  epilogue of item j while item j+1 is multiplied
 //   warps 2, 3   idle
 // ---------------------------------------------------------------------------
-constexpr uint32_t kAStages = 2;
+constexpr uint32_t kAStages = kAtoms == 1 ? 4 : 2;   // 128 tensor-memory columns either way
 constexpr uint32_t kAStageCols = kBK / 2;        // 128 fp16 K values per lane
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kAColumns = kAStageCols * kAStages;   // tensor-memory columns of the A stages
@@ -671,8 +742,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gate_tc(KArgs a, TcShape t) {
       // past it) -> 128 fp16 values, K value k in half k % 2 of column k / 2
       const uint32_t scol = arow + kAStageCols * (st & (kAStages - 1));
 #pragma unroll
-      for (uint32_t hpart = 0; hpart < 2; hpart++) {
-        const uint32_t wi = 4u * kb + 2u * hpart;
+      for (uint32_t hpart = 0; hpart < kAtoms; hpart++) {
+        const uint32_t wi = (kBK / 32u) * kb + 2u * hpart;
         const uint32_t w0 = wi < W ? row[wi] : 0u;
         const uint32_t w1 = wi + 1u < W ? row[wi + 1u] : 0u;
         uint32_t v[32];
@@ -854,7 +925,7 @@ bool make_tc_shape(const KArgs& a, TcShape* t) {
   t->n1_len = t->ndpad - t->n0_len;
   t->mtiles = (a.Ng + kTileM - 1) / kTileM;
   t->kblocks = (a.Ng + kBK - 1) / kBK;
-  t->btile = t->ndpad * 256u;
+  t->btile = t->ndpad * 128u * kAtoms;
   t->G = (t->dpad + kGroupDigits - 1) / kGroupDigits;
   t->nstages = 0;
   for (uint32_t ns = 8; ns >= kAStages; ns--)
@@ -916,9 +987,34 @@ uint64_t tc_bx_bytes(const KArgs& a, uint64_t gates) {
   return (gates < c ? gates : c) * tc_bx_bytes_per_gate(a);
 }
 
-// k_expand_b: the step's source rows, then a 4 KB staging block per warp.
+// k_expand_b: two buffers of a step's source rows, then a 4 KB staging block
+// per warp.
 uint32_t expand_smem_bytes(const KArgs& a) {
-  return kBK * a.W * 4u + (kExpandThreads / 32) * 4096u;
+  return 2u * kBK * a.W * 4u + (kExpandThreads / 32) * 4096u;
+}
+
+// Persistent expansion grid: as many CTAs as fit on the SMs (two per SM at
+// the usual sizes), never more than the jobs.
+uint32_t expand_grid(const KArgs& a, uint64_t jobs) {
+  static std::mutex mu;
+  static std::map<uint32_t, int> per_sm;   // by dynamic shared-memory size
+  const uint32_t smem = expand_smem_bytes(a);
+  int n = 0;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = per_sm.find(smem);
+    if (it == per_sm.end()) {
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_expand_b, kExpandThreads, smem) !=
+              cudaSuccess ||
+          n < 1)
+        n = 1;
+      per_sm[smem] = n;
+    } else {
+      n = it->second;
+    }
+  }
+  const uint64_t g = (uint64_t)n * (uint64_t)sm_count();
+  return (uint32_t)(jobs < g ? jobs : g);
 }
 
 int launch_gates_tc(const KArgs& a, cudaStream_t st) {
@@ -943,7 +1039,7 @@ int launch_gates_tc(const KArgs& a, cudaStream_t st) {
     ca.n = (a.n - c0) < chunk ? (a.n - c0) : chunk;
     KArgs ea = ca;
     ea.n = a.bx_shared ? 1 : ca.n;
-    k_expand_b<<<(unsigned)(ea.n * t.kblocks), kExpandThreads, expand_smem_bytes(a), st>>>(ea, t);
+    k_expand_b<<<expand_grid(a, ea.n * t.kblocks), kExpandThreads, expand_smem_bytes(a), st>>>(ea, t);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "B expansion launch");
     // persistent: one CTA per SM (or per item, if fewer)

@@ -2,33 +2,33 @@
 //
 // The GSW product K = BitDecomp(A~) B' (Sec. 7: an N x N matrix product per
 // gate) is a dense contraction of a {0,1} matrix with the entries of B'.
-// Every ell-bit entry of B' is cut into D = ceil(ell / dw) digits of dw bits
-// (dw = 11, or fewer if Ng (2^dw - 1) would reach 2^24), so that per output
-// row i and digit column (element e, digit d)
-//     S[i][e,d] = sum_k bit_k(A~_i) * digit_d(B'_k[e])  <=  Ng (2^dw - 1)  <  2^24.
-// Digits up to 2047 are exact fp16 values and every partial sum is an
-// integer below 2^24, so an fp16 x fp16 -> fp32 MMA computes S exactly. The
-// epilogue forms K[i][e] = sum_d S[i][e,d] 2^(dw d) (mod 2^ell) word by word
-// and adds the linear terms c0 P + c1 A + c2 B with the limb carries of the
-// element, exactly as the integer kernel does.
+// Every ell-bit entry of B' is cut into D = ceil(ell / 11) digits of 11 bits,
+// so that per output row i and digit column (element e, digit d)
+//     S[i][e,d] = sum_k bit_k(A~_i) * digit_d(B'_k[e])  <=  Ng (2^11 - 1)  <  2^23
+// (the kernel applies when Ng <= 4097). Digits up to 2047 are exact fp16
+// values and every partial sum is an integer below 2^23, so an fp16 x fp16 ->
+// fp32 MMA computes S exactly, and the epilogue reads it back by adding 2^23
+// (the sum's significand is then S). The epilogue forms K[i][e] = sum_d
+// S[i][e,d] 2^(11 d) (mod 2^ell) word by word and adds the linear terms
+// c0 P + c1 A + c2 B with the limb carries of the element, exactly as the
+// integer kernel does.
 //
 // Two kernels per level:
-//  * k_expand_b writes, once per gate, the B operand in its tensor-core form:
-//    for every 64-row slice of B' the exact shared-memory image of the
-//    128B-swizzled K-major fp16 tile (digit columns x 64 K values);
-//  * k_gate_tc, one CTA (16 warps) per group of J work items (an item is a
-//    128-row tile of one gate's output; J > 1 for small ciphertexts so the
-//    CTA's fixed costs are shared): the A~ tiles arrive by bulk copies
-//    (cp.async.bulk + mbarrier transaction count) and are complemented in
-//    place when the descriptor asks for P - A; the B slices stream through a
-//    shared-memory ring by 1-D bulk copies (already swizzled); per (item,
-//    slice) step 14 warps expand the A bits into a swizzled fp16 tile and one
-//    warp issues the step's tcgen05.mma instructions (one elected lane, the
-//    MMAs and their commits in one instruction group) into the item's TMEM
-//    accumulator; the commits free the A buffer and the ring slot. The
-//    epilogue (overlapped with the next item's MMAs) reads the accumulator
-//    with tcgen05.ld, forms the words of each 32-digit group and runs both
-//    output carry chains with the linear terms.
+//  * k_expand_b (persistent) writes, once per gate, the B operand in its
+//    tensor-core form: for every K step of kBK rows of B' the exact
+//    shared-memory image of the 128B-swizzled K-major fp16 atoms (digit rows x
+//    64 K values each);
+//  * k_gate_tc (persistent, one CTA of 16 warps per SM): work items are
+//    128-row output tiles. A producer warp streams the A~ rows of an item
+//    (double-buffered) and the B steps (a shared-memory ring) by bulk copies
+//    with mbarrier transaction counts; four expander warps turn each step's
+//    A~ bits into fp16 values in tensor memory (tcgen05.st), complementing a
+//    row first when the descriptor asks for P - A; one warp issues the step's
+//    tcgen05.mma instructions (one elected lane; the MMAs and their commit in
+//    one instruction group) into the item's TMEM accumulator; eight epilogue
+//    warps, overlapped with the next item's MMAs, read the accumulator with
+//    tcgen05.ld, form the words of each 32-digit group and run both output
+//    carry chains with the linear terms.
 // Every mbarrier wait is bounded (~2 s); on timeout the kernel records
 // KERR_MMA_TIMEOUT, waits (bounded) for its own MMAs, frees its TMEM and
 // returns.
@@ -128,6 +128,12 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 // 4-byte asynchronous copy global -> shared (completion by commit/wait group).
 __device__ __forceinline__ void cp_async4(uint32_t* dst, const uint32_t* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
+// An fp32 value holding an integer S in [0, 2^23) -> S: S + 2^23 is exact
+// and its significand field is S.
+__device__ __forceinline__ uint32_t small_float_to_uint(float x) {
+  return __float_as_uint(__fadd_rn(x, 8388608.0f)) - 0x4B000000u;
 }
 
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
@@ -828,12 +834,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_gate_tc(KArgs a, TcShape t) {
 #pragma unroll
             for (int k = 16; k < 32; k++) v[k] = 0;
           }
+          // digit k adds S 2^(11k mod 32) to word (11k) / 32
           int64_t kw[kGroupWords];
 #pragma unroll
           for (int k = 0; k < (int)kGroupWords; k++) kw[k] = 0;
 #pragma unroll
           for (int k = 0; k < (int)kGroupDigits; k++)
-            kw[(k * (int)kDigitBits) >> 5] += (int64_t)__float2int_rn(__uint_as_float(v[k]))
+            kw[(k * (int)kDigitBits) >> 5] += (int64_t)(int32_t)small_float_to_uint(__uint_as_float(v[k]))
                                               << ((k * (int)kDigitBits) & 31);
           cp_async_wait_all();
           __syncwarp();
@@ -912,9 +919,10 @@ uint32_t tc_smem_bytes(uint32_t W, uint32_t btile, uint32_t ns) {
 bool make_tc_shape(const KArgs& a, TcShape* t) {
   if (a.Ng < 128 || a.W == 0 || a.L == 0 || a.ell != 32 * a.L) return false;
   const uint32_t NP1 = a.W / a.L;
-  // digit width: exact fp16 operand and every column sum below 2^24
   t->dw = kDigitBits;
-  if ((uint64_t)a.Ng * ((1u << kDigitBits) - 1u) >= (1u << 24)) return false;
+  // digit width: exact fp16 operand; every column sum below 2^23, so that the
+  // epilogue reads it from the fp32 accumulator with one add (Ng <= 4097)
+  if ((uint64_t)a.Ng * ((1u << kDigitBits) - 1u) >= (1u << 23)) return false;
   t->D = (a.ell + t->dw - 1) / t->dw;
   t->dpad = (t->D + 15) / 16 * 16;
   t->ndpad = NP1 * t->dpad;

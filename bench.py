@@ -757,15 +757,21 @@ def main():
                  "speedup_of_batched": pms / ms}
         del plans
 
-    # end to end through the C ABI with host buffers (H2D in, D2H out, each step)
+    # end to end through the C ABI with host buffers: every step copies its
+    # inputs from pinned host memory and its outputs back, double-buffered so
+    # that step i's copies overlap steps i - 1 and i + 1
     h_in = d_in.cpu().pin_memory()
-    h_out = torch.empty(d_out.shape, dtype=d_out.dtype).pin_memory()
+    h_outs = [torch.empty(d_out.shape, dtype=d_out.dtype).pin_memory() for _ in range(2)]
+    d_in2 = torch.empty_like(d_in)
+    d_out2 = torch.empty_like(d_out)
+    pipe = lambda n: batch.eval_host_pipelined(  # noqa: E731
+        [h_in] * n, [h_outs[i % 2] for i in range(n)], [d_in, d_in2], [d_out, d_out2], scratch,
+        stream)
     with torch.cuda.stream(stream):
-        batch.eval_host(h_in, h_out, d_in, d_out, scratch, stream)
+        pipe(2)   # warm-up: both buffer sets' graphs
         barrier()
         t0 = time.perf_counter()
-        for _ in range(args.steps):
-            batch.eval_host(h_in, h_out, d_in, d_out, scratch, stream)
+        pipe(args.steps)
         e2e_ms = (time.perf_counter() - t0) * 1000.0 / args.steps
         barrier()
     e2e_ms = max_over_ranks(e2e_ms, world, "cuda")
@@ -796,7 +802,9 @@ def main():
             "cpu_baseline": cpu,
             "e2e": {"value": world * len(items) * 1000.0 / e2e_ms, "unit": "FFT/s",
                     "h2d_bytes_per_step": info["inputs"] * cw * 4,
-                    "d2h_bytes_per_step": info["outputs"] * cw * 4},
+                    "d2h_bytes_per_step": info["outputs"] * cw * 4,
+                    "api": "sfft_batch_eval_host_pipelined (copies overlapped with the "
+                           "neighbouring steps)"},
             "gpu_launches": args.steps * kernels_per_step,
             "clocks": clk.summary(),
         }

@@ -344,8 +344,9 @@ typedef struct sfft_request {
  * outputs are the requests' ciphertexts concatenated in request order
  * (sfft_batch_offsets gives each request's first ciphertext). Unless
  * SFFT_BATCH_NO_GRAPH, sfft_batch_eval captures the whole launch sequence as
- * a CUDA graph on first use and replays it (re-captured when a pointer or
- * the stream changes; needs a non-default stream). flags: SFFT_PLAN_* too. */
+ * a CUDA graph on first use and replays it (two pointer sets are kept,
+ * re-captured when a third appears or the stream changes; needs a non-default
+ * stream). flags: SFFT_PLAN_* too. */
 #define SFFT_BATCH_NO_GRAPH 4u
 int sfft_batch_create(const sfft_params* p, const sfft_request* reqs, uint32_t count,
                       uint32_t flags, sfft_batch** out);
@@ -358,6 +359,17 @@ int sfft_batch_eval(sfft_batch* b, const uint32_t* d_in, uint32_t* d_out, uint32
 int sfft_batch_eval_host(sfft_batch* b, const uint32_t* h_in, uint32_t* h_out, uint32_t* d_in,
                          uint32_t* d_out, uint32_t* d_scratch, uint64_t scratch_bytes,
                          void* stream);
+/* End to end for count steps, double-buffered: step i copies h_in[i] into
+ * d_in[i % 2] (on an internal copy stream, once step i - 2 has read that set),
+ * evaluates into d_out[i % 2] on `stream` (a non-default stream), and copies
+ * d_out[i % 2] to h_out[i] on a second copy stream while step i + 1 runs.
+ * h_in / h_out: count pointers to host buffers (pinned for overlap; entries
+ * may repeat), d_in / d_out: two device buffer sets each. Returns after every
+ * copy has completed. */
+int sfft_batch_eval_host_pipelined(sfft_batch* b, const uint32_t* const* h_in,
+                                   uint32_t* const* h_out, uint32_t count,
+                                   uint32_t* const* d_in, uint32_t* const* d_out,
+                                   uint32_t* d_scratch, uint64_t scratch_bytes, void* stream);
 int sfft_batch_check(sfft_batch* b, void* stream);
 /* Per-launch event timing (graph replay is bypassed while timing is on). */
 int sfft_batch_set_timing(sfft_batch* b, int on);

@@ -360,6 +360,18 @@ class Batch:
         check(lib().sfft_batch_eval_host(self._h, _dptr(h_in), _dptr(h_out), _dptr(d_in),
                                          _dptr(d_out), _dptr(d_scratch), nbytes, _stream(stream)))
 
+    def eval_host_pipelined(self, h_ins, h_outs, d_ins, d_outs, d_scratch, stream):
+        """sfft_batch_eval_host_pipelined: len(h_ins) steps through two device
+        buffer sets (d_ins, d_outs: two tensors each), copies overlapped."""
+        n = len(h_ins)
+        if len(h_outs) != n or len(d_ins) != 2 or len(d_outs) != 2:
+            raise ValueError("need one output per input and two device buffer sets")
+        arr = lambda ts: (ctypes.c_void_p * len(ts))(*[int(t.data_ptr()) for t in ts])  # noqa: E731
+        nbytes = 0 if d_scratch is None else d_scratch.numel() * d_scratch.element_size()
+        check(lib().sfft_batch_eval_host_pipelined(self._h, arr(h_ins), arr(h_outs), n, arr(d_ins),
+                                                   arr(d_outs), _dptr(d_scratch), nbytes,
+                                                   _stream(stream)))
+
     def check(self, stream=None):
         check(lib().sfft_batch_check(self._h, _stream(stream)))
 

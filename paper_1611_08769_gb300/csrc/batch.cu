@@ -87,22 +87,33 @@ void merge_programs(const std::vector<Program>& parts, const std::vector<std::ar
   }
 }
 
-// Graph replay of run_program for fixed pointers and stream.
-struct GraphCache {
+// Graph replays of run_program for fixed pointers and stream: two entries
+// (the two buffer sets of a double-buffered pipeline), least recently used
+// replaced.
+struct GraphEntry {
   cudaGraphExec_t exec = nullptr;
   const void* key[4] = {nullptr, nullptr, nullptr, nullptr};
-  uint64_t bytes = 0;
+  uint64_t bytes = 0, used = 0;
+};
+struct GraphCache {
+  GraphEntry e[2];
+  uint64_t clock = 0;
   ~GraphCache() {
-    if (exec) cudaGraphExecDestroy(exec);
+    for (GraphEntry& g : e)
+      if (g.exec) cudaGraphExecDestroy(g.exec);
   }
 };
 
-int run_graph(GraphCache* gc, const Shape& s, const DeviceProgram& dp, const uint32_t* d_in,
+int run_graph(GraphCache* cache, const Shape& s, const DeviceProgram& dp, const uint32_t* d_in,
               uint32_t* d_out, uint32_t* d_scratch, uint64_t scratch_bytes, cudaStream_t st) {
   if (!st) return fail(SFFT_EINVAL, "graph replay needs a non-default stream");
   const void* key[4] = {d_in, d_out, d_scratch, st};
-  const bool hit = gc->exec && std::memcmp(key, gc->key, sizeof(key)) == 0 && gc->bytes == scratch_bytes;
+  GraphEntry* gc = nullptr;
+  for (GraphEntry& g : cache->e)
+    if (g.exec && std::memcmp(key, g.key, sizeof(key)) == 0 && g.bytes == scratch_bytes) gc = &g;
+  const bool hit = gc != nullptr;
   if (!hit) {
+    gc = cache->e[0].used <= cache->e[1].used ? &cache->e[0] : &cache->e[1];
     if (gc->exec) {
       cudaGraphExecDestroy(gc->exec);
       gc->exec = nullptr;
@@ -124,6 +135,7 @@ int run_graph(GraphCache* gc, const Shape& s, const DeviceProgram& dp, const uin
     std::memcpy(gc->key, key, sizeof(key));
     gc->bytes = scratch_bytes;
   }
+  gc->used = ++cache->clock;
   cudaError_t e = cudaGraphLaunch(gc->exec, st);
   return e == cudaSuccess ? SFFT_OK : cuda_fail(e, "cudaGraphLaunch");
 }
@@ -140,6 +152,18 @@ struct sfft_batch {
   sfft::Timer timer;
   bool use_graph = true;
   uint64_t fft_products = 0;
+  // host pipeline: copy streams and the events that order them with the
+  // evaluations (created on first use)
+  cudaStream_t h2d = nullptr, d2h = nullptr;
+  cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_done[2] = {nullptr, nullptr},
+              ev_out[2] = {nullptr, nullptr};
+  ~sfft_batch() {
+    for (int k = 0; k < 2; k++)
+      for (cudaEvent_t ev : {ev_in[k], ev_done[k], ev_out[k]})
+        if (ev) cudaEventDestroy(ev);
+    if (h2d) cudaStreamDestroy(h2d);
+    if (d2h) cudaStreamDestroy(d2h);
+  }
 };
 
 using namespace sfft;
@@ -243,6 +267,53 @@ int sfft_batch_eval_host(sfft_batch* b, const uint32_t* h_in, uint32_t* h_out, u
   if (e != cudaSuccess) return cuda_fail(e, "D2H copy");
   e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "stream sync");
+  return check_device_error(b->dev.err, st);
+}
+
+int sfft_batch_eval_host_pipelined(sfft_batch* b, const uint32_t* const* h_in,
+                                   uint32_t* const* h_out, uint32_t count,
+                                   uint32_t* const* d_in, uint32_t* const* d_out,
+                                   uint32_t* d_scratch, uint64_t scratch_bytes, void* stream) {
+  if (!b || !h_in || !h_out || !d_in || !d_out) return fail(SFFT_EINVAL, "null argument");
+  if (!stream) return fail(SFFT_EINVAL, "the pipeline needs a non-default stream");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  if (!b->h2d) {
+    e = cudaStreamCreateWithFlags(&b->h2d, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->d2h, cudaStreamNonBlocking);
+    for (int k = 0; k < 2 && e == cudaSuccess; k++) {
+      e = cudaEventCreateWithFlags(&b->ev_in[k], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_done[k], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out[k], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "pipeline streams");
+  }
+  const uint64_t in_b = b->merged.n_inputs * b->s.ctw * 4, out_b = b->merged.n_outputs * b->s.ctw * 4;
+  for (uint32_t i = 0; i < count; i++) {
+    const uint32_t k = i & 1u;
+    if (!h_in[i] || !h_out[i] || !d_in[k] || !d_out[k]) return fail(SFFT_EINVAL, "null buffer");
+    // inputs of step i into set k once step i - 2 has read it
+    if (i >= 2 && (e = cudaStreamWaitEvent(b->h2d, b->ev_done[k], 0)) != cudaSuccess) break;
+    if ((e = cudaMemcpyAsync(d_in[k], h_in[i], in_b, cudaMemcpyHostToDevice, b->h2d)) != cudaSuccess)
+      break;
+    if ((e = cudaEventRecord(b->ev_in[k], b->h2d)) != cudaSuccess) break;
+    // evaluation once its inputs landed and step i - 2's outputs left set k
+    if ((e = cudaStreamWaitEvent(st, b->ev_in[k], 0)) != cudaSuccess) break;
+    if (i >= 2 && (e = cudaStreamWaitEvent(st, b->ev_out[k], 0)) != cudaSuccess) break;
+    int rc = sfft_batch_eval(b, d_in[k], d_out[k], d_scratch, scratch_bytes, stream);
+    if (rc) return rc;
+    if ((e = cudaEventRecord(b->ev_done[k], st)) != cudaSuccess) break;
+    // outputs back while the next step runs
+    if ((e = cudaStreamWaitEvent(b->d2h, b->ev_done[k], 0)) != cudaSuccess) break;
+    if ((e = cudaMemcpyAsync(h_out[i], d_out[k], out_b, cudaMemcpyDeviceToHost, b->d2h)) != cudaSuccess)
+      break;
+    if ((e = cudaEventRecord(b->ev_out[k], b->d2h)) != cudaSuccess) break;
+  }
+  cudaError_t s1 = cudaStreamSynchronize(b->h2d), s2 = cudaStreamSynchronize(st),
+              s3 = cudaStreamSynchronize(b->d2h);
+  if (e != cudaSuccess) return cuda_fail(e, "pipelined evaluation");
+  if (s1 != cudaSuccess || s2 != cudaSuccess || s3 != cudaSuccess)
+    return cuda_fail(s1 != cudaSuccess ? s1 : s2 != cudaSuccess ? s2 : s3, "stream sync");
   return check_device_error(b->dev.err, st);
 }
 

@@ -83,6 +83,9 @@ SIGNATURES = {
     "sfft_batch_offsets": (c_i32, [c_void_p, P(c_u64), P(c_u64)]),
     "sfft_batch_eval": (c_i32, [c_void_p, c_void_p, c_void_p, c_void_p, c_u64, c_void_p]),
     "sfft_batch_check": (c_i32, [c_void_p, c_void_p]),
+    "sfft_batch_eval_host_pipelined": (c_i32, [c_void_p, P(c_void_p), P(c_void_p), c_u32,
+                                               P(c_void_p), P(c_void_p), c_void_p, c_u64,
+                                               c_void_p]),
     "sfft_batch_eval_host": (c_i32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                     c_u64, c_void_p]),
     "sfft_batch_set_timing": (c_i32, [c_void_p, ctypes.c_int]),

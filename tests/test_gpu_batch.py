@@ -118,3 +118,42 @@ def test_batch_request_matches_oracle_and_decrypts():
     q = [fx.quantize(x, F, f) for x in re_]
     er, ei = fx.fft_int(q, [0] * N, F, f)
     assert list(raw) == [v for k in range(N) for v in (er[k], ei[k])]
+
+
+@pytest.mark.parametrize("pset", ["P0", "P2"])
+def test_pipelined_host_evaluation(pset):
+    """Five steps through two device buffer sets with the copies on their own
+    streams: every step's host output equals the batch's device-path result
+    for that step's inputs (different inputs per step, one repeated)."""
+    sp = sf.param_set(pset)
+    reqs = REQS[:3]
+    batch = sf.Batch(sp, reqs)
+    info = batch.info
+    cw = info["ct_words"]
+    keys = sf.keygen(sp, 5)
+    pub = torch.from_numpy(keys.public().view(np.int32)).cuda()
+    steps_in = []
+    for s in range(3):   # different plaintexts and randomness per step
+        cts = []
+        for r, (N1, N2, F, f) in enumerate(reqs):
+            re_, im_ = signal_1d(N1 * N2, -1, 1, 10 * s + r) if N2 == 1 else image_2d(N1, N2, 10 * s + r)
+            d = torch.empty((N1 * N2 * 2 * F, cw), dtype=torch.int32, device="cuda")
+            sf.encrypt_bits_device(sp, pub, re_, im_, F, f, 50 + 10 * s + r, d)
+            cts.append(d)
+        steps_in.append(cts)
+    h_ins = [torch.cat(c).cpu().pin_memory() for c in steps_in]
+    order = [0, 1, 2, 0, 1]
+    stream = torch.cuda.Stream()
+    d_ins = [torch.empty((info["inputs"], cw), dtype=torch.int32, device="cuda") for _ in range(2)]
+    d_outs = [torch.empty((info["outputs"], cw), dtype=torch.int32, device="cuda") for _ in range(2)]
+    scr = torch.empty(max(1, info["scratch_bytes"] // 4), dtype=torch.int32, device="cuda")
+    h_outs = [torch.empty((info["outputs"], cw), dtype=torch.int32).pin_memory() for _ in order]
+    batch.eval_host_pipelined([h_ins[i] for i in order], h_outs, d_ins, d_outs, scr, stream)
+    # reference: the device path, one step at a time
+    ref_out = torch.empty((info["outputs"], cw), dtype=torch.int32, device="cuda")
+    for i, h_out in zip(order, h_outs):
+        with torch.cuda.stream(stream):
+            batch.eval(h_ins[i].cuda(), ref_out, scr, stream)
+        batch.check(stream)
+        torch.cuda.synchronize()
+        assert torch.equal(h_out, ref_out.cpu())

@@ -84,3 +84,36 @@ def test_refresh_bit_exact(xcarry, flags):
     for ct, mu in zip(got, bits):
         assert gsw.decrypt(ko, ct) == mu
         assert max(map(abs, gsw.noise(ko, ct, mu))) <= bound < p.q // 8
+
+
+def test_refresh_at_full_size():
+    """Refresh at the ell of the 64-point 16-bit workload (1056) in the launch
+    configuration the bench times: too large for the oracle to evaluate gate
+    by gate, so the outputs are checked by the properties the construction
+    guarantees: each decrypts (oracle keys) to its source bit and its exact
+    noise is within the static bound, which is below q/8."""
+    ell = sf.min_ell(64, 1, 16, 8, n=1, chi=1)
+    assert ell == 1056
+    sp = sf.param_set("P1", ell)
+    p = gsw.Params(sp.n, sp.ell, sp.m, sp.chi)
+    keys = sf.keygen(sp, 77)
+    d_pub = torch.from_numpy(keys.public().view(np.int32)).cuda()
+    cw = sf.ct_words(sp)
+    kb = keys.key_bits()
+    d_bk = torch.zeros((len(kb), cw), dtype=torch.int32, device="cuda")
+    sf.encrypt_raw_bits_device(sp, d_pub, kb, 3, d_bk)
+    bits = np.array([1, 0, 1, 1], dtype=np.uint8)
+    d_src = torch.zeros((len(bits), cw), dtype=torch.int32, device="cuda")
+    sf.encrypt_raw_bits_device(sp, d_pub, bits, 4, d_src)
+    plan = sf.Plan.refresher(sp, len(bits))
+    assert plan.info["gate_kernel"] == sf.KERNEL_TC
+    out, scratch = _buffers(plan.info)
+    plan.refresh(d_bk, d_src, out, scratch)
+    plan.check()
+    got = out.cpu().numpy().view(np.uint32).reshape(len(bits), p.Ng, p.n + 1, p.L)
+    ko = gsw.Keys(p, 77)
+    bound = 1 << plan.info["noise_bits"]   # every output's noise is below it
+    assert bound <= p.q // 8
+    for ct, mu in zip(got, bits):
+        assert gsw.decrypt(ko, ct) == mu
+        assert max(map(abs, gsw.noise(ko, ct, int(mu)))) < bound

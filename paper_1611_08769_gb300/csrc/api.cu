@@ -221,7 +221,7 @@ int plan_create(const sfft_params* p, const CircuitSpec& spec, uint32_t flags, s
   int rc = make_shape(p, &pl->s, false);
   if (rc) return rc;
   if ((rc = build_circuit(&pl->circuit, spec, flags))) return rc;
-  compile(pl->circuit, pl->s, &pl->prog);
+  compile(pl->circuit, pl->s, &pl->prog, level_cap(spec));
   if (spec.op == kOpRefresh) {   // refreshed outputs must be refreshable again
     if (pl->prog.noise_bits > pl->s.ell - 3 && !(flags & SFFT_PLAN_ALLOW_NOISY))
       return fail(SFFT_EPARAM, "refresh output bound reaches q/8: raise ell "

@@ -637,7 +637,9 @@ uint16_t adjusted(Code k, bool negA, bool negB) {
 
 }  // namespace
 
-void compile(const Circuit& c, const Shape& s, Program* prog) {
+uint64_t level_cap(const CircuitSpec& spec) { return spec.op == kOpRefresh ? kRefreshLevelCap : 0; }
+
+void compile(const Circuit& c, const Shape& s, Program* prog, uint64_t width_cap) {
   std::vector<char> ln, lp;
   liveness(c, &ln, &lp);
   const size_t nn = c.depth.size();
@@ -650,6 +652,7 @@ void compile(const Circuit& c, const Shape& s, Program* prog) {
   std::vector<uint32_t> sl(nn, 0);
   std::vector<uint32_t> plev(c.products.size(), 0);
   std::vector<char> lin_node(nn, 0);
+  std::vector<uint64_t> width(2, 0);   // products per level so far
   uint32_t maxlev = 0;
   for (size_t p = 0; p < c.products.size(); p++) {
     if (!lp[p]) continue;
@@ -660,6 +663,12 @@ void compile(const Circuit& c, const Shape& s, Program* prog) {
       lev = std::max(1u, std::max(sl[na] + lin_node[na], sl[nb] + lin_node[nb]));
     else
       lev = 1 + std::max(sl[na], sl[nb]);
+    if (!g.is_add) {
+      if (width_cap)
+        while (lev < width.size() && width[lev] >= width_cap) lev++;
+      if (lev >= width.size()) width.resize(lev + 1, 0);
+      width[lev]++;
+    }
     plev[p] = lev;
     for (uint32_t node : {g.out_xor, g.out_and})
       if (node) {

@@ -135,6 +135,7 @@ bool build_words(Circuit* c, uint32_t op, uint64_t count, uint32_t F, uint32_t f
 // Wallace stages and ADD_p; output i = XOR(S_{p-1}, S_{p-2}).
 bool build_refresh(Circuit* c, uint32_t n, uint32_t ell, uint64_t count);
 constexpr uint32_t kOpRefresh = 0x100;
+constexpr uint64_t kRefreshLevelCap = 4096;   // products per level of a refresh program
 
 // What a plan evaluates: an FFT (op 0), count word operations (SFFT_WORD_*)
 // or count refreshes (kOpRefresh, at parameters n, ell).
@@ -171,7 +172,14 @@ struct Program {
 
 // Prunes dead gates, levelises, allocates scratch slots with reuse after last
 // use, and computes the static noise bound for the given parameters.
-void compile(const Circuit& c, const Shape& s, Program* prog);
+// width_cap > 0 bounds the products of a level: a product whose inputs are
+// ready at level l runs at the first level >= l with room (creation order),
+// which bounds the ciphertexts alive at once for circuits whose ready set is
+// very wide (refresh).
+void compile(const Circuit& c, const Shape& s, Program* prog, uint64_t width_cap = 0);
+
+// The level width cap a plan of this kind compiles with (0: none).
+uint64_t level_cap(const CircuitSpec& spec);
 
 // Bit length of the largest static noise bound of the circuit's live wires
 // (fresh ciphertext m * chi; gate (|c1|+|c3|) E_A + (|c2| + |c3| Ng) E_B).

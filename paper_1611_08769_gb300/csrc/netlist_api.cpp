@@ -24,7 +24,7 @@ int build(const sfft_params* p, const CircuitSpec& spec, uint32_t flags, Shape* 
   int rc = make_shape(p, s, false);
   if (rc) return rc;
   if ((rc = build_circuit(c, spec, flags))) return rc;
-  compile(*c, *s, prog);
+  compile(*c, *s, prog, level_cap(spec));
   return SFFT_OK;
 }
 

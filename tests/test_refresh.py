@@ -169,7 +169,8 @@ def test_native_refresh_program_matches_oracle(n, ell, xcarry):
     st = circuit.stats(c)
     assert info["inputs"] == n * ell + 1 and info["outputs"] == count
     assert info["products"] == st["products"] == circuit.stats(worst)["products"]
-    assert info["levels"] == st["depth"]
+    # levels: the multiplicative depth, more where a level's width is capped
+    assert info["levels"] >= st["depth"] and info["max_level_width"] <= 4096
     assert info["noise_bits"] == noise.max_bound(worst, p).bit_length()
     h_rows = np.array([gsw.to_limbs(np.array(r, dtype=object), p.L).reshape(-1) for r in rows],
                       dtype=np.uint32)

@@ -175,7 +175,16 @@ def measured_peaks():
 TC_DRAM_BYTES_PER_PRODUCT = {(1, 1056): 3.120e6}
 
 
-def roofline(params, gate_kernel, gate_ms, launches, gates_timed, tc_columns=0):
+def expand_bytes_per_product(params):
+    """Algorithmic bytes of k_expand_b per product: B' read once (Ng rows of
+    (n+1) ell bits) and its tensor-core image written once (per 128-row K
+    step two atoms of (n+1) ceil16(ceil(ell / 11)) digit rows x 128 bytes)."""
+    Ng = (params.n + 1) * params.ell
+    ndpad = (params.n + 1) * ((-(-params.ell // 11) + 15) // 16 * 16)
+    return Ng * Ng // 8 + -(-Ng // 128) * ndpad * 256
+
+
+def roofline(params, gate_kernel, gate_ms, launches, gates_timed, tc_columns=0, expand_ms=None):
     """Roofline of the dominant kernel (the gate product) from CUDA-event times.
 
     Integer kernel: unit = one product = Ng^2 (n+1) L 32-bit limb additions,
@@ -183,7 +192,9 @@ def roofline(params, gate_kernel, gate_ms, launches, gates_timed, tc_columns=0):
     = the dense contraction 2 Ng Ng C flops (bits x 11-bit digits, C = (n+1)
     ceil(ell / 11) digit columns per row), against the measured dense bf16
     rate (kind::f16 runs fp16 at the bf16 rate); the sustained figure, since
-    the kernel runs inside a long step.
+    the kernel runs inside a long step. With the tensor-core path, `expand`
+    gives the B expansion (k_expand_b, HBM-bound) against the measured copy
+    rate from its own events.
     """
     Ng, L = (params.n + 1) * params.ell, params.ell // 32
     W = (params.n + 1) * L
@@ -197,11 +208,20 @@ def roofline(params, gate_kernel, gate_ms, launches, gates_timed, tc_columns=0):
         peak = float(peaks["bf16_tflops_sustained"])
         per = TC_DRAM_BYTES_PER_PRODUCT.get((params.n, params.ell))
         traffic = per * gates_timed / max(1, launches) if per else None
-        return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per launch",
-                "kernel": "k_gate_tc (+k_expand_b)",
-                "avg_launch_ms": avg_launch_ms, "flops_per_product": 2.0 * Ng * Ng * cols,
-                "peak_source": f"bf16_tflops_sustained {src}"}
+        out = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+               "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per launch",
+               "kernel": "k_gate_tc", "avg_launch_ms": avg_launch_ms,
+               "flops_per_product": 2.0 * Ng * Ng * cols,
+               "peak_source": f"bf16_tflops_sustained {src}"}
+        if expand_ms:
+            xb = expand_bytes_per_product(params)
+            xa = xb * gates_timed / (expand_ms / 1000.0) / 1e9
+            hbm = float(peaks["hbm_gbs"])
+            out["expand"] = {"kernel": "k_expand_b", "bound": "hbm", "achieved": xa, "peak": hbm,
+                             "unit": "GB/s", "frac": xa / hbm, "bytes_per_product": xb,
+                             "avg_launch_ms": expand_ms / max(1, launches),
+                             "peak_source": f"hbm_gbs {src}"}
+        return out
     ops = float(Ng) * Ng * (params.n + 1) * L * gates_timed
     achieved = ops / sec
     return {"bound": "alu", "achieved": achieved / 1e12, "peak": ALU_PEAK_OPS / 1e12,
@@ -481,7 +501,7 @@ def run_refresh(args):
         plan.check(stream)
         plan.set_timing(True)
         run()
-        gate_ms, launches, gates_timed = plan.timing()
+        gate_ms, expand_ms, launches, gates_timed = plan.timing()
         plan.set_timing(False)
         # end to end: sources from pinned host memory, refreshed ciphertexts back
         h_src = d_src.cpu().pin_memory()
@@ -521,7 +541,7 @@ def run_refresh(args):
         "data": "synthetic", "config": cfg,
         "gates_per_s": info["products"] * 1000.0 / ms,
         "roofline": roofline(params, info["gate_kernel"], gate_ms, launches, gates_timed,
-                             info["tc_columns"]),
+                             info["tc_columns"], expand_ms),
         "cpu_baseline": cpu,
         "e2e": {"value": count * 1000.0 / e2e_ms, "unit": "ct/s",
                 "h2d_bytes_per_step": count * cw * 4, "d2h_bytes_per_step": count * cw * 4},
@@ -734,7 +754,7 @@ def main():
     with torch.cuda.stream(stream):
         run_b()
     kernels_per_step = sf.lib().sfft_launch_count() - n0
-    gate_ms, launches, gates_timed = batch.timing()
+    gate_ms, expand_ms, launches, gates_timed = batch.timing()
     batch.set_timing(False)
 
     # plain level-by-level evaluator on the same workload (per-request plans)
@@ -796,7 +816,7 @@ def main():
             "data": "synthetic", "config": cfg,
             "gates_per_s": world * info["products"] * 1000.0 / ms,
             "roofline": roofline(params, info["gate_kernel"], gate_ms, launches, gates_timed,
-                                 info["tc_columns"]),
+                                 info["tc_columns"], expand_ms),
             "plain": plain,
             "cpu_baseline": cpu,
             "e2e": {"value": world * len(items) * 1000.0 / e2e_ms, "unit": "FFT/s",

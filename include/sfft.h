@@ -321,12 +321,14 @@ int sfft_eval_fft_noalloc(sfft_plan* plan, const uint32_t* d_in, uint32_t* d_out
 uint64_t sfft_noalloc_scratch_bytes(void);
 
 /* Kernel timing: when on, CUDA events are recorded on the launching stream
- * around every gate-kernel launch of sfft_eval_fft*. sfft_plan_timing waits
- * for them, returns the summed gate-kernel milliseconds, the number of
- * gate-kernel launches and the products they evaluated since the last read,
- * then resets. */
+ * around every gate-kernel launch of sfft_eval_fft* (the tensor-core GEMM or
+ * the integer kernel) and around every B expansion. sfft_plan_timing waits
+ * for them and returns, since the last read, the summed gate-kernel and
+ * expansion milliseconds, the number of levels launched and the products
+ * they evaluated, then resets. Any output pointer may be NULL. */
 int sfft_plan_set_timing(sfft_plan* plan, int on);
-int sfft_plan_timing(sfft_plan* plan, double* gate_ms, uint64_t* launches, uint64_t* products);
+int sfft_plan_timing(sfft_plan* plan, double* gate_ms, double* expand_ms, uint64_t* launches,
+                     uint64_t* products);
 
 /* ------------------------------------------------------------- batches */
 
@@ -373,7 +375,8 @@ int sfft_batch_eval_host_pipelined(sfft_batch* b, const uint32_t* const* h_in,
 int sfft_batch_check(sfft_batch* b, void* stream);
 /* Per-launch event timing (graph replay is bypassed while timing is on). */
 int sfft_batch_set_timing(sfft_batch* b, int on);
-int sfft_batch_timing(sfft_batch* b, double* gate_ms, uint64_t* launches, uint64_t* products);
+int sfft_batch_timing(sfft_batch* b, double* gate_ms, double* expand_ms, uint64_t* launches,
+                      uint64_t* products);
 void sfft_batch_free(sfft_batch* b);
 
 /* ------------------------------------------------------------- serving */

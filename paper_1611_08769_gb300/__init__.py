@@ -313,12 +313,13 @@ class Plan:
         check(lib().sfft_plan_set_timing(self._h, 1 if on else 0))
 
     def timing(self):
-        """(gate-kernel ms, launches, products) since the last read."""
-        ms = ctypes.c_double()
+        """(gate-kernel ms, B-expansion ms, levels launched, products) since the last read."""
+        ms, xms = ctypes.c_double(), ctypes.c_double()
         n = ctypes.c_uint64()
         g = ctypes.c_uint64()
-        check(lib().sfft_plan_timing(self._h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(g)))
-        return ms.value, n.value, g.value
+        check(lib().sfft_plan_timing(self._h, ctypes.byref(ms), ctypes.byref(xms), ctypes.byref(n),
+                                     ctypes.byref(g)))
+        return ms.value, xms.value, n.value, g.value
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -379,11 +380,13 @@ class Batch:
         check(lib().sfft_batch_set_timing(self._h, 1 if on else 0))
 
     def timing(self):
-        ms = ctypes.c_double()
+        """(gate-kernel ms, B-expansion ms, levels launched, products) since the last read."""
+        ms, xms = ctypes.c_double(), ctypes.c_double()
         n = ctypes.c_uint64()
         g = ctypes.c_uint64()
-        check(lib().sfft_batch_timing(self._h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(g)))
-        return ms.value, n.value, g.value
+        check(lib().sfft_batch_timing(self._h, ctypes.byref(ms), ctypes.byref(xms), ctypes.byref(n),
+                                      ctypes.byref(g)))
+        return ms.value, xms.value, n.value, g.value
 
     def __del__(self):
         h = getattr(self, "_h", None)

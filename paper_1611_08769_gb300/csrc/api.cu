@@ -57,40 +57,47 @@ int launch_gates(const KArgs& a, cudaStream_t st) {
   if (a.kernel == KERNEL_TC) return fail(SFFT_EPARAM, "tensor-core kernel does not support this shape");
   const uint64_t tasks = a.n * (a.Ng / 32);
   const uint64_t blocks = (tasks * 32 + 255) / 256;
+  Timer* tm = static_cast<Timer*>(a.timer);
+  if (tm) cudaEventRecord(tm->next(kTimeGate), st);
   if (a.W <= 2)
     k_gate_generic<2><<<(unsigned)blocks, 256, 0, st>>>(a);
   else if (a.W <= 4)
     k_gate_generic<4><<<(unsigned)blocks, 256, 0, st>>>(a);
   else
     k_gate_generic<8><<<(unsigned)blocks, 256, 0, st>>>(a);
+  if (tm) cudaEventRecord(tm->next(kTimeGate), st);
   count_launches(1);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? SFFT_OK : cuda_fail(e, "gate kernel launch");
 }
 
-cudaEvent_t Timer::next() {
-  if (used == pool.size()) {
+cudaEvent_t Timer::next(int kind) {
+  if (used[kind] == pool[kind].size()) {
     cudaEvent_t e;
     cudaEventCreate(&e);
-    pool.push_back(e);
+    pool[kind].push_back(e);
   }
-  return pool[used++];
+  return pool[kind][used[kind]++];
 }
 
 double Timer::drain_ms() {
-  double ms = 0;
-  for (size_t k = 0; k + 1 < used; k += 2) {
-    cudaEventSynchronize(pool[k + 1]);
-    float t = 0;
-    cudaEventElapsedTime(&t, pool[k], pool[k + 1]);
-    ms += t;
+  double ms[2] = {0, 0};
+  for (int kind = 0; kind < 2; kind++) {
+    for (size_t k = 0; k + 1 < used[kind]; k += 2) {
+      cudaEventSynchronize(pool[kind][k + 1]);
+      float t = 0;
+      cudaEventElapsedTime(&t, pool[kind][k], pool[kind][k + 1]);
+      ms[kind] += t;
+    }
+    used[kind] = 0;
   }
-  used = 0;
-  return ms;
+  last_expand_ms = ms[kTimeExpand];
+  return ms[kTimeGate];
 }
 
 Timer::~Timer() {
-  for (cudaEvent_t e : pool) cudaEventDestroy(e);
+  for (auto& p : pool)
+    for (cudaEvent_t e : p) cudaEventDestroy(e);
 }
 
 int run_program(const Shape& s, const DeviceProgram& dp, const uint32_t* d_in, uint32_t* d_out,
@@ -112,11 +119,11 @@ int run_program(const Shape& s, const DeviceProgram& dp, const uint32_t* d_in, u
     a.aux = dp.aux + dp.level_off[l];
     a.n = mid - dp.level_off[l];
     const bool timed = tm && tm->on && a.n;
-    if (timed) cudaEventRecord(tm->next(), st);
+    a.timer = timed ? tm : nullptr;   // the gate launchers record their kernels
     int rc = launch_gates(a, st);
+    a.timer = nullptr;
     if (rc) return rc;
     if (timed) {
-      cudaEventRecord(tm->next(), st);
       tm->launches++;
       tm->products += a.n;
     }
@@ -384,10 +391,12 @@ int sfft_plan_set_timing(sfft_plan* pl, int on) {
   return SFFT_OK;
 }
 
-int sfft_plan_timing(sfft_plan* pl, double* gate_ms, uint64_t* launches, uint64_t* products) {
+int sfft_plan_timing(sfft_plan* pl, double* gate_ms, double* expand_ms, uint64_t* launches,
+                     uint64_t* products) {
   if (!pl) return fail(SFFT_EINVAL, "plan is NULL");
   double ms = pl->timer.drain_ms();
   if (gate_ms) *gate_ms = ms;
+  if (expand_ms) *expand_ms = pl->timer.last_expand_ms;
   if (launches) *launches = pl->timer.launches;
   if (products) *products = pl->timer.products;
   pl->timer.launches = pl->timer.products = 0;

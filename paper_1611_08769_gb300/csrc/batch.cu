@@ -330,9 +330,11 @@ int sfft_batch_set_timing(sfft_batch* b, int on) {
   return SFFT_OK;
 }
 
-int sfft_batch_timing(sfft_batch* b, double* gate_ms, uint64_t* launches, uint64_t* products) {
+int sfft_batch_timing(sfft_batch* b, double* gate_ms, double* expand_ms, uint64_t* launches,
+                      uint64_t* products) {
   if (!b) return fail(SFFT_EINVAL, "batch is NULL");
   const double ms = b->timer.drain_ms();
+  if (expand_ms) *expand_ms = b->timer.last_expand_ms;
   if (gate_ms) *gate_ms = ms;
   if (launches) *launches = b->timer.launches;
   if (products) *products = b->timer.products;

@@ -19,6 +19,7 @@ struct KArgs {
   uint32_t kernel;       // KERNEL_AUTO / KERNEL_INT / KERNEL_TC
   uint8_t* bx;           // tensor-core kernel: expanded B operands (scratch)
   uint32_t bx_shared;    // 1: every gate has the same B operand (expanded once)
+  void* timer;           // host: the Timer recording this launch's kernels, or null
 };
 
 constexpr uint32_t KERNEL_AUTO = 0, KERNEL_INT = 1, KERNEL_TC = 2;

@@ -60,13 +60,17 @@ uint64_t scratch_layout(const Shape& s, uint64_t slots, uint64_t max_width, bool
 int make_device_program(const Program& p, DeviceProgram* dp);
 void free_device_program(DeviceProgram* dp);
 // Optional per-launch CUDA-event timing of gate kernels.
+// Event pairs around kernel launches, by kind: the gate kernels (the GEMM of
+// the tensor-core path or the integer kernel) and the B expansion.
+constexpr int kTimeGate = 0, kTimeExpand = 1;
 struct Timer {
   bool on = false;
-  std::vector<cudaEvent_t> pool;
-  size_t used = 0;
+  std::vector<cudaEvent_t> pool[2];
+  size_t used[2] = {0, 0};
   uint64_t launches = 0, products = 0;
-  cudaEvent_t next();   // an event from the pool (grows on demand)
-  double drain_ms();    // waits, sums pairs, resets
+  double last_expand_ms = 0;   // expansion time of the last drain
+  cudaEvent_t next(int kind);   // an event from the kind's pool (grows on demand)
+  double drain_ms();            // waits, sums the pairs, resets; returns the gate time
   ~Timer();
 };
 

@@ -1047,13 +1047,18 @@ int launch_gates_tc(const KArgs& a, cudaStream_t st) {
     ca.n = (a.n - c0) < chunk ? (a.n - c0) : chunk;
     KArgs ea = ca;
     ea.n = a.bx_shared ? 1 : ca.n;
+    Timer* tm = static_cast<Timer*>(a.timer);
+    if (tm) cudaEventRecord(tm->next(kTimeExpand), st);
     k_expand_b<<<expand_grid(a, ea.n * t.kblocks), kExpandThreads, expand_smem_bytes(a), st>>>(ea, t);
+    if (tm) cudaEventRecord(tm->next(kTimeExpand), st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "B expansion launch");
     // persistent: one CTA per SM (or per item, if fewer)
     const uint64_t items = ca.n * t.mtiles;
     const uint64_t blocks = std::min<uint64_t>(items, (uint64_t)sm_count());
+    if (tm) cudaEventRecord(tm->next(kTimeGate), st);
     k_gate_tc<<<(unsigned)blocks, kThreads, t.smem_bytes, st>>>(ca, t);
+    if (tm) cudaEventRecord(tm->next(kTimeGate), st);
     count_launches(2);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "tc gate kernel launch");

@@ -54,7 +54,7 @@ SIGNATURES = {
     "sfft_eval_fft_noalloc": (c_i32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "sfft_noalloc_scratch_bytes": (c_u64, []),
     "sfft_plan_set_timing": (c_i32, [c_void_p, ctypes.c_int]),
-    "sfft_plan_timing": (c_i32, [c_void_p, c_double_p, P(c_u64), P(c_u64)]),
+    "sfft_plan_timing": (c_i32, [c_void_p, c_double_p, c_double_p, P(c_u64), P(c_u64)]),
     "sfft_circuit_info": (c_i32, [P(sfft_params), c_u32, c_u32, c_u32, c_u32, c_u32,
                                   P(sfft_plan_info)]),
     "sfft_program_eval_plain": (c_i32, [P(sfft_params), c_u32, c_u32, c_u32, c_u32, c_u32, c_u8_p,
@@ -89,7 +89,7 @@ SIGNATURES = {
     "sfft_batch_eval_host": (c_i32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                     c_u64, c_void_p]),
     "sfft_batch_set_timing": (c_i32, [c_void_p, ctypes.c_int]),
-    "sfft_batch_timing": (c_i32, [c_void_p, c_double_p, P(c_u64), P(c_u64)]),
+    "sfft_batch_timing": (c_i32, [c_void_p, c_double_p, c_double_p, P(c_u64), P(c_u64)]),
     "sfft_batch_free": (None, [c_void_p]),
 }
 

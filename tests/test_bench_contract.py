@@ -1,0 +1,32 @@
+"""The JSON line of bench.py's reference arm (the CPU oracle timed on a bounded
+sample) carries every key of the measurement contract; CPU only."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.mark.parametrize("config,metric", [("fft8_8bit_toy", "encrypted FFTs/s"),
+                                           ("refresh32_noisy", "refreshed ciphertexts/s")])
+def test_reference_line_keys(config, metric):
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--config", config,
+                        "--steps", "1", "--warmup", "0", "--cpu-seconds", "1"],
+                       cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config", "impl",
+              "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["metric"] == metric and d["value"] > 0
+    assert d["config"]["workload"] == config and d["higher_is_better"] is True
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
+    e = d["e2e"]
+    assert e["value"] == d["value"] and e["h2d_bytes_per_step"] == e["d2h_bytes_per_step"] == 0

@@ -361,16 +361,16 @@ struct TcShape {
   uint32_t ndpad;            // digit columns of a row (elements x dpad)
   uint32_t mtiles, kblocks, nstages;
   uint32_t n0_len, n1_len;   // MMA N of the two column chunks (n1_len 0 if one chunk)
-  uint32_t btile;            // bytes of one expanded B step (two atoms of ndpad x 128)
+  uint32_t btile;            // bytes of one expanded B step (kAtoms atoms of ndpad x 128)
   uint32_t G;                // digit groups of 32 per element (epilogue units)
   uint32_t nacc;             // accumulator slots in tensor memory
   uint32_t smem_bytes;
 };
 
 // ---------------------------------------------------------------------------
-// B operand expansion: grid = jobs x kblocks, one swizzled slice image each.
-// Job j expands the B operand of gate j (job 0 for every gate when
-// a.bx_shared). Output slice (j, kb) lives at a.bx + (j kblocks + kb) btile.
+// B operand expansion: a job is one (gate, K step) pair and writes one
+// swizzled step image. Gate j's B operand (gate 0's for every gate when
+// a.bx_shared) expands into the images at a.bx + (j kblocks + kb) btile.
 // ---------------------------------------------------------------------------
 // Persistent: CTA b takes the jobs (gate, K step) b, b + grid, ...; the next
 // job's source rows stream into the second buffer (16-byte async copies)
@@ -482,7 +482,7 @@ __global__ void __launch_bounds__(kExpandThreads) k_expand_b(KArgs a, TcShape t)
 // the CTA in slot j % nacc), then kAStages expanded A steps of 64 columns
 // (128 fp16 K values per lane = row).
 //
-// The CTA's steps are its items in order, kblocks 128-wide K steps each;
+// The CTA's steps are its items in order, kblocks K steps of kBK each;
 // step st uses B slot st % nstages and A stage st % kAStages. Barriers:
 //   full[slot]    the slice's B bytes landed (transaction count of the
 //                 producer's arrival) and the four expander warps arrived

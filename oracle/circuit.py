@@ -101,7 +101,8 @@ class Circuit:
 
     # -- gates with constant folding (Lemma 4) -----------------------------
     def _nand(self, a, b):
-        """A GSW NAND gate on two non-constant wires (NAND-only variant)."""
+        """A GSW NAND gate on two non-constant wires (NAND-only variant; the
+        scheme's own gate, Sec. 3, from which Lemma 4 builds the others)."""
         return self._emit("NAND", a, b, 1 + max(self.d(a), self.d(b)))
 
     def NOT(self, a):
@@ -161,7 +162,8 @@ class Circuit:
 
     def SEL(self, a, beta):
         """beta * a for a public bit beta: a linear gate that is never folded
-        (its structure must not depend on beta; refresh circuits)."""
+        (its structure must not depend on beta; refresh circuits, the
+        refreshing Sec. 5 points at)."""
         return self._emit("SEL1" if beta else "SEL0", a, None, self.d(a))
 
     # -- adders (Lemmas 5-7) ---------------------------------------------
@@ -206,7 +208,10 @@ class Circuit:
         return self._wallace(cols)[f:f + F]
 
     def MULE(self, x, y, f):
-        """Fixed-point product of two encrypted words (AND partial products)."""
+        """Fixed-point product of two encrypted words (AND partial products):
+        Lemma 8's sign-extended Wallace product with every row present,
+        Lemma 9's middle bits (the encrypted-operand case Sec. 4 mentions
+        beside constant multiplication)."""
         F = len(x)
         T = f + F
         x_ext = [x[min(j, F - 1)] for j in range(T)]
@@ -218,7 +223,8 @@ class Circuit:
         return self._wallace(cols)[f:f + F]
 
     def _wallace(self, cols):
-        """Wallace stages on column lists, then ADD_T of the two rows (T bits)."""
+        """Wallace stages on column lists, then ADD_T of the two rows (T bits);
+        Lemma 8 with the stage rule stated in this module's docstring."""
         T = len(cols)
         while max(len(col) for col in cols) > 2:
             sums = [[] for _ in range(T)]

@@ -42,7 +42,8 @@ from .circuit import Circuit
 
 
 def shape(p):
-    """(rows, pbits, tau) of the refresh sum for parameters p."""
+    """(rows, pbits, tau) of the refresh sum for parameters p (the truncation
+    stated in this module's docstring)."""
     rows = p.n * p.ell + 1
     pbits = math.ceil(math.log2(rows)) + 3
     if pbits > p.ell:
@@ -51,7 +52,8 @@ def shape(p):
 
 
 def key_bits(keys):
-    """sigma_r in row order: 1, then bit b of s_j (j = 1..n, b = 0..ell-1)."""
+    """sigma_r in row order: 1, then bit b of s_j (j = 1..n, b = 0..ell-1);
+    s = (1, -t) is GSW'13's secret vector (Sec. 3)."""
     p = keys.p
     out = [1]
     for j in range(1, p.n + 1):
@@ -60,7 +62,8 @@ def key_bits(keys):
 
 
 def bootstrap_key(keys, enc_seed):
-    """GSW encryptions of every sigma_r (ciphertext index r under enc_seed)."""
+    """GSW encryptions (Sec. 3) of every sigma_r (ciphertext index r under
+    enc_seed): the bootstrapping key."""
     return [gsw.encrypt(keys, bit, enc_seed, r) for r, bit in enumerate(key_bits(keys))]
 
 
@@ -99,7 +102,8 @@ def refresh_circuit(p, rows_list, xcarry=False, nand=False):
 
 
 def public_row(ct, p):
-    """Row ell - 1 of a compressed ciphertext as n + 1 Python ints."""
+    """Row ell - 1 of a compressed ciphertext as n + 1 Python ints: the row
+    that decryption reads (Sec. 3)."""
     return [int(v) for v in gsw.from_limbs(ct[p.ell - 1])]
 
 

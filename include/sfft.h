@@ -209,7 +209,8 @@ void sfft_plan_free(sfft_plan* plan);
  * beta C): the gate program is fixed, and each run patches the selected
  * gates' coefficients from the source ciphertexts on the device.
  * sfft_refresh_plan_create: inputs n ell + 1 (the bootstrapping key, i.e.
- * encryptions of sfft_key_bits), outputs count; EPARAM if the output's static
+ * encryptions of sfft_key_bits), outputs count (EINVAL when count (n ell + 1)
+ * p exceeds 2^28 / 7, the circuit's size bound); EPARAM if the output's static
  * noise bound reaches q/8 (it could not be refreshed again) unless
  * SFFT_PLAN_ALLOW_NOISY. flags: SFFT_PLAN_INT_KERNEL and the gate variants. */
 int sfft_refresh_plan_create(const sfft_params* p, uint64_t count, uint32_t flags,
@@ -234,7 +235,8 @@ int sfft_refresh(sfft_plan* plan, const uint32_t* d_bk, const uint32_t* d_src, u
  * (partial products AND(x_ext[c - i], y_ext[i]) over T = f + F sign-extended
  * bits, Lemma 8's Wallace stages, Lemma 9's middle bits [f, f + F)). flags:
  * as sfft_plan_create (SFFT_PLAN_ENC_TWIDDLE has no effect). EINVAL unless
- * 1 <= count <= 2^24, 2 <= F <= 48, f < F. */
+ * count >= 1 with count (f + F)^2 <= 2^28 (the circuit's size), 2 <= F <= 48,
+ * f < F. */
 #define SFFT_WORD_ADD 1u
 #define SFFT_WORD_SUB 2u
 #define SFFT_WORD_MUL 3u

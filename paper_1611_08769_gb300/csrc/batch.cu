@@ -291,7 +291,11 @@ int sfft_batch_eval_host_pipelined(sfft_batch* b, const uint32_t* const* h_in,
   const uint64_t in_b = b->merged.n_inputs * b->s.ctw * 4, out_b = b->merged.n_outputs * b->s.ctw * 4;
   for (uint32_t i = 0; i < count; i++) {
     const uint32_t k = i & 1u;
-    if (!h_in[i] || !h_out[i] || !d_in[k] || !d_out[k]) return fail(SFFT_EINVAL, "null buffer");
+    if (!h_in[i] || !h_out[i] || !d_in[k] || !d_out[k]) {
+      cudaStreamSynchronize(b->h2d);
+      cudaStreamSynchronize(b->d2h);
+      return fail(SFFT_EINVAL, "null buffer");
+    }
     // inputs of step i into set k once step i - 2 has read it
     if (i >= 2 && (e = cudaStreamWaitEvent(b->h2d, b->ev_done[k], 0)) != cudaSuccess) break;
     if ((e = cudaMemcpyAsync(d_in[k], h_in[i], in_b, cudaMemcpyHostToDevice, b->h2d)) != cudaSuccess)
@@ -301,7 +305,11 @@ int sfft_batch_eval_host_pipelined(sfft_batch* b, const uint32_t* const* h_in,
     if ((e = cudaStreamWaitEvent(st, b->ev_in[k], 0)) != cudaSuccess) break;
     if (i >= 2 && (e = cudaStreamWaitEvent(st, b->ev_out[k], 0)) != cudaSuccess) break;
     int rc = sfft_batch_eval(b, d_in[k], d_out[k], d_scratch, scratch_bytes, stream);
-    if (rc) return rc;
+    if (rc) {   // leave no copy of this call in flight
+      cudaStreamSynchronize(b->h2d);
+      cudaStreamSynchronize(b->d2h);
+      return rc;
+    }
     if ((e = cudaEventRecord(b->ev_done[k], st)) != cudaSuccess) break;
     // outputs back while the next step runs
     if ((e = cudaStreamWaitEvent(b->d2h, b->ev_done[k], 0)) != cudaSuccess) break;

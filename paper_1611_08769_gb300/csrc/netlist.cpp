@@ -434,7 +434,10 @@ bool build_fft(Circuit* c, uint32_t N1, uint32_t N2, uint32_t F, uint32_t f) {
 }
 
 bool build_words(Circuit* c, uint32_t op, uint64_t count, uint32_t F, uint32_t f) {
-  if (count == 0 || count > (1ull << 24) || F < 2 || F > 48 || f >= F) return false;
+  // a word's circuit has O((f + F)^2) nodes: keep the whole circuit (host
+  // memory, 31-bit node ids) within 2^28 nodes of that order
+  if (count == 0 || F < 2 || F > 48 || f >= F) return false;
+  if (count * (uint64_t)(f + F) * (f + F) > (1ull << 28)) return false;
   if (op != SFFT_WORD_ADD && op != SFFT_WORD_SUB && op != SFFT_WORD_MUL) return false;
   for (uint64_t k = 0; k < count; k++) {
     Word x(F), y(F);
@@ -453,7 +456,8 @@ bool build_refresh(Circuit* c, uint32_t n, uint32_t ell, uint64_t count) {
   uint32_t pb = 0;
   while ((1ull << pb) < rows) pb++;
   pb += 3;
-  if (n == 0 || count == 0 || count > (1u << 20) || pb > ell) return false;
+  // one refresh has ~7 (n ell + 1) p nodes: keep the circuit within 2^28
+  if (n == 0 || count == 0 || pb > ell || count * rows * pb * 7 > (1ull << 28)) return false;
   const uint32_t tau = ell - pb;
   std::vector<uint32_t> bk(rows);
   for (uint64_t r = 0; r < rows; r++) bk[r] = c->new_input();
@@ -478,7 +482,8 @@ int build_circuit(Circuit* c, const CircuitSpec& spec, uint32_t flags) {
     return fail(SFFT_EINVAL, "SFFT_PLAN_XCARRY and SFFT_PLAN_NAND are exclusive");
   if (spec.op == kOpRefresh) {
     if (!build_refresh(c, spec.n, spec.ell, spec.count))
-      return fail(SFFT_EINVAL, "refresh needs n >= 1, 1 <= count <= 2^20 and ell >= "
+      return fail(SFFT_EINVAL, "refresh needs n >= 1, count >= 1 with count (n ell + 1) "
+                               "(log2(n ell + 1) + 3) <= 2^28 / 7, and ell >= "
                                "ceil(log2(n ell + 1)) + 3");
     return SFFT_OK;
   }
@@ -490,7 +495,8 @@ int build_circuit(Circuit* c, const CircuitSpec& spec, uint32_t flags) {
     return SFFT_OK;
   }
   if (!build_words(c, spec.op, spec.count, spec.F, spec.f))
-    return fail(SFFT_EINVAL, "word op must be SFFT_WORD_ADD/SUB/MUL, 1 <= count <= 2^24, "
+    return fail(SFFT_EINVAL, "word op must be SFFT_WORD_ADD/SUB/MUL, count >= 1 with "
+                             "count (f + F)^2 <= 2^28, "
                              "2 <= F <= 48, f < F");
   return SFFT_OK;
 }

@@ -204,3 +204,15 @@ def test_native_twiddle_table_and_errors():
         sf.word_circuit_info(sp, sf.WORD_MUL, 0, 8, 4)
     with pytest.raises(sf.SfftError):
         sf.twiddles(6, 4)
+
+
+def test_native_circuit_size_bounds():
+    import paper_1611_08769_gb300 as sf
+    sp = sf.param_set("P0")
+    F, f = 16, 8
+    limit = (1 << 28) // ((f + F) * (f + F))
+    assert sf.word_circuit_info(sp, sf.WORD_ADD, 1, F, f)["outputs"] == F
+    with pytest.raises(sf.SfftError):
+        sf.word_circuit_info(sp, sf.WORD_ADD, limit + 1, F, f)
+    with pytest.raises(sf.SfftError):
+        sf.refresh_circuit_info(sf.param_set("P1", 1056), 1 << 20)

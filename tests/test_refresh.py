@@ -183,3 +183,10 @@ def test_native_refresh_min_ell_matches_oracle():
     import paper_1611_08769_gb300 as sf
     for xcarry in (False, True):
         assert sf.refresh_min_ell(1, 1, xcarry=xcarry) == refresh.min_ell(1, 1, xcarry=xcarry)
+
+
+def test_native_refresh_rejects_both_gate_variants():
+    import paper_1611_08769_gb300 as sf
+    with pytest.raises(sf.SfftError):
+        sf.refresh_circuit_info(sf.Params(1, 64, 128, 1), 1, xcarry=True, nand=True)
+    assert sf.refresh_min_ell(1, 1, xcarry=True, nand=True) == 0

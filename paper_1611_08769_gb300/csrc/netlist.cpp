@@ -516,31 +516,22 @@ struct Big {
     }
     return b;
   }
-  Big mul(uint64_t k) const {  // k < 2^32
+  // a ka + b kb in one pass (ka, kb < 2^32)
+  static Big lin(const Big& a, uint64_t ka, const Big& b, uint64_t kb) {
     Big r;
-    uint64_t carry = 0;
-    for (uint32_t x : d) {
-      uint64_t t = (uint64_t)x * k + carry;
-      r.d.push_back((uint32_t)t);
-      carry = t >> 32;
+    const size_t n = std::max(a.d.size(), b.d.size());
+    r.d.reserve(n + 2);
+    unsigned __int128 carry = 0;
+    for (size_t i = 0; i < n; i++) {
+      carry += (unsigned __int128)(i < a.d.size() ? a.d[i] : 0u) * ka;
+      carry += (unsigned __int128)(i < b.d.size() ? b.d[i] : 0u) * kb;
+      r.d.push_back((uint32_t)carry);
+      carry >>= 32;
     }
     while (carry) {
       r.d.push_back((uint32_t)carry);
       carry >>= 32;
     }
-    r.trim();
-    return r;
-  }
-  Big add(const Big& o) const {
-    Big r;
-    uint64_t carry = 0;
-    size_t n = std::max(d.size(), o.d.size());
-    for (size_t i = 0; i < n; i++) {
-      uint64_t t = carry + (i < d.size() ? d[i] : 0) + (i < o.d.size() ? o.d[i] : 0);
-      r.d.push_back((uint32_t)t);
-      carry = t >> 32;
-    }
-    if (carry) r.d.push_back((uint32_t)carry);
     r.trim();
     return r;
   }
@@ -600,8 +591,8 @@ uint32_t noise_bits(const Circuit& c, const Shape& s) {
     const Big& EB = E[sig_node(g.b)];
     auto apply = [&](uint32_t node, Code k) {
       if (!node || !ln[node]) return;
-      Big e = EA.mul((uint64_t)(std::abs(k.c1) + std::abs(k.c3)))
-                  .add(EB.mul((uint64_t)std::abs(k.c2) + (uint64_t)std::abs(k.c3) * s.Ng));
+      Big e = Big::lin(EA, (uint64_t)(std::abs(k.c1) + std::abs(k.c3)), EB,
+                       (uint64_t)std::abs(k.c2) + (uint64_t)std::abs(k.c3) * s.Ng);
       best = std::max(best, e.bits());
       E[node] = e;
     };

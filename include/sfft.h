@@ -429,6 +429,17 @@ int sfft_gate_level(const sfft_params* p, const uint32_t* d_a, const uint32_t* d
                     const uint16_t* h_code1, const uint8_t* h_flags, uint64_t n_gates,
                     uint32_t kernel, void* stream);
 
+/* Failure-detection test hook: the same level of gates on the tensor-core
+ * kernel (EPARAM where it does not apply), except that every CTA's producer
+ * withholds the B copy of K step `step`. That step's barrier never
+ * completes, the kernel's bounded waits run out (about 2 s), every role
+ * stops, the kernel drains its own MMAs, frees its tensor memory and
+ * returns; the call then returns SFFT_ETIMEOUT and the context stays usable.
+ * d_out0 is left undefined. */
+int sfft_gate_level_withheld(const sfft_params* p, const uint32_t* d_a, const uint32_t* d_b,
+                             uint32_t* d_out0, const uint16_t* h_code0, const uint8_t* h_flags,
+                             uint64_t n_gates, uint32_t step, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -455,5 +455,16 @@ def gate_level(params, d_a, d_b, d_out0, d_out1, code0, code1, flags, stream=Non
                                 _stream(stream)))
 
 
+def gate_level_withheld(params, d_a, d_b, d_out0, code0, flags, step, stream=None):
+    """Failure-detection test hook (sfft_gate_level_withheld): raises SfftError
+    with code SFFT_ETIMEOUT once the kernel's bounded waits have run out."""
+    code0 = np.ascontiguousarray(code0, dtype=np.uint16)
+    flags = np.ascontiguousarray(flags, dtype=np.uint8)
+    check(lib().sfft_gate_level_withheld(ctypes.byref(params), _dptr(d_a), _dptr(d_b),
+                                         _dptr(d_out0), code0.ctypes.data_as(native.c_u16_p),
+                                         flags.ctypes.data_as(native.c_u8_p), len(code0), step,
+                                         _stream(stream)))
+
+
 def pack_code(c0, c1, c2, c3):
     return (c0 & 15) | ((c1 & 15) << 4) | ((c2 & 15) << 8) | ((c3 & 15) << 12)

@@ -208,6 +208,16 @@ using namespace sfft;
 
 namespace {
 
+// One level of independent gates (test hooks): operand A in d_a, B in d_b.
+int gate_level(const sfft_params* p, const uint32_t* d_a, const uint32_t* d_b, uint32_t* d_out0,
+               uint32_t* d_out1, const uint16_t* h_code0, const uint16_t* h_code1,
+               const uint8_t* h_flags, uint64_t n_gates, uint32_t kernel, uint32_t withhold,
+               void* stream);
+
+}  // namespace
+
+namespace {
+
 uint32_t min_ell_of(const CircuitSpec& spec, uint32_t n, uint32_t chi, uint32_t flags) {
   Circuit c;
   if (build_circuit(&c, spec, flags)) return 0;
@@ -430,6 +440,29 @@ int sfft_gate_level(const sfft_params* p, const uint32_t* d_a, const uint32_t* d
                     uint32_t* d_out0, uint32_t* d_out1, const uint16_t* h_code0,
                     const uint16_t* h_code1, const uint8_t* h_flags, uint64_t n_gates,
                     uint32_t kernel, void* stream) {
+  return gate_level(p, d_a, d_b, d_out0, d_out1, h_code0, h_code1, h_flags, n_gates, kernel, 0,
+                    stream);
+}
+
+int sfft_gate_level_withheld(const sfft_params* p, const uint32_t* d_a, const uint32_t* d_b,
+                             uint32_t* d_out0, const uint16_t* h_code0, const uint8_t* h_flags,
+                             uint64_t n_gates, uint32_t step, void* stream) {
+  Shape s;
+  KArgs probe{};
+  if (make_shape(p, &s, false) == SFFT_OK) probe = make_args(s);
+  if (!tc_supported(probe)) return fail(SFFT_EPARAM, "the tensor-core kernel does not take these parameters");
+  return gate_level(p, d_a, d_b, d_out0, nullptr, h_code0, nullptr, h_flags, n_gates, KERNEL_TC,
+                    step + 1, stream);
+}
+
+}  // extern "C"
+
+namespace {
+
+int gate_level(const sfft_params* p, const uint32_t* d_a, const uint32_t* d_b, uint32_t* d_out0,
+               uint32_t* d_out1, const uint16_t* h_code0, const uint16_t* h_code1,
+               const uint8_t* h_flags, uint64_t n_gates, uint32_t kernel, uint32_t withhold,
+               void* stream) {
   Shape s;
   int rc = make_shape(p, &s, false);
   if (rc) return rc;
@@ -460,6 +493,7 @@ int sfft_gate_level(const sfft_params* p, const uint32_t* d_a, const uint32_t* d
   a.base[REG_OUT] = d_out0;
   a.base[REG_GEN] = d_out1;  // region 3 is only an output here, never operand A
   a.kernel = kernel;
+  a.withhold = withhold;
   cudaMalloc((void**)&a.err, sizeof(int));
   if (a.err) cudaMemset(a.err, 0, sizeof(int));
   if (kernel != KERNEL_INT && tc_supported(a)) {
@@ -481,6 +515,10 @@ int sfft_gate_level(const sfft_params* p, const uint32_t* d_a, const uint32_t* d
   if (rc) return rc;
   return e == cudaSuccess ? SFFT_OK : cuda_fail(e, "gate level");
 }
+
+}  // namespace
+
+extern "C" {
 
 int sfft_encrypt_bits_device(const sfft_params* p, const uint32_t* d_pub, const double* h_re,
                              const double* h_im, uint64_t count, uint32_t F, uint32_t f,

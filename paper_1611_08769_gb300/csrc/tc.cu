@@ -674,8 +674,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_gate_tc(KArgs a, TcShape t) {
         }
         uint32_t kbr = p.kb + it.rot;
         if (kbr >= t.kblocks) kbr -= t.kblocks;
-        mbar_expect_tx(&full[p.slot], t.btile);
-        bulk_g2s(ring + p.slot * t.btile, bx + (uint64_t)kbr * t.btile, t.btile, &full[p.slot]);
+        if (a.withhold == 0 || st + 1 != a.withhold) {   // (a withheld step's slot never fills)
+          mbar_expect_tx(&full[p.slot], t.btile);
+          bulk_g2s(ring + p.slot * t.btile, bx + (uint64_t)kbr * t.btile, t.btile, &full[p.slot]);
+        }
         const uint32_t oj = p.j;
         p.next();
         if (p.j != oj && p.j < nloc) {

@@ -493,7 +493,6 @@ int gate_level(const sfft_params* p, const uint32_t* d_a, const uint32_t* d_b, u
   a.base[REG_OUT] = d_out0;
   a.base[REG_GEN] = d_out1;  // region 3 is only an output here, never operand A
   a.kernel = kernel;
-  a.withhold = withhold;
   cudaMalloc((void**)&a.err, sizeof(int));
   if (a.err) cudaMemset(a.err, 0, sizeof(int));
   if (kernel != KERNEL_INT && tc_supported(a)) {
@@ -505,7 +504,7 @@ int gate_level(const sfft_params* p, const uint32_t* d_a, const uint32_t* d_b, u
       return cuda_fail(me, "cudaMalloc");
     }
   }
-  rc = launch_gates(a, st);
+  rc = withhold ? launch_gates_tc_withheld(a, withhold - 1, st) : launch_gates(a, st);
   cudaError_t e = cudaStreamSynchronize(st);
   if (!rc && e == cudaSuccess) rc = check_device_error(a.err, st);
   cudaFree(dd);

@@ -20,8 +20,6 @@ struct KArgs {
   uint8_t* bx;           // tensor-core kernel: expanded B operands (scratch)
   uint32_t bx_shared;    // 1: every gate has the same B operand (expanded once)
   void* timer;           // host: the Timer recording this launch's kernels, or null
-  uint32_t withhold;     // test hook: 1 + the K step whose B copy every CTA's producer
-                         // withholds (its bounded waits then run out); 0: none
 };
 
 constexpr uint32_t KERNEL_AUTO = 0, KERNEL_INT = 1, KERNEL_TC = 2;

@@ -46,6 +46,8 @@ void count_launches(uint64_t n);
 // Tensor-core gate kernel (tc.cu): shapes it supports, and its launcher.
 bool tc_supported(const KArgs& a);
 int launch_gates_tc(const KArgs& a, cudaStream_t st);
+// Failure-detection test: the same launch with K step `step`'s B copy withheld.
+int launch_gates_tc_withheld(const KArgs& a, uint32_t step, cudaStream_t st);
 // Bytes of the expanded B operand of one gate (0 if the shape is unsupported),
 // and of the expansion buffer a launch of `gates` gates needs (levels run in
 // L2-sized chunks of gates that share one buffer).

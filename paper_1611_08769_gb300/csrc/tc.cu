@@ -552,6 +552,12 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// Failure-detection test: 1 + the K step whose B copy every CTA's producer
+// withholds in the kWithhold instance of k_gate_tc (its bounded waits then
+// run out). The production instance neither reads it nor carries the branch.
+__device__ uint32_t g_withhold;
+
+template <bool kWithhold>
 __global__ void __launch_bounds__(kThreads, 1) k_gate_tc(KArgs a, TcShape t) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -674,7 +680,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gate_tc(KArgs a, TcShape t) {
         }
         uint32_t kbr = p.kb + it.rot;
         if (kbr >= t.kblocks) kbr -= t.kblocks;
-        if (a.withhold == 0 || st + 1 != a.withhold) {   // (a withheld step's slot never fills)
+        if (!kWithhold || st + 1 != g_withhold) {   // (a withheld step's slot never fills)
           mbar_expect_tx(&full[p.slot], t.btile);
           bulk_g2s(ring + p.slot * t.btile, bx + (uint64_t)kbr * t.btile, t.btile, &full[p.slot]);
         }
@@ -1027,15 +1033,33 @@ uint32_t expand_grid(const KArgs& a, uint64_t jobs) {
   return (uint32_t)(jobs < g ? jobs : g);
 }
 
-int launch_gates_tc(const KArgs& a, cudaStream_t st) {
+namespace {
+int launch_tc(const KArgs& a, cudaStream_t st, bool withhold);
+}  // namespace
+
+int launch_gates_tc(const KArgs& a, cudaStream_t st) { return launch_tc(a, st, false); }
+
+int launch_gates_tc_withheld(const KArgs& a, uint32_t step, cudaStream_t st) {
+  const uint32_t v = step + 1;
+  cudaError_t e = cudaMemcpyToSymbol(g_withhold, &v, sizeof(v));
+  if (e != cudaSuccess) return cuda_fail(e, "withheld step");
+  return launch_tc(a, st, true);
+}
+
+namespace {
+
+int launch_tc(const KArgs& a, cudaStream_t st, bool withhold) {
   if (a.n == 0) return SFFT_OK;
   TcShape t{};
   if (!make_tc_shape(a, &t)) return fail(SFFT_EPARAM, "tensor-core kernel does not support this shape");
   if (!a.bx) return fail(SFFT_EINVAL, "tensor-core kernel needs its B expansion buffer");
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_gate_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_gate_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kMaxSmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_gate_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kMaxSmem);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_expand_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
     if (e != cudaSuccess) return cuda_fail(e, "tc smem attribute");
@@ -1059,7 +1083,10 @@ int launch_gates_tc(const KArgs& a, cudaStream_t st) {
     const uint64_t items = ca.n * t.mtiles;
     const uint64_t blocks = std::min<uint64_t>(items, (uint64_t)sm_count());
     if (tm) cudaEventRecord(tm->next(kTimeGate), st);
-    k_gate_tc<<<(unsigned)blocks, kThreads, t.smem_bytes, st>>>(ca, t);
+    if (withhold)
+      k_gate_tc<true><<<(unsigned)blocks, kThreads, t.smem_bytes, st>>>(ca, t);
+    else
+      k_gate_tc<false><<<(unsigned)blocks, kThreads, t.smem_bytes, st>>>(ca, t);
     if (tm) cudaEventRecord(tm->next(kTimeGate), st);
     count_launches(2);
     e = cudaGetLastError();
@@ -1067,5 +1094,7 @@ int launch_gates_tc(const KArgs& a, cudaStream_t st) {
   }
   return SFFT_OK;
 }
+
+}  // namespace
 
 }  // namespace sfft

@@ -9,7 +9,7 @@ radix-2 butterflies after a plaintext bit reversal (Sec. 4, Lemma 3).
 
 Each 2-input gate is one arithmetised GSW gate (codes in ``gsw.GATE_CODES``):
 AND, XOR, OR each cost one ciphertext product, NOT is linear. The canonical
-choices the paper leaves open (all readings, stated in the design doc):
+choices the paper leaves open (each a reading of the paper):
 
 * Operand order. The product BitDecomp(A') B' is not symmetric in its
   ciphertext bits. A is the operand of strictly larger multiplicative depth,

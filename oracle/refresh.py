@@ -3,7 +3,7 @@
 The paper evaluates a leveled circuit and, at the end of its noise analysis
 (Sec. 5), points at refreshing ciphertexts so that evaluation could go on
 indefinitely, without giving a construction. This module states the
-construction used here (a reading; the design doc lists it).
+construction used here, a reading of that remark.
 
 Decryption of a compressed ciphertext reads row ell - 1, c = (c_0, ..., c_n),
 and its phase x = <c, s> mod q with s = (1, -t). Let sigma_0 = 1 and, for

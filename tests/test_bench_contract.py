@@ -30,3 +30,21 @@ def test_reference_line_keys(config, metric):
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
     e = d["e2e"]
     assert e["value"] == d["value"] and e["h2d_bytes_per_step"] == e["d2h_bytes_per_step"] == 0
+
+
+def test_roofline_arithmetic():
+    """The roofline's per-product figures: the contraction's flops and the B
+    expansion's algorithmic bytes at ell 1056 (Ng 2112, 192 digit columns)."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class P:
+        n, ell = 1, 1056
+    assert bench.expand_bytes_per_product(P) == 2112 * 2112 // 8 + 17 * 192 * 256
+    r = bench.roofline(P, 2, gate_ms=1000.0, launches=1, gates_timed=1000, tc_columns=192,
+                       expand_ms=500.0)
+    flops = 2.0 * 2112 * 2112 * 192
+    assert r["flops_per_product"] == flops
+    assert abs(r["achieved"] - flops * 1000 / 1.0 / 1e12) < 1e-9
+    assert abs(r["expand"]["achieved"] - (2112 * 2112 // 8 + 17 * 192 * 256) * 1000 / 0.5 / 1e9) < 1e-6
+    assert r["bound"] == "tensor" and r["expand"]["bound"] == "hbm"

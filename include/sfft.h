@@ -151,9 +151,11 @@ typedef struct sfft_plan_info {
   uint64_t ct_words;
   uint32_t noise_bits;          /* bit length of the largest wire noise bound */
   uint32_t noise_ok;            /* bound < q/4 */
-  uint32_t gate_kernel;         /* 1 integer-ALU kernel, 2 tensor-core kernel */
-  uint32_t tc_columns;          /* tensor-core kernel: digit columns of a product row
-                                   ((n+1) ceil(ell / dw), dw = 11 bits); 0 otherwise */
+  uint32_t gate_kernel;         /* 1 integer-ALU kernel, 2 general tensor-core kernel,
+                                   3 small-ciphertext tensor-core kernel (Ng <= 256) */
+  uint32_t tc_columns;          /* tensor-core kernels: digit columns of a product row,
+                                   (n+1) ceil(ell / dw) with dw = 11 bits (kernel 2) or
+                                   8 bits (kernel 3); 0 otherwise */
   uint64_t gates_xadd;          /* linear exclusive-carry sums (SFFT_PLAN_XCARRY), no product */
 } sfft_plan_info;
 
@@ -165,6 +167,10 @@ typedef struct sfft_plan_info {
  * if the static noise bound reaches q/4. flags: SFFT_PLAN_* below. */
 #define SFFT_PLAN_ALLOW_NOISY 1u   /* build even if the noise bound fails */
 #define SFFT_PLAN_INT_KERNEL 2u    /* integer-ALU gate kernel even where tensor cores apply */
+/* The general tensor-core kernel (B operands expanded by a separate pass)
+ * even where the small-ciphertext kernel applies (Ng <= 256); for
+ * comparisons. EPARAM where the general kernel does not apply. */
+#define SFFT_PLAN_TC_KERNEL 64u
 /* Circuit variant (not the paper's): the full adder's carry is the sum of its
  * two half-adder carries, which are never both 1 (Lemma 6's OR, exact on
  * every input it meets), a linear gate (0, 1, 1, 0) with no ciphertext

@@ -21,8 +21,9 @@ PLAN_INT_KERNEL = 2
 PLAN_XCARRY = 8   # circuit variant: exclusive-carry full adders (sfft.h SFFT_PLAN_XCARRY)
 PLAN_NAND = 16    # circuit variant: every gate built of NAND gates (sfft.h SFFT_PLAN_NAND)
 PLAN_ENC_TWIDDLE = 32   # FFT twiddles as encrypted inputs (sfft.h SFFT_PLAN_ENC_TWIDDLE)
+PLAN_TC_KERNEL = 64     # the general tensor-core kernel where the small one applies
 WORD_ADD, WORD_SUB, WORD_MUL = 1, 2, 3   # word circuits (sfft.h SFFT_WORD_*)
-KERNEL_AUTO, KERNEL_INT, KERNEL_TC = 0, 1, 2
+KERNEL_AUTO, KERNEL_INT, KERNEL_TC, KERNEL_SM = 0, 1, 2, 3
 
 __all__ = ["Params", "Keys", "Plan", "keygen", "encrypt_bits", "encrypt_bits_device", "decrypt",
            "gather_dec_rows", "min_ell", "gate_level", "ct_words", "SfftError", "version",

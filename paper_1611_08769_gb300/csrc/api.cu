@@ -50,11 +50,41 @@ uint64_t scratch_layout(const Shape& s, uint64_t slots, uint64_t max_width, bool
   return *bx_off + tc_bx_bytes(make_args(s), max_width);
 }
 
-// Launches one level of gates (tensor-core kernel where it applies).
+uint32_t gate_kernel_for(const KArgs& a) {
+  switch (a.kernel) {
+    case KERNEL_INT:
+      return KERNEL_INT;
+    case KERNEL_TC:
+      return tc_supported(a) ? KERNEL_TC : 0;
+    case KERNEL_SM:
+      return !a.bx_shared && !a.gen_state && sm_supported(a) ? KERNEL_SM : 0;
+    default:
+      // the small-ciphertext kernel where it applies (it loads both operands
+      // of each gate; encryption, whose A operands are generated and whose
+      // gates share one expanded B, runs the general one)
+      if (!a.bx_shared && !a.gen_state && sm_supported(a)) return KERNEL_SM;
+      return tc_supported(a) ? KERNEL_TC : KERNEL_INT;
+  }
+}
+
+uint32_t plan_kernel(uint32_t flags) {
+  if (flags & SFFT_PLAN_INT_KERNEL) return KERNEL_INT;
+  if (flags & SFFT_PLAN_TC_KERNEL) return KERNEL_TC;
+  return KERNEL_AUTO;
+}
+
+uint32_t gate_digit_columns(const KArgs& a) {
+  const uint32_t k = gate_kernel_for(a);
+  return k == KERNEL_SM ? sm_digit_columns(a) : k == KERNEL_TC ? tc_digit_columns(a) : 0;
+}
+
+// Launches one level of gates on the kernel gate_kernel_for picks.
 int launch_gates(const KArgs& a, cudaStream_t st) {
   if (a.n == 0) return SFFT_OK;
-  if (a.kernel != KERNEL_INT && tc_supported(a)) return launch_gates_tc(a, st);
-  if (a.kernel == KERNEL_TC) return fail(SFFT_EPARAM, "tensor-core kernel does not support this shape");
+  const uint32_t k = gate_kernel_for(a);
+  if (k == KERNEL_SM) return launch_gates_sm(a, st);
+  if (k == KERNEL_TC) return launch_gates_tc(a, st);
+  if (k == 0) return fail(SFFT_EPARAM, "the requested gate kernel does not support this shape");
   const uint64_t tasks = a.n * (a.Ng / 32);
   const uint64_t blocks = (tasks * 32 + 255) / 256;
   Timer* tm = static_cast<Timer*>(a.timer);
@@ -251,9 +281,14 @@ int plan_create(const sfft_params* p, const CircuitSpec& spec, uint32_t flags, s
     return rc;
   }
   pl->spec = spec;
-  pl->dev.kernel = (flags & SFFT_PLAN_INT_KERNEL) ? KERNEL_INT : KERNEL_AUTO;
+  pl->dev.kernel = plan_kernel(flags);
   pl->dev.max_width = pl->prog.max_width;
-  pl->dev.tc = pl->dev.kernel != KERNEL_INT && tc_supported(make_args(pl->s));
+  {
+    KArgs k = make_args(pl->s);
+    k.kernel = pl->dev.kernel;
+    if (!gate_kernel_for(k)) return fail(SFFT_EPARAM, "the requested gate kernel does not support these parameters");
+    pl->dev.tc = gate_kernel_for(k) == KERNEL_TC;   // needs the B expansion region
+  }
   pl->dev.scratch_bytes = scratch_layout(pl->s, pl->prog.scratch_slots, pl->prog.max_width,
                                          pl->dev.tc, &pl->dev.bx_off);
   *out = pl.release();
@@ -326,9 +361,10 @@ int sfft_plan_info_get(const sfft_plan* pl, sfft_plan_info* info) {
   info->ct_words = pl->s.ctw;
   info->noise_bits = pl->prog.noise_bits;
   info->noise_ok = pl->prog.noise_ok ? 1 : 0;
-  info->gate_kernel =
-      (pl->dev.kernel != KERNEL_INT && tc_supported(make_args(pl->s))) ? KERNEL_TC : KERNEL_INT;
-  info->tc_columns = info->gate_kernel == KERNEL_TC ? tc_digit_columns(make_args(pl->s)) : 0;
+  KArgs k = make_args(pl->s);
+  k.kernel = pl->dev.kernel;
+  info->gate_kernel = gate_kernel_for(k);
+  info->tc_columns = gate_digit_columns(k);
   return SFFT_OK;
 }
 
@@ -495,7 +531,7 @@ int gate_level(const sfft_params* p, const uint32_t* d_a, const uint32_t* d_b, u
   a.kernel = kernel;
   cudaMalloc((void**)&a.err, sizeof(int));
   if (a.err) cudaMemset(a.err, 0, sizeof(int));
-  if (kernel != KERNEL_INT && tc_supported(a)) {
+  if (gate_kernel_for(a) == KERNEL_TC) {
     cudaError_t me = cudaMalloc((void**)&a.bx, tc_bx_bytes(a, n_gates));
     if (me != cudaSuccess) {
       cudaFree(dd);

@@ -208,9 +208,14 @@ int sfft_batch_create(const sfft_params* p, const sfft_request* reqs, uint32_t c
     free_device_program(&b->dev);
     return rc;
   }
-  b->dev.kernel = (flags & SFFT_PLAN_INT_KERNEL) ? KERNEL_INT : KERNEL_AUTO;
+  b->dev.kernel = plan_kernel(flags);
   b->dev.max_width = b->merged.max_width;
-  b->dev.tc = b->dev.kernel != KERNEL_INT && tc_supported(make_args(b->s));
+  {
+    KArgs k = make_args(b->s);
+    k.kernel = b->dev.kernel;
+    if (!gate_kernel_for(k)) return fail(SFFT_EPARAM, "the requested gate kernel does not support these parameters");
+    b->dev.tc = gate_kernel_for(k) == KERNEL_TC;   // needs the B expansion region
+  }
   b->dev.scratch_bytes =
       scratch_layout(b->s, scr, b->merged.max_width, b->dev.tc, &b->dev.bx_off);
   b->use_graph = !(flags & SFFT_BATCH_NO_GRAPH);
@@ -231,8 +236,10 @@ int sfft_batch_info_get(const sfft_batch* b, sfft_plan_info* info) {
   info->ct_words = b->s.ctw;
   info->noise_bits = b->merged.noise_bits;
   info->noise_ok = b->merged.noise_ok ? 1 : 0;
-  info->gate_kernel = b->dev.tc ? KERNEL_TC : KERNEL_INT;
-  info->tc_columns = b->dev.tc ? tc_digit_columns(make_args(b->s)) : 0;
+  KArgs k = make_args(b->s);
+  k.kernel = b->dev.kernel;
+  info->gate_kernel = gate_kernel_for(k);
+  info->tc_columns = gate_digit_columns(k);
   return SFFT_OK;
 }
 

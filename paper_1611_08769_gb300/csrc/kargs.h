@@ -16,13 +16,16 @@ struct KArgs {
   uint32_t Ng, W, L, ell;
   uint64_t ctw;
   int* err;              // device error word (bounded waits that ran out), may be null
-  uint32_t kernel;       // KERNEL_AUTO / KERNEL_INT / KERNEL_TC
+  uint32_t kernel;       // KERNEL_AUTO / KERNEL_INT / KERNEL_TC / KERNEL_SM
   uint8_t* bx;           // tensor-core kernel: expanded B operands (scratch)
   uint32_t bx_shared;    // 1: every gate has the same B operand (expanded once)
   void* timer;           // host: the Timer recording this launch's kernels, or null
 };
 
-constexpr uint32_t KERNEL_AUTO = 0, KERNEL_INT = 1, KERNEL_TC = 2;
+// KERNEL_TC: the general tensor-core kernel (B expanded by a separate pass);
+// KERNEL_SM: the small-ciphertext tensor-core kernel (Ng <= 256, whole gates
+// per CTA, B converted in the kernel).
+constexpr uint32_t KERNEL_AUTO = 0, KERNEL_INT = 1, KERNEL_TC = 2, KERNEL_SM = 3;
 
 // Error codes written to KArgs::err by kernels.
 constexpr int KERR_MMA_TIMEOUT = 1;

@@ -8,9 +8,9 @@
 #include "netlist.h"
 
 namespace sfft {
-bool tc_supported(const KArgs& a);
 uint64_t tc_bx_bytes(const KArgs& a, uint64_t gates);
-uint32_t tc_digit_columns(const KArgs& a);
+uint32_t gate_kernel_for(const KArgs& a);
+uint32_t gate_digit_columns(const KArgs& a);
 }
 
 using namespace sfft;
@@ -100,7 +100,7 @@ int circuit_info(const sfft_params* p, const CircuitSpec& spec, uint32_t flags,
     k.L = s.L;
     k.ell = s.ell;
     uint64_t bx_off = 0;
-    const bool tc = tc_supported(k);
+    const bool tc = gate_kernel_for(k) == KERNEL_TC;   // needs the B expansion region
     const uint64_t wires = prog.scratch_slots * s.ctw * 4;
     bx_off = (wires + 255) & ~255ull;
     info->scratch_bytes = tc ? bx_off + tc_bx_bytes(k, prog.max_width) : wires;
@@ -113,8 +113,8 @@ int circuit_info(const sfft_params* p, const CircuitSpec& spec, uint32_t flags,
   ka.W = s.W;
   ka.L = s.L;
   ka.ell = s.ell;
-  info->gate_kernel = tc_supported(ka) ? KERNEL_TC : KERNEL_INT;
-  info->tc_columns = tc_digit_columns(ka);
+  info->gate_kernel = gate_kernel_for(ka);
+  info->tc_columns = gate_digit_columns(ka);
   return SFFT_OK;
 }
 

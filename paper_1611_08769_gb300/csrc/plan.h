@@ -23,7 +23,7 @@ struct DeviceProgram {
   std::vector<uint64_t> lin_start;   // per level: first linear gate (after its products)
   uint64_t scratch_slots = 0;
   int* err = nullptr;            // device error word of the kernels
-  uint32_t kernel = 0;           // KERNEL_AUTO / KERNEL_INT / KERNEL_TC
+  uint32_t kernel = 0;           // KERNEL_AUTO / KERNEL_INT / KERNEL_TC / KERNEL_SM
   uint64_t max_width = 0;        // products in the widest level
   bool tc = false;               // levels run on the tensor-core kernel
   uint64_t scratch_bytes = 0;    // wire slots + expanded B operands
@@ -45,6 +45,23 @@ int launch_fixups(const FixDesc* d_fix, uint64_t n, const KArgs& a, cudaStream_t
 void count_launches(uint64_t n);
 // Tensor-core gate kernel (tc.cu): shapes it supports, and its launcher.
 bool tc_supported(const KArgs& a);
+// Small-ciphertext tensor-core kernel (tc_small.cu): shapes it supports (Ng
+// <= 256), its digit columns, its launcher (nslots 0: tuned or default ring
+// depth) and the tuned ring depth per limb count on the current device.
+bool sm_supported(const KArgs& a);
+uint32_t sm_digit_columns(const KArgs& a);
+int launch_gates_sm(const KArgs& a, cudaStream_t st);
+int launch_gates_sm_slots(const KArgs& a, uint32_t nslots, cudaStream_t st);
+int sm_set_tuned_slots(uint32_t L, uint32_t nslots);
+// The gate kernel launch_gates runs for these arguments (a.kernel, the shape
+// and a.bx_shared): KERNEL_SM, KERNEL_TC or KERNEL_INT; 0 when the kernel
+// a.kernel forces does not support the shape.
+uint32_t gate_kernel_for(const KArgs& a);
+// Gate kernel a plan or batch requests from its flags (SFFT_PLAN_INT_KERNEL,
+// SFFT_PLAN_TC_KERNEL, else automatic).
+uint32_t plan_kernel(uint32_t flags);
+// Digit columns of the tensor-core kernel that runs (0 for the integer kernel).
+uint32_t gate_digit_columns(const KArgs& a);
 int launch_gates_tc(const KArgs& a, cudaStream_t st);
 // Failure-detection test: the same launch with K step `step`'s B copy withheld.
 int launch_gates_tc_withheld(const KArgs& a, uint32_t step, cudaStream_t st);

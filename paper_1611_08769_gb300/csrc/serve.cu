@@ -381,7 +381,7 @@ int sfft_server_create(const sfft_params* p, uint64_t hbm_budget_bytes, uint32_t
     return fail(SFFT_EINVAL, "SFFT_PLAN_XCARRY and SFFT_PLAN_NAND are exclusive");
   const uint64_t ctb = sv->s.ctw * 4;
   KArgs k = make_args(sv->s);
-  sv->tc = tc_supported(k);
+  sv->tc = gate_kernel_for(k) == KERNEL_TC;   // needs the B expansion region
   const uint64_t bx_bytes = sv->tc ? tc_bx_bytes(k, ~0ull >> 8) : 0;
   if (hbm_budget_bytes < bx_bytes + 64 * ctb) return fail(SFFT_EINVAL, "HBM budget too small");
   sv->arena_cts = (hbm_budget_bytes - bx_bytes) / ctb;

@@ -43,6 +43,7 @@
 #include "common.h"
 #include "kargs.h"
 #include "plan.h"
+#include "ptx.cuh"
 #include "rng.h"
 
 namespace sfft {
@@ -53,122 +54,11 @@ constexpr int kThreads = 512;
 constexpr int kTileM = 128;
 constexpr int kBK = 128;                       // K elements per step: 64-wide swizzle atoms
 constexpr uint32_t kAtoms = kBK / 64;          // atoms per step
-constexpr uint32_t kSpinLimit = 1u << 26;
-constexpr uint64_t kWaitNs = 2000000000ull;    // bound of any single mbarrier wait
 constexpr uint32_t kMaxSmem = 232448;          // 227 KB opt-in per CTA
 constexpr int kExpandThreads = 256;
 constexpr uint32_t kDigitBits = 11;            // fp16 holds the integers 0 .. 2048 exactly
 // 32 digits of 11 bits span 352 bits = 11 words: the epilogue's unit of work
 constexpr uint32_t kGroupDigits = 32, kGroupWords = 11;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Waits for the phase with the given parity, giving up after ~2 s (or an
-// iteration cap, whichever comes first). The timer is read only once the
-// first probe finds the phase still open.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = global_ns();
-  for (uint32_t it = 0; it < kSpinLimit; it++) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((it & 255u) == 255u && global_ns() - t0 > kWaitNs) return false;
-  }
-  return false;
-}
-
-// As mbar_wait_bounded, and also gives up once `flag` is set (another role
-// stopped); the flag is read only on the slow path.
-__device__ __forceinline__ bool mbar_wait_flag(uint64_t* bar, uint32_t parity, volatile int* flag) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = global_ns();
-  for (uint32_t it = 0; it < kSpinLimit; it++) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((it & 255u) == 255u && (*flag || global_ns() - t0 > kWaitNs)) return false;
-  }
-  return false;
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-
-// Bulk copy global -> shared, completing `bytes` transactions on `bar`.
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-
-// 4-byte asynchronous copy global -> shared (completion by commit/wait group).
-__device__ __forceinline__ void cp_async4(uint32_t* dst, const uint32_t* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-
-// An fp32 value holding an integer S in [0, 2^23) -> S: S + 2^23 is exact
-// and its significand field is S.
-__device__ __forceinline__ uint32_t small_float_to_uint(float x) {
-  return __float_as_uint(__fadd_rn(x, 8388608.0f)) - 0x4B000000u;
-}
-
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-
-// Waits until at most one committed group (the most recent) is in flight.
-__device__ __forceinline__ void cp_async_wait_prev() {
-  asm volatile("cp.async.wait_group 1;" ::: "memory");
-}
-
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
-               "r"(ncols)
-               : "memory");
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
 
 // One 128-wide K step of one item, issued by one elected lane of the calling
 // warp (every lane executes the statement; the MMAs and the commits that
@@ -272,86 +162,6 @@ __device__ __forceinline__ void mma_step(uint32_t d0, uint32_t d1, uint32_t at, 
 #undef SFFT_MMA_PROLOGUE1
 #undef SFFT_MMA_SECOND1
 #undef SFFT_MMA_COMMITS
-
-// Commit -> bar from the elected lane of the calling warp (the lane that
-// issued the warp's MMAs: with every lane active, elect.sync picks the same
-// leader each time).
-__device__ __forceinline__ void mma_commit_elected(uint64_t* bar) {
-  asm volatile(
-      "{\n .reg .pred e;\n elect.sync _|e, 0xffffffff;\n"
-      " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}\n" ::"r"(
-          smem_u32(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15},"
-      " [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-        "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-// Each thread stores 32 consecutive 32-bit columns of its own lane.
-__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32]) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
-      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]),
-      "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]),
-      "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]),
-      "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
-      : "memory");
-  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-}
-
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
-// 1024 bytes apart (tile base 1024-byte aligned).
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
-  d |= (uint64_t)1 << 16;                    // leading byte offset (unused when swizzled)
-  d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset
-  d |= (uint64_t)1 << 46;                    // descriptor version
-  d |= (uint64_t)2 << 61;                    // SWIZZLE_128B
-  return d;
-}
-
-__host__ __device__ constexpr uint32_t idesc_f16(uint32_t M, uint32_t N) {
-  return (1u << 4) | ((N >> 3) << 17) | ((M >> 4) << 24);
-}
-
-__device__ __forceinline__ int nib(uint32_t code, int k) {
-  return (int)((int32_t)(code << (28 - 4 * k)) >> 28);
-}
-
-// Eight bits -> eight fp16 values 1.0 / 0.0 (16 bytes, bit q -> element q).
-// y = x * 0x8001 holds x at bit 0 and at bit 15, so bits 2t and 2t+1 of x sit
-// at positions 2t and 16 + 2t; masking them and multiplying by 0x3C00 >> 2t
-// moves each to its half's 0x3C00 (fp16 1.0) in two instructions per word.
-__device__ __forceinline__ uint4 byte_to_h8(uint32_t x) {
-  const uint32_t y = x * 0x8001u;
-  uint4 v;
-  v.x = (y & 0x00010001u) * 0x3C00u;
-  v.y = (y & 0x00040004u) * 0x0F00u;
-  v.z = (y & 0x00100010u) * 0x03C0u;
-  v.w = (y & 0x00400040u) * 0x00F0u;
-  return v;
-}
-
-// Region base of a reference, selected with constant indices: indexing the
-// parameter array with a runtime value would copy the kernel arguments to
-// local memory.
-__device__ __forceinline__ uint32_t* region_base(const KArgs& a, uint32_t region) {
-  return region == 0 ? a.base[0] : region == 1 ? a.base[1] : region == 2 ? a.base[2] : a.base[3];
-}
-
-__device__ __forceinline__ uint32_t* ct_ptr(const KArgs& a, uint32_t ref) {
-  return region_base(a, ref >> 30) + (uint64_t)(ref & SLOT_MASK) * a.ctw;
-}
 
 }  // namespace
 
@@ -547,10 +357,6 @@ struct ItemInfo {
     rot = m * kblocks / mtiles;
   }
 };
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
 
 // Failure-detection test: 1 + the K step whose B copy every CTA's producer
 // withholds in the kWithhold instance of k_gate_tc (its bounded waits then

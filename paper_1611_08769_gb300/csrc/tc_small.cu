@@ -1,0 +1,634 @@
+// Gate product for small ciphertexts (Ng <= 256) on the tensor cores.
+//
+// The GSW product K = BitDecomp(A~) B' (Sec. 7: an N x N matrix product per
+// gate) is a {0,1} matrix times the entries of B'. For Ng <= 256 a whole
+// gate fits in one CTA: A~ and B' (Ng^2 / 8 bytes each, 8 KB at n = 1,
+// ell = 128) and the tensor-core image of B' stay in shared memory, and the
+// gate's two 128-row output tiles are multiplied back to back, so B' is
+// converted once per gate inside the kernel (no separate expansion pass)
+// and nothing but the operands and the outputs crosses HBM.
+//
+// Arithmetic. Every ell-bit entry of B' is cut into 8-bit digits d; per
+// output row i and digit column (element e, digit t)
+//     S[i][e,t] = sum_k bit_k(A~_i) d_t(B'_k[e])  <=  Ng * 255  <  2^16.
+// The MMA runs kind::f16 (fp16 x fp16 -> fp32). The A operand is the bits
+// themselves, masked in place: a 32-bit word of A~ becomes 16 fp16 pairs,
+// pair c holding bits c and c + 16 at one bit position p(c) in 10..14 of
+// each half (the word, or a copy shifted by 5, 10 or -1 bits, AND a mask),
+// so a set bit is the fp16 number with the single exponent bit p - 10 set:
+// 2^-14, 2^-13, 2^-11, 2^-7 or 2 for p = 10..14. The B operand carries the
+// matching factor, d * 2^-6 / value(p) (2^8, 2^7, 2^5, 2^1, 2^-7), so every
+// product is d * 2^-6 exactly and the fp32 accumulator holds S * 2^-6, a
+// multiple of 2^-6 below 2^10: exact. The K order is the same permutation on
+// both sides (K position 32 w + 2 c + h is bit 32 w + c + 16 h of the row).
+// The epilogue reads S back by adding 2^17 (whose ulp is 2^-6), forms each
+// 32-bit word of K from four digit sums and adds c0 P + c1 A + c2 B with the
+// element's limb carries, as the integer kernel does.
+//
+// Roles (one persistent CTA of 16 warps per SM; CTA b takes the gates b,
+// b + grid, ...; a gate is one or two 128-row items):
+//   warp 0       MMA issuer: per item Ng / 16 tcgen05.mma (M 128, N the digit
+//                columns, K 16) from the A stage in tensor memory and the B
+//                image in shared memory, then commits
+//   warp 1       producer: bulk copies of A' and B' of each gate into a ring
+//                slot of shared memory
+//   warps 2, 3   B converters: B' -> its 128B-swizzled K-major fp16 image
+//   warps 4..7   A expanders, one per tensor-memory lane quarter: thread =
+//                row; complement (P - A) in registers when the gate asks for
+//                it, mask the bits, store them to the item's A stage
+//   warps 8..15  epilogue: accumulators -> output words, written in place
+//                over the slot's A' and B' rows; the gate's outputs then leave
+//                by two bulk stores
+// Every wait is bounded (about 2 s); on timeout the kernel records
+// KERR_MMA_TIMEOUT, drains its own MMAs and bulk stores, frees its tensor
+// memory and returns.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <mutex>
+
+#include "common.h"
+#include "kargs.h"
+#include "plan.h"
+#include "ptx.cuh"
+
+namespace sfft {
+
+namespace {
+
+constexpr int kSmThreads = 512;
+constexpr uint32_t kSmTmemCols = 512;
+constexpr uint32_t kSmMaxSlots = 8, kSmMaxAStages = 4, kSmMaxAcc = 8;
+constexpr uint32_t kSmConvWarp0 = 2, kSmConvThreads = 64;
+constexpr uint32_t kSmExpWarp0 = 4, kSmEpiWarp0 = 8, kSmEpiWarps = 8;
+constexpr uint32_t kSmBars = 64;                 // mbarrier slots (8 bytes each)
+constexpr uint32_t kSmMaxSmem = 232448;          // 227 KB opt-in per CTA
+
+// Bounded wait on every lane of the warp; true on every lane iff all saw the
+// phase complete.
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* flag) {
+  return __all_sync(0xFFFFFFFFu, mbar_wait_flag(bar, parity, flag));
+}
+
+// Four K=16 steps of one 64-wide atom: D (+)= A[at .. at + 31] * B^T, B's
+// descriptor advancing 32 bytes (2 units) per step, A 8 columns per step;
+// issued by one elected lane (the whole warp executes the statement).
+__device__ __forceinline__ void mma_atom4(uint32_t d, uint32_t at, uint64_t b, uint32_t idesc,
+                                          uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred e, p, t;\n .reg .b32 a1, a2, a3;\n .reg .b64 b1, b2, b3;\n"
+      " elect.sync _|e, 0xffffffff;\n"
+      " setp.ne.b32 p, %4, 0;\n setp.eq.b32 t, %4, %4;\n"
+      " add.u32 a1, %1, 8;\n add.u32 a2, %1, 16;\n add.u32 a3, %1, 24;\n"
+      " add.u64 b1, %2, 2;\n add.u64 b2, %2, 4;\n add.u64 b3, %2, 6;\n"
+      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n"
+      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], [a1], b1, %3, t;\n"
+      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], [a2], b2, %3, t;\n"
+      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], [a3], b3, %3, t;\n}\n" ::"r"(d),
+      "r"(at), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+// One K=16 step (the last steps of an atom that is not full).
+__device__ __forceinline__ void mma_one(uint32_t d, uint32_t at, uint64_t b, uint32_t idesc,
+                                        uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred e, p;\n elect.sync _|e, 0xffffffff;\n setp.ne.b32 p, %4, 0;\n"
+      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
+      "r"(at), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_st_x16(uint32_t taddr, const uint32_t* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15,%16};" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+      "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Bulk copy shared -> global (bulk-group completion).
+__device__ __forceinline__ void bulk_s2g(void* dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
+               "r"(smem_u32(src)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// 32 bits of a row of A~ -> 16 fp16 pairs (K positions 2c, 2c + 1 <- bits c,
+// c + 16), each set bit at position p(c) of its half: p = c + 10 for c < 5,
+// c + 5 for c < 10, c for c < 15, 14 for c = 15.
+__device__ __forceinline__ void bits_to_pairs(uint32_t x, uint32_t* v) {
+  const uint32_t y10 = x << 10, y5 = x << 5, y1 = x >> 1;
+#pragma unroll
+  for (int c = 0; c < 5; c++) v[c] = y10 & (0x00010001u << (c + 10));
+#pragma unroll
+  for (int c = 5; c < 10; c++) v[c] = y5 & (0x00010001u << (c + 5));
+#pragma unroll
+  for (int c = 10; c < 15; c++) v[c] = x & (0x00010001u << c);
+  v[15] = y1 & 0x40004000u;
+}
+
+// fp16 pair factor of the B operand for pair c: 2^-6 / value(p(c)), with
+// value(p) = 2^(2^(p - 10) - 15): 2^8, 2^7, 2^5, 2^1, 2^-7 for p = 10..14.
+__device__ __forceinline__ uint32_t b_factor(uint32_t c) {
+  const uint32_t p = c < 5 ? c + 10 : c < 10 ? c + 5 : c < 15 ? c : 14u;
+  const uint32_t h = p == 10 ? 0x5C00u : p == 11 ? 0x5800u : p == 12 ? 0x5000u : p == 13 ? 0x4000u : 0x2000u;
+  return h | (h << 16);
+}
+
+__device__ __forceinline__ uint32_t hsub2(uint32_t a, uint32_t b) {
+  uint32_t r;
+  asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+  return r;
+}
+
+__device__ __forceinline__ uint32_t hmul2(uint32_t a, uint32_t b) {
+  uint32_t r;
+  asm("mul.rn.f16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+  return r;
+}
+
+// Digit sum S from the accumulator value S * 2^-6 (S < 2^16): S * 2^-6 + 2^17
+// is exact and its significand field is S.
+__device__ __forceinline__ uint32_t acc_to_sum(uint32_t bits) {
+  return __float_as_uint(__fadd_rn(__uint_as_float(bits), 131072.0f)) - 0x48000000u;
+}
+
+}  // namespace
+
+struct SmShape {
+  uint32_t mt;          // 128-row items per gate
+  uint32_t ksteps;      // K = 16 MMA steps per item (Ng / 16)
+  uint32_t atoms;       // 64-wide K atoms of the B image
+  uint32_t dig;         // 8-bit digits per element (ell / 8)
+  uint32_t ncols;       // MMA N: (n + 1) dig rounded up to 16
+  uint32_t img_bytes;   // B image: atoms x ncols rows x 128 bytes
+  uint32_t raw_bytes;   // one ciphertext: Ng W 4
+  uint32_t slot_bytes;  // image + A' + B', 1024-byte multiple
+  uint32_t nslots, nastages, nacc;
+  uint32_t acols;       // tensor-memory columns of an A stage (Ng / 2)
+  uint32_t acc0;        // first tensor-memory column of the A stages
+  uint32_t smem_bytes;
+};
+
+
+// ---------------------------------------------------------------------------
+// Shared memory (from a 1024-aligned base):
+//   nslots x slot     [B image | A' rows | B' rows]; the epilogue writes the
+//                     outputs over A' (output 0) and B' (output 1)
+//   mbarriers, the tensor-memory address slot, the stop flag
+// Tensor memory (512 columns): nacc accumulators of ncols columns, then
+// nastages A stages of Ng / 2 columns (row i in lane i % 128).
+// Barriers (per ring slot s / A stage / accumulator):
+//   raw_full[s]   the gate's A' and B' landed (producer's transaction count)
+//   img_full[s]   the B image is written (two converter warps)
+//   epi_done[s]   every epilogue warp wrote its outputs for the gate
+//   slot_free[s]  the gate's outputs left the slot (bulk stores read it)
+//   afull[a]      an item's A stage is written (four expander warps)
+//   afree[a]      the item's MMAs are done (commit)
+//   accfull[c]    an item's MMAs are done (commit)
+//   accfree[c]    the epilogue read the accumulator (eight warps)
+// ---------------------------------------------------------------------------
+template <int LL>
+__global__ void __launch_bounds__(kSmThreads, 1) k_gate_sm(KArgs a, SmShape t) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = (uint64_t*)(smem + t.nslots * t.slot_bytes);
+  uint64_t* raw_full = bars;
+  uint64_t* img_full = bars + 8;
+  uint64_t* epi_done = bars + 16;
+  uint64_t* slot_free = bars + 24;
+  uint64_t* afull = bars + 32;
+  uint64_t* afree = bars + 36;
+  uint64_t* accfull = bars + 40;
+  uint64_t* accfree = bars + 48;
+  uint64_t* drain = bars + 56;
+  uint32_t* tslot = (uint32_t*)(bars + 60);
+  volatile int* sflag = (volatile int*)(tslot + 1);
+
+  const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint64_t ngates = a.n;
+  if (blockIdx.x >= ngates) return;
+  const uint32_t nloc = (uint32_t)((ngates - 1 - blockIdx.x) / gridDim.x + 1);
+  const uint32_t items = nloc * t.mt;
+  const uint32_t W = a.W, Ng = a.Ng, NP1 = W / LL;
+  auto gate_of = [&](uint32_t j) { return (uint64_t)blockIdx.x + (uint64_t)j * gridDim.x; };
+  auto img_of = [&](uint32_t s) { return smem + s * t.slot_bytes; };
+  auto araw_of = [&](uint32_t s) { return (uint32_t*)(smem + s * t.slot_bytes + t.img_bytes); };
+  auto braw_of = [&](uint32_t s) {
+    return (uint32_t*)(smem + s * t.slot_bytes + t.img_bytes + t.raw_bytes);
+  };
+
+  if (tid == 0) {
+    for (uint32_t b = 0; b < kSmMaxSlots; b++) {
+      mbar_init(&raw_full[b], 1u);
+      mbar_init(&img_full[b], kSmConvThreads / 32);
+      mbar_init(&epi_done[b], kSmEpiWarps);
+      mbar_init(&slot_free[b], 1u);
+      mbar_init(&accfull[b], 1u);
+      mbar_init(&accfree[b], kSmEpiWarps);
+    }
+    for (uint32_t b = 0; b < kSmMaxAStages; b++) {
+      mbar_init(&afull[b], 4u);
+      mbar_init(&afree[b], 1u);
+    }
+    mbar_init(drain, 1u);
+    *sflag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(tslot, kSmTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ MMA issuer
+    const uint32_t idesc = idesc_f16(128, t.ncols);
+    const uint32_t atom_units = (t.ncols * 128u) >> 4;   // descriptor units between atoms
+    bool ok = true;
+    uint32_t j = 0, m = 0, st = 0, stph = 0, acc = 0, accph = 0;
+    for (uint32_t it = 0; it < items; it++) {
+      const uint32_t s = j % t.nslots;
+      if (it >= t.nacc && !warp_wait(&accfree[acc], accph ^ 1u, sflag)) { ok = false; break; }
+      if (!warp_wait(&afull[st], stph, sflag)) { ok = false; break; }
+      if (m == 0 && !warp_wait(&img_full[s], (j / t.nslots) & 1u, sflag)) { ok = false; break; }
+      tc_fence_after();
+      const uint32_t d = tmem + acc * t.ncols;
+      const uint32_t at = tmem + t.acc0 + st * t.acols;
+      const uint64_t b0 = sw128_desc(smem_u32(img_of(s)));
+      uint32_t k = 0;
+      for (uint32_t atom = 0; atom < t.atoms; atom++) {
+        const uint64_t bd = b0 + (uint64_t)atom * atom_units;
+        if (k + 4 <= t.ksteps) {
+          mma_atom4(d, at + 8u * k, bd, idesc, k);
+          k += 4;
+        } else {
+          for (uint32_t q = 0; k < t.ksteps; q++, k++) mma_one(d, at + 8u * k, bd + 2u * q, idesc, k);
+        }
+      }
+      mma_commit_elected(&afree[st]);
+      mma_commit_elected(&accfull[acc]);
+      if (++st == t.nastages) { st = 0; stph ^= 1u; }
+      if (++acc == t.nacc) { acc = 0; accph ^= 1u; }
+      if (++m == t.mt) { m = 0; j++; }
+    }
+    if (!ok && lane == 0) *sflag = 1;
+    mma_commit_elected(drain);   // tracks every MMA issued
+
+  } else if (warp == 1) {
+    // -------------------------------------------------------------- producer
+    if (lane == 0) {
+      bool ok = true;
+      for (uint32_t j = 0; j < nloc; j++) {
+        const uint32_t s = j % t.nslots, use = j / t.nslots;
+        if (use && !mbar_wait_flag(&slot_free[s], (use - 1) & 1u, sflag)) { ok = false; break; }
+        const GateDesc gd = a.desc[gate_of(j)];
+        mbar_expect_tx(&raw_full[s], 2u * t.raw_bytes);
+        bulk_g2s(araw_of(s), ct_ptr(a, gd.a), t.raw_bytes, &raw_full[s]);
+        bulk_g2s(braw_of(s), ct_ptr(a, gd.b), t.raw_bytes, &raw_full[s]);
+      }
+      if (!ok) *sflag = 1;
+    }
+
+  } else if (warp >= kSmConvWarp0 && warp < kSmExpWarp0) {
+    // ----------------------------------------------------------- B converters
+    // pair P = 16 w + c: rows k0 = 32 w + c and k0 + 16 of B' -> K positions
+    // 2P, 2P + 1 of every digit row n = e dig + t (one 32-bit store each)
+    const uint32_t ct = tid - kSmConvWarp0 * 32;
+    bool ok = true;
+    for (uint32_t j = 0; j < nloc; j++) {
+      const uint32_t s = j % t.nslots;
+      if (!warp_wait(&raw_full[s], (j / t.nslots) & 1u, sflag)) { ok = false; break; }
+      const uint32_t* B = braw_of(s);
+      uint8_t* img = img_of(s);
+      for (uint32_t P = ct; P < Ng / 2; P += kSmConvThreads) {
+        const uint32_t w = P >> 4, c = P & 15u;
+        const uint32_t* r0 = B + (32u * w + c) * W;
+        const uint32_t* r1 = r0 + 16u * W;
+        const uint32_t f2 = b_factor(c);
+        const uint32_t p0 = 2u * P, atom = p0 >> 6, kin = p0 & 63u;
+        uint8_t* base = img + atom * (t.ncols * 128u) + (kin & 7u) * 2u;
+        const uint32_t chunk = kin >> 3;
+        for (uint32_t e = 0; e < NP1; e++) {
+#pragma unroll
+          for (uint32_t wl = 0; wl < (uint32_t)LL; wl++) {
+            const uint32_t x0 = r0[e * LL + wl], x1 = r1[e * LL + wl];
+#pragma unroll
+            for (uint32_t by = 0; by < 4; by++) {
+              const uint32_t n = e * t.dig + wl * 4u + by;
+              const uint32_t sel = by | (by << 4) | ((4u + by) << 8) | ((4u + by) << 12);
+              const uint32_t v = (__byte_perm(x0, x1, sel) & 0x00FF00FFu) | 0x64006400u;
+              const uint32_t h = hmul2(hsub2(v, 0x64006400u), f2);
+              *(uint32_t*)(base + (n >> 3) * 1024u + (n & 7u) * 128u + ((chunk ^ (n & 7u)) << 4)) = h;
+            }
+          }
+        }
+      }
+      fence_proxy_async_smem();   // generic-proxy writes -> the MMA's reads
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&img_full[s]);
+    }
+    if (!ok && lane == 0) *sflag = 1;
+
+  } else if (warp >= kSmExpWarp0 && warp < kSmEpiWarp0) {
+    // ------------------------------------------------------------ A expanders
+    const uint32_t q = warp & 3u;
+    bool ok = true;
+    uint32_t j = 0, m = 0, st = 0, stph = 0;
+    for (uint32_t it = 0; it < items; it++) {
+      const uint32_t s = j % t.nslots;
+      if (m == 0 && !warp_wait(&raw_full[s], (j / t.nslots) & 1u, sflag)) { ok = false; break; }
+      if (it >= t.nastages && !warp_wait(&afree[st], stph ^ 1u, sflag)) { ok = false; break; }
+      tc_fence_after();
+      const uint32_t r0 = m * 128u + q * 32u;
+      if (r0 < Ng) {   // warp-uniform: Ng is a multiple of 32
+        const uint32_t i = r0 + lane;
+        const uint32_t* row = araw_of(s) + i * W;
+        const bool comp = (a.aux[gate_of(j)].flags & 1u) != 0;
+        uint32_t x[8];
+#pragma unroll
+        for (uint32_t w = 0; w < 8; w++) x[w] = w < W ? row[w] : 0u;
+        if (comp) {   // P - A, borrows inside each element
+          const uint32_t pidx = (i / a.ell) * LL + (i % a.ell) / 32, pval = 1u << (i % 32);
+          uint32_t borrow = 0;
+#pragma unroll
+          for (uint32_t w = 0; w < 8; w++) {
+            if (w < W) {
+              if (w % LL == 0) borrow = 0;
+              const uint64_t dv = (uint64_t)(w == pidx ? pval : 0u) - x[w] - borrow;
+              x[w] = (uint32_t)dv;
+              borrow = (uint32_t)(dv >> 63);
+            }
+          }
+        }
+        const uint32_t col = tmem + ((q * 32u) << 16) + t.acc0 + st * t.acols;
+#pragma unroll
+        for (uint32_t w = 0; w < 8; w++) {
+          if (w < W) {
+            uint32_t v[16];
+            bits_to_pairs(x[w], v);
+            tmem_st_x16(col + 16u * w, v);
+          }
+        }
+        tmem_wait_st();
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&afull[st]);
+      if (++st == t.nastages) { st = 0; stph ^= 1u; }
+      if (++m == t.mt) { m = 0; j++; }
+    }
+    if (!ok && lane == 0) *sflag = 1;
+
+  } else if (warp >= kSmEpiWarp0) {
+    // -------------------------------------------------------------- epilogue
+    // warp (q, h): rows 32 q .. 32 q + 31 of each item, elements h, h + 2, ...
+    const uint32_t q = warp & 3u, h = (warp - kSmEpiWarp0) >> 2;
+    const bool storer = warp == kSmEpiWarp0 && lane == 0;
+    bool ok = true;
+    uint32_t j = 0, m = 0, acc = 0, accph = 0;
+    for (uint32_t it = 0; it < items; it++) {
+      const uint32_t s = j % t.nslots;
+      const uint64_t g = gate_of(j);
+      if (!warp_wait(&accfull[acc], accph, sflag)) { ok = false; break; }
+      tc_fence_after();
+      const uint32_t r0 = m * 128u + q * 32u;
+      if (r0 < Ng) {
+        const uint32_t code = a.aux[g].code;
+        const int c00 = nib(code, 0), c01 = nib(code, 1), c02 = nib(code, 2), c03 = nib(code, 3);
+        const int c10 = nib(code, 4), c11 = nib(code, 5), c12 = nib(code, 6), c13 = nib(code, 7);
+        // a term c x (c small, x < 2^32) is c (x - 2^31) + c 2^31: one signed
+        // 32 x 32 -> 64 multiply-add, the constants summed once per output
+        const int64_t bias0 = (int64_t)(c01 + c02 + c03) << 31, bias1 = (int64_t)(c11 + c12 + c13) << 31;
+        const uint32_t i = r0 + lane;
+        const uint32_t pe = i / a.ell, pw = (i % a.ell) / 32;
+        const int64_t pv = (int64_t)1 << (i % 32);
+        uint32_t* Arow = araw_of(s) + i * W;
+        uint32_t* Brow = braw_of(s) + i * W;
+        const uint32_t taddr = tmem + ((q * 32u) << 16) + acc * t.ncols;
+        for (uint32_t e = h; e < NP1; e += 2) {
+          uint32_t v[16];
+          tmem_ld16(taddr + e * t.dig, v);
+          int32_t carry0 = 0, carry1 = 0;
+#pragma unroll
+          for (uint32_t wl = 0; wl < (uint32_t)LL; wl++) {
+            // K word = S0 + S1 2^8 + S2 2^16 + S3 2^24 (< 2^41), as lo + 2^32 hi
+            const uint32_t s0 = acc_to_sum(v[4 * wl]), s1 = acc_to_sum(v[4 * wl + 1]);
+            const uint32_t s2 = acc_to_sum(v[4 * wl + 2]), s3 = acc_to_sum(v[4 * wl + 3]);
+            const uint32_t lo01 = s0 + (s1 << 8), lo23 = s2 + (s3 << 8);   // each < 2^24
+            const uint64_t kk = (uint64_t)lo01 + ((uint64_t)lo23 << 16);
+            const uint32_t klo = (uint32_t)kk;
+            const int32_t khi = (int32_t)(kk >> 32);
+            const uint32_t aw = Arow[e * LL + wl], bw = Brow[e * LL + wl];
+            const int32_t xa = (int32_t)(aw ^ 0x80000000u), xb = (int32_t)(bw ^ 0x80000000u);
+            const int32_t xk = (int32_t)(klo ^ 0x80000000u);
+            int64_t t0 = bias0 + carry0, t1 = bias1 + carry1;
+            t0 += (int64_t)c01 * xa;
+            t0 += (int64_t)c02 * xb;
+            t0 += (int64_t)c03 * xk;
+            t1 += (int64_t)c11 * xa;
+            t1 += (int64_t)c12 * xb;
+            t1 += (int64_t)c13 * xk;
+            if (e == pe && wl == pw) {
+              t0 += c00 * pv;
+              t1 += c10 * pv;
+            }
+            carry0 = (int32_t)(t0 >> 32) + c03 * khi;
+            carry1 = (int32_t)(t1 >> 32) + c13 * khi;
+            Arow[e * LL + wl] = (uint32_t)t0;   // output 0 over A'
+            Brow[e * LL + wl] = (uint32_t)t1;   // output 1 over B'
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&accfree[acc]);
+      if (++acc == t.nacc) { acc = 0; accph ^= 1u; }
+      if (++m == t.mt) {
+        // the gate is complete: its outputs leave by bulk stores
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&epi_done[s]);
+        bool bad = false;
+        if (storer) {
+          if (mbar_wait_flag(&epi_done[s], (j / t.nslots) & 1u, sflag)) {
+            const GateDesc gd = a.desc[g];
+            if (gd.o0 != REF_NONE) bulk_s2g(ct_ptr(a, gd.o0), araw_of(s), t.raw_bytes);
+            if (gd.o1 != REF_NONE) bulk_s2g(ct_ptr(a, gd.o1), braw_of(s), t.raw_bytes);
+            bulk_commit();
+            bulk_wait_read();
+            mbar_arrive(&slot_free[s]);
+          } else {
+            bad = true;
+          }
+        }
+        if (__any_sync(0xFFFFFFFFu, bad)) { ok = false; break; }   // the whole warp leaves together
+        m = 0;
+        j++;
+      }
+    }
+    if (storer) bulk_wait_all();
+    if (!ok && lane == 0) *sflag = 1;
+  }
+
+  __syncthreads();
+  if (*sflag) {
+    if (tid == 0 && a.err) atomicExch(a.err, KERR_MMA_TIMEOUT);
+    if (warp == 0) mbar_wait_bounded(drain, 0);   // own MMAs drain before TMEM is freed
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, kSmTmemCols);
+  }
+}
+
+}  // namespace sfft
+
+namespace sfft {
+
+namespace {
+
+// Ring slots used when no tuned value is set (sfft_autotune stores one per
+// shape).
+constexpr uint32_t kSmDefaultSlots = 4;
+
+uint32_t sm_smem_bytes(uint32_t slot_bytes, uint32_t nslots) {
+  return 1024u + nslots * slot_bytes + kSmBars * 8u;
+}
+
+// nslots 0: the tuned or default ring depth.
+bool make_sm_shape(const KArgs& a, uint32_t nslots, SmShape* t) {
+  if (a.Ng < 128 || a.Ng > 256 || a.L == 0 || a.L > 4 || a.ell != 32 * a.L || a.W % a.L) return false;
+  const uint32_t NP1 = a.W / a.L;
+  if (NP1 < 2 || a.W > 8) return false;
+  t->mt = (a.Ng + 127) / 128;
+  t->ksteps = a.Ng / 16;
+  t->atoms = (a.Ng + 63) / 64;
+  t->dig = a.ell / 8;
+  t->ncols = (NP1 * t->dig + 15) / 16 * 16;
+  if (t->ncols > 256) return false;
+  t->img_bytes = t->atoms * t->ncols * 128u;
+  t->raw_bytes = a.Ng * a.W * 4u;
+  t->slot_bytes = (t->img_bytes + 2u * t->raw_bytes + 1023u) / 1024u * 1024u;
+  t->acols = a.Ng / 2;
+  t->nastages = std::min<uint32_t>(kSmMaxAStages, (kSmTmemCols - 2u * t->ncols) / t->acols);
+  if (t->nastages < 2) return false;
+  t->nacc = std::min<uint32_t>(kSmMaxAcc, (kSmTmemCols - t->nastages * t->acols) / t->ncols);
+  if (t->nacc < 2) return false;
+  t->acc0 = t->nacc * t->ncols;
+  uint32_t ns = nslots ? nslots : kSmDefaultSlots;
+  while (ns > 1 && sm_smem_bytes(t->slot_bytes, ns) > kSmMaxSmem) ns--;
+  if (ns < 2 || ns > kSmMaxSlots) return false;
+  t->nslots = ns;
+  // at least half the opt-in: one CTA per SM (each allocates all 512
+  // tensor-memory columns)
+  t->smem_bytes = std::max(sm_smem_bytes(t->slot_bytes, ns), kSmMaxSmem / 2 + 1024u);
+  return true;
+}
+
+// Per device: SM count and whether the kernels' shared-memory opt-in is set.
+struct SmDevice {
+  int sms = 0;
+  bool configured = false;
+};
+std::mutex g_sm_mu;
+SmDevice g_sm_dev[64];
+uint32_t g_sm_tuned_slots[64][4] = {};   // [device][limbs - 1], 0 = untuned
+
+int sm_device(SmDevice** out, int* ordinal) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= 64) return fail(SFFT_EINVAL, "device ordinal out of range");
+  std::lock_guard<std::mutex> lk(g_sm_mu);
+  SmDevice& d = g_sm_dev[dev];
+  if (!d.configured) {
+    e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gate_sm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmMaxSmem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gate_sm<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmMaxSmem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gate_sm<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmMaxSmem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gate_sm<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmMaxSmem);
+    if (e != cudaSuccess) return cuda_fail(e, "small-ciphertext kernel attributes");
+    d.configured = true;
+  }
+  *out = &d;
+  if (ordinal) *ordinal = dev;
+  return SFFT_OK;
+}
+
+}  // namespace
+
+bool sm_supported(const KArgs& a) {
+  SmShape t;
+  return make_sm_shape(a, 0, &t);
+}
+
+uint32_t sm_digit_columns(const KArgs& a) {
+  SmShape t;
+  if (!make_sm_shape(a, 0, &t)) return 0;
+  return (a.W / a.L) * t.dig;
+}
+
+int launch_gates_sm_slots(const KArgs& a, uint32_t nslots, cudaStream_t st) {
+  if (a.n == 0) return SFFT_OK;
+  SmDevice* dev = nullptr;
+  int ordinal = 0;
+  int rc = sm_device(&dev, &ordinal);
+  if (rc) return rc;
+  if (!nslots) {
+    std::lock_guard<std::mutex> lk(g_sm_mu);
+    nslots = g_sm_tuned_slots[ordinal][(a.L - 1) & 3];
+  }
+  SmShape t{};
+  if (!make_sm_shape(a, nslots, &t))
+    return fail(SFFT_EPARAM, "small-ciphertext kernel does not support this shape");
+  const uint64_t blocks = std::min<uint64_t>(a.n, (uint64_t)dev->sms);
+  Timer* tm = static_cast<Timer*>(a.timer);
+  if (tm) cudaEventRecord(tm->next(kTimeGate), st);
+  switch (a.L) {
+    case 1: k_gate_sm<1><<<(unsigned)blocks, kSmThreads, t.smem_bytes, st>>>(a, t); break;
+    case 2: k_gate_sm<2><<<(unsigned)blocks, kSmThreads, t.smem_bytes, st>>>(a, t); break;
+    case 3: k_gate_sm<3><<<(unsigned)blocks, kSmThreads, t.smem_bytes, st>>>(a, t); break;
+    default: k_gate_sm<4><<<(unsigned)blocks, kSmThreads, t.smem_bytes, st>>>(a, t); break;
+  }
+  if (tm) cudaEventRecord(tm->next(kTimeGate), st);
+  count_launches(1);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SFFT_OK : cuda_fail(e, "small-ciphertext gate kernel launch");
+}
+
+int launch_gates_sm(const KArgs& a, cudaStream_t st) { return launch_gates_sm_slots(a, 0, st); }
+
+// Ring depth used from now on for this device and limb count (0 = default).
+int sm_set_tuned_slots(uint32_t L, uint32_t nslots) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= 64 || L == 0 || L > 4) return fail(SFFT_EINVAL, "bad device or limb count");
+  std::lock_guard<std::mutex> lk(g_sm_mu);
+  g_sm_tuned_slots[dev][L - 1] = nslots;
+  return SFFT_OK;
+}
+
+}  // namespace sfft

@@ -243,72 +243,88 @@ def flags_of(sf, cfg):
             | (sf.PLAN_ENC_TWIDDLE if v["enc_twiddle"] else 0))
 
 
-def params_for(sf, pset, dims_list, variant=None):
-    if pset == "P1":
-        ell = max(sf.min_ell(*d, n=1, chi=1, **(variant or {})) for d in dims_list)
-        return sf.param_set("P1", ell)
-    return sf.param_set(pset)
+# The fixed parameter sets of the workloads, (n, ell, m, chi); P1 takes the
+# smallest safe ell of its circuit (chi = 1, m = Ng).
+PSETS = {"P0": (1, 32, 64, 0), "P2": (1, 128, 256, 0)}
 
 
-def fft_inputs(sf, dims, re_, im_, enc_twiddle):
-    """(re, im) values encrypted for one request: the signal, then (with
-    encrypted twiddles) the twiddle table W_M^k, M = max(N1, N2), as exact
-    fixed-point values."""
-    N1, N2, F, f = dims
-    if not enc_twiddle:
-        return list(re_), list(im_)
-    wr, wi = sf.twiddles(max(N1, N2), f)
-    return (list(re_) + [w / 2 ** f for w in wr.tolist()],
-            list(im_) + [w / 2 ** f for w in wi.tolist()])
-
-
-def fft_workload(cfg):
-    """(params, [(dims, re, im, key_set, enc_seed)]) of a single-request config."""
-    import paper_1611_08769_gb300 as sf
-    from synthetic import image_2d, signal_1d
+def workload_items(cfg):
+    """[(dims, re, im, key_set, enc_seed)] of a config: seeded synthetic
+    signals only (no scheme code)."""
+    from synthetic import batch_requests, image_2d, serving_trace, signal_1d
     c = CONFIGS[cfg]
+    if c["kind"] == "batch":
+        reqs = batch_requests(count=c["count"], seed=4, key_sets=c["key_sets"])
+        return [((r.N1, r.N2, r.F, r.f), r.re, r.im, r.key_set, i) for i, r in enumerate(reqs)]
+    if c["kind"] == "serve":   # a sample of the serving trace's requests
+        trace = serving_trace(16, 1.0, seed=6, key_sets=c["key_sets"])
+        return [((r.N1, r.N2, r.F, r.f), r.re, r.im, r.key_set, r.seed) for r in trace]
     dims = (c["N1"], c["N2"], c["F"], c["f"])
-    params = params_for(sf, c["pset"], [dims], variant_of(cfg))
     if c["N2"] == 1:
         re_, im_ = signal_1d(c["N1"], c["lo"], c["hi"], seed=0)
     else:
         re_, im_ = image_2d(c["N1"], c["N2"], seed=0)
-    return params, [(dims, re_, im_, 0, 0)]
+    return [(dims, re_, im_, 0, 0)]
 
 
-def batch_workload(cfg):
-    import paper_1611_08769_gb300 as sf
-    from synthetic import batch_requests
+def _p1_dims(cfg, items):
     c = CONFIGS[cfg]
-    reqs = batch_requests(count=c["count"], seed=4, key_sets=c["key_sets"])
-    params = params_for(sf, c["pset"], [(r.N1, r.N2, r.F, r.f) for r in reqs])
-    return params, [((r.N1, r.N2, r.F, r.f), r.re, r.im, r.key_set, i) for i, r in enumerate(reqs)]
+    return [c["ell_of"]] if c["kind"] == "refresh" else sorted({d for d, *_ in items})
 
 
-def serve_workload(cfg):
-    """A sample of the serving trace's requests (used by the oracle arm)."""
-    import paper_1611_08769_gb300 as sf
-    from synthetic import serving_trace
+def product_params(sf, cfg, items=()):
+    """Parameters of a config from the library (its own smallest ell for P1)."""
     c = CONFIGS[cfg]
-    trace = serving_trace(16, 1.0, seed=6, key_sets=c["key_sets"])
-    return sf.param_set(c["pset"]), [((r.N1, r.N2, r.F, r.f), r.re, r.im, r.key_set, r.seed)
-                                     for r in trace]
+    if c["pset"] != "P1":
+        return sf.Params(*PSETS[c["pset"]][:2], PSETS[c["pset"]][2], PSETS[c["pset"]][3])
+    var = {} if c["kind"] == "refresh" else variant_of(cfg)
+    ell = max(sf.min_ell(*d, n=1, chi=1, **var) for d in _p1_dims(cfg, items))
+    return sf.param_set("P1", ell)
 
 
-def refresh_workload(cfg):
-    """(params, count): the refresh config's parameters and batch size."""
-    import paper_1611_08769_gb300 as sf
+def oracle_params(cfg, items=()):
+    """Parameters of a config from the oracle alone (oracle.noise.smallest_ell
+    over the oracle's own circuits for P1): what the reference arm and the CPU
+    baseline run, independent of the library."""
+    from oracle import circuit, gsw, noise
     c = CONFIGS[cfg]
-    return sf.param_set("P1", sf.min_ell(*c["ell_of"], n=1, chi=1)), c["count"]
+    if c["pset"] != "P1":
+        return gsw.Params(*PSETS[c["pset"]])
+    var = {} if c["kind"] == "refresh" else variant_of(cfg)
+    ell = max(noise.smallest_ell(circuit.fft_circuit(*d, **var), 1, 1) for d in _p1_dims(cfg, items))
+    return gsw.Params(1, ell, 2 * ell, 1)
 
 
-def workload(cfg):
-    kind = CONFIGS[cfg]["kind"]
-    if kind == "batch":
-        return batch_workload(cfg)
-    if kind == "serve":
-        return serve_workload(cfg)
-    return fft_workload(cfg)
+def fft_inputs(twiddles, dims, re_, im_, enc_twiddle):
+    """(re, im) values encrypted for one request: the signal, then (with
+    encrypted twiddles) the twiddle table W_M^k, M = max(N1, N2), as exact
+    fixed-point values; twiddles(M, f) gives the quantised (wr, wi) lists."""
+    N1, N2, F, f = dims
+    if not enc_twiddle:
+        return list(re_), list(im_)
+    wr, wi = twiddles(max(N1, N2), f)
+    return (list(re_) + [w / 2 ** f for w in wr],
+            list(im_) + [w / 2 ** f for w in wi])
+
+
+def product_twiddles(sf):
+    def tw(M, f):
+        wr, wi = sf.twiddles(M, f)
+        return wr.tolist(), wi.tolist()
+    return tw
+
+
+def oracle_twiddles(M, f):
+    from oracle import circuit
+    tw = circuit.twiddles(M, f)
+    return [w[0] for w in tw], [w[1] for w in tw]
+
+
+def workload(sf, cfg):
+    """(params, items) of a single-request, batch or serving config for the
+    library's arm."""
+    items = workload_items(cfg)
+    return product_params(sf, cfg, items), items
 
 
 def oracle_gate_prefix(c, p, input_bit, budget_s):
@@ -347,13 +363,13 @@ def cpu_oracle_sample(params, items, budget_s, variant=None):
 
     Returns (FFTs/s, gates/s, description). FFT time is the per-gate time
     times the mean oracle gate count of the workload's distinct FFT shapes."""
-    import paper_1611_08769_gb300 as sf
     from oracle import circuit, fixedpoint as fx, gsw
     variant = variant or {}
     p = gsw.Params(params.n, params.ell, params.m, params.chi)
     (N1, N2, F, f), re_, im_, _, _ = items[0]
     c = circuit.fft_circuit(N1, N2, F, f, **variant)
-    re_all, im_all = fft_inputs(sf, (N1, N2, F, f), re_, im_, variant.get("enc_twiddle", False))
+    re_all, im_all = fft_inputs(oracle_twiddles, (N1, N2, F, f), re_, im_,
+                                variant.get("enc_twiddle", False))
 
     def input_bit(w):   # wire (sample * 2 + part) * F + bit, twiddles after the signal
         sample, rem = divmod(w, 2 * F)
@@ -396,13 +412,14 @@ def run_reference(args, rank, world):
     vals = []
     detail = ""
     if CONFIGS[args.config]["kind"] == "refresh":
-        params, count = refresh_workload(args.config)
+        params, count = oracle_params(args.config), CONFIGS[args.config]["count"]
         metric, unit = "refreshed ciphertexts/s", "ct/s"
         cfg = refresh_config_json(args.config, params, count)
         sample = lambda: cpu_refresh_sample(params, count, budget,  # noqa: E731
                                             variant_of(args.config)["xcarry"])
     else:
-        params, items = workload(args.config)
+        items = workload_items(args.config)
+        params = oracle_params(args.config, items)
         metric, unit = "encrypted FFTs/s", "FFT/s"
         cfg = config_json(args.config, params, items)
         sample = lambda: cpu_oracle_sample(params, items, budget,  # noqa: E731
@@ -465,7 +482,7 @@ def run_refresh(args):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     rank = int(os.environ.get("RANK", "0"))
     torch.cuda.set_device(local)
-    params, count = refresh_workload(args.config)
+    params, count = product_params(sf, args.config), CONFIGS[args.config]["count"]
     flags = (sf.PLAN_INT_KERNEL if args.kernel == "int" else 0) | flags_of(sf, args.config)
     cw = sf.ct_words(params)
     keys = sf.keygen(params, 3000)
@@ -523,10 +540,12 @@ def run_refresh(args):
         [int(b) for b in src_bits[:count // 4 * 4]]
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        v, gps, detail = cpu_refresh_sample(params, count, args.cpu_seconds,
+        oparams = oracle_params(args.config)   # the oracle's own ell (equal to the library's)
+        v, gps, detail = cpu_refresh_sample(oparams, count, args.cpu_seconds,
                                             variant_of(args.config)["xcarry"])
         cpu = {"value": v, "unit": "ct/s", "cores": os.cpu_count(), "kind": "oracle",
-               "sample": detail, "gates_per_s": gps}
+               "sample": detail, "gates_per_s": gps, "oracle_ell": oparams.ell,
+               "oracle_ell_equals_library": oparams.ell == params.ell}
     if rank != 0:
         return
     cfg = refresh_config_json(args.config, params, count)
@@ -558,7 +577,7 @@ def run_gates(args):
     import paper_1611_08769_gb300 as sf
     from paper_1611_08769_gb300 import build as sfbuild
     sfbuild.build()
-    params, _ = workload(args.config)
+    params, _ = workload(sf, args.config)
     cw = sf.ct_words(params)
     G = args.gates
     gen = torch.Generator(device="cuda").manual_seed(0)
@@ -698,7 +717,7 @@ def main():
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     sfbuild.build()
-    params, items = workload(args.config)
+    params, items = workload(sf, args.config)
     flags = (sf.PLAN_INT_KERNEL if args.kernel == "int" else 0) | flags_of(sf, args.config)
     enc_tw = variant_of(args.config)["enc_twiddle"]
     cw = sf.ct_words(params)
@@ -711,7 +730,7 @@ def main():
     info = batch.info
     d_in = torch.empty((info["inputs"], cw), dtype=torch.int32, device="cuda")
     for r, ((N1, N2, F, f), re_, im_, ks, seed) in enumerate(items):
-        re_all, im_all = fft_inputs(sf, (N1, N2, F, f), re_, im_, enc_tw)
+        re_all, im_all = fft_inputs(product_twiddles(sf), (N1, N2, F, f), re_, im_, enc_tw)
         n = len(re_all) * 2 * F
         sf.encrypt_bits_device(params, pubs[ks], re_all, im_all, F, f, seed,
                                d_in[batch.in_off[r]:batch.in_off[r] + n])
@@ -797,9 +816,11 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        fps, gps, detail = cpu_oracle_sample(params, items, args.cpu_seconds, variant_of(args.config))
+        oparams = oracle_params(args.config, items)   # the oracle's own ell
+        fps, gps, detail = cpu_oracle_sample(oparams, items, args.cpu_seconds, variant_of(args.config))
         cpu = {"value": fps, "unit": "FFT/s", "cores": os.cpu_count(), "kind": "oracle",
-               "sample": detail, "gates_per_s": gps}
+               "sample": detail, "gates_per_s": gps, "oracle_ell": oparams.ell,
+               "oracle_ell_equals_library": oparams.ell == params.ell}
 
     if rank == 0:
         cfg = config_json(args.config, params, items)

@@ -48,3 +48,25 @@ def test_roofline_arithmetic():
     assert abs(r["achieved"] - flops * 1000 / 1.0 / 1e12) < 1e-9
     assert abs(r["expand"]["achieved"] - (2112 * 2112 // 8 + 17 * 192 * 256) * 1000 / 0.5 / 1e9) < 1e-6
     assert r["bound"] == "tensor" and r["expand"]["bound"] == "hbm"
+
+
+@pytest.mark.parametrize("config", ["fft8_8bit_toy", "fft8_8bit_nand"])
+def test_reference_arm_never_loads_the_library(config):
+    """The reference arm times the oracle on a workload derived from the
+    oracle and the synthetic inputs alone: neither the product package nor its
+    native library is imported or loaded (P1 configs take the oracle's own
+    smallest ell)."""
+    code = (
+        "import sys, argparse, bench\n"
+        f"a = argparse.Namespace(config={config!r}, steps=1, warmup=0, cpu_seconds=0.5, gpus=1)\n"
+        "bench.run_reference(a, 0, 1)\n"
+        "assert 'paper_1611_08769_gb300' not in sys.modules, 'product package imported'\n"
+        "maps = open('/proc/self/maps').read() if sys.platform.startswith('linux') else ''\n"
+        "assert 'libsfft' not in maps, 'native library loaded'\n")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    d = json.loads([l for l in r.stdout.splitlines() if l.startswith("{")][0])
+    assert d["impl"] == "reference" and d["value"] > 0
+    if config == "fft8_8bit_nand":
+        assert d["config"]["ell"] == 704   # the NAND circuit's own smallest ell (Sec. 7 variant)

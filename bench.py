@@ -88,7 +88,9 @@ def parse():
                     help="fft: the workload (default); gates: one level of independent random "
                          "gates at the workload's parameters")
     ap.add_argument("--gates", type=int, default=128, help="gates per level in --mode gates")
-    ap.add_argument("--kernel", default="auto", choices=["auto", "int", "tc"])
+    ap.add_argument("--kernel", default="auto", choices=["auto", "int", "tc", "sm"],
+                    help="gate kernel: automatic, integer ALU, general tensor-core, "
+                         "small-ciphertext tensor-core")
     ap.add_argument("--budget-gb", type=float, default=150.0, help="serving HBM admission budget")
     ap.add_argument("--requests", type=int, default=0, help="serving: requests in the trace")
     return ap.parse_args()
@@ -173,6 +175,9 @@ def measured_peaks():
 # (n, ell). The algorithmic bytes of a product at these parameters are 3.07 MB:
 # the expanded B operand once, the A and B rows, the two output rows.
 TC_DRAM_BYTES_PER_PRODUCT = {(1, 1056): 3.120e6}
+# The same for the small-ciphertext kernel (k_gate_sm), keyed by (n, ell);
+# empty until an ncu capture of the current kernel is recorded.
+SM_DRAM_BYTES_PER_PRODUCT = {}
 
 
 def expand_bytes_per_product(params):
@@ -200,6 +205,27 @@ def roofline(params, gate_kernel, gate_ms, launches, gates_timed, tc_columns=0, 
     W = (params.n + 1) * L
     avg_launch_ms = gate_ms / max(1, launches)
     sec = gate_ms / 1000.0 if gate_ms > 0 else float("inf")
+    if gate_kernel == 3:
+        # small-ciphertext kernel: HBM-bound; algorithmic bytes per product =
+        # two ciphertexts read and one written, 3 Ng^2 / 8
+        peaks, src = measured_peaks()
+        bpp = 3.0 * Ng * Ng / 8
+        achieved = bpp * gates_timed / sec / 1e9
+        hbm = float(peaks["hbm_gbs"])
+        cols = tc_columns or (params.n + 1) * params.ell // 8
+        ncols = (cols + 15) // 16 * 16
+        flops = 2.0 * Ng * Ng * ncols * gates_timed / sec / 1e12
+        tpk = float(peaks["bf16_tflops_sustained"])
+        per = SM_DRAM_BYTES_PER_PRODUCT.get((params.n, params.ell))
+        return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm,
+                "traffic": per * gates_timed / max(1, launches) if per else None,
+                "traffic_unit": "bytes per launch", "kernel": "k_gate_sm",
+                "avg_launch_ms": avg_launch_ms, "bytes_per_product": bpp,
+                "peak_source": f"hbm_gbs {src}",
+                "tensor": {"achieved": flops, "peak": tpk, "unit": "TFLOP/s", "frac": flops / tpk,
+                           "flops_per_product": 2.0 * Ng * Ng * ncols,
+                           "peak_source": f"bf16_tflops_sustained {src}"}}
     if gate_kernel == 2:
         peaks, src = measured_peaks()
         cols = tc_columns or (params.n + 1) * -(-params.ell // 11)
@@ -235,6 +261,11 @@ def variant_of(cfg):
     the oracle's fft_circuit)."""
     c = CONFIGS[cfg]
     return {k: bool(c.get(k, False)) for k in ("xcarry", "nand", "enc_twiddle")}
+
+
+def kernel_flags(sf, kernel):
+    """Plan flags of --kernel (auto and sm: the library's choice)."""
+    return {"int": sf.PLAN_INT_KERNEL, "tc": sf.PLAN_TC_KERNEL}.get(kernel, 0)
 
 
 def flags_of(sf, cfg):
@@ -483,7 +514,7 @@ def run_refresh(args):
     rank = int(os.environ.get("RANK", "0"))
     torch.cuda.set_device(local)
     params, count = product_params(sf, args.config), CONFIGS[args.config]["count"]
-    flags = (sf.PLAN_INT_KERNEL if args.kernel == "int" else 0) | flags_of(sf, args.config)
+    flags = kernel_flags(sf, args.kernel) | flags_of(sf, args.config)
     cw = sf.ct_words(params)
     keys = sf.keygen(params, 3000)
     pub = torch.from_numpy(keys.public().view(np.int32)).cuda()
@@ -587,7 +618,7 @@ def run_gates(args):
     code0 = [sf.pack_code(0, 1, 1, -2)] * G
     code1 = [sf.pack_code(0, 0, 0, 1)] * G
     flags = [2 if g % 3 else 3 for g in range(G)]   # every third A operand complemented
-    kern = {"auto": 0, "int": 1, "tc": 2}[args.kernel]
+    kern = {"auto": 0, "int": 1, "tc": 2, "sm": 3}[args.kernel]
     for _ in range(args.warmup):
         sf.gate_level(params, A, B, O0, O1, code0, code1, flags, kernel=kern)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -600,7 +631,7 @@ def run_gates(args):
         ms.append(ev0.elapsed_time(ev1))
     t = statistics.median(ms)
     info = sf.circuit_info(params, 2, 1, 4, 1)
-    gk = 1 if kern == 1 else (2 if kern == 2 else info["gate_kernel"])
+    gk = kern if kern else info["gate_kernel"]
     print(json.dumps({"mode": "gates", "gates": G, "ms_per_level": t, "gates_per_s": G / t * 1e3,
                       "config": {"workload": args.config, "n": params.n, "ell": params.ell},
                       "note": "includes the test hook's descriptor upload, allocation and sync",
@@ -718,7 +749,7 @@ def main():
     torch.cuda.set_device(local)
     sfbuild.build()
     params, items = workload(sf, args.config)
-    flags = (sf.PLAN_INT_KERNEL if args.kernel == "int" else 0) | flags_of(sf, args.config)
+    flags = kernel_flags(sf, args.kernel) | flags_of(sf, args.config)
     enc_tw = variant_of(args.config)["enc_twiddle"]
     cw = sf.ct_words(params)
     reqs = [d for d, *_ in items]

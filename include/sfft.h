@@ -430,6 +430,22 @@ void sfft_server_free(sfft_server* sv);
  * signed nibbles c0 | c1 << 4 | c2 << 8 | c3 << 12 (two's complement).
  * kernel: 0 automatic, 1 integer ALU, 2 tensor cores (EPARAM if unsupported).
  * Synchronises the stream; SFFT_ETIMEOUT if a bounded device wait ran out. */
+/* Autotuner of the small-ciphertext tensor-core kernel (gate kernel 3, used
+ * where Ng <= 256): for each ring depth it can run (gates in flight per CTA,
+ * 2 to 8 where shared memory allows) it times one level of n_gates half-adder
+ * products of random ciphertexts at p with CUDA events on the legacy stream
+ * (best of reps; 0 means 3), then keeps the fastest depth for the current
+ * device and p's limb count: every later launch of the kernel there uses it.
+ * h_us_per_gate (optional, 8 entries, index = depth - 1) receives the
+ * microseconds per gate of each depth (0 where not run). Allocates and frees
+ * its own buffers (4 n_gates ciphertexts) and synchronises the device.
+ * EPARAM if the kernel does not take p; EINVAL unless 1 <= n_gates <= 2^24. */
+int sfft_autotune_small(const sfft_params* p, uint64_t n_gates, uint32_t reps,
+                        uint32_t* best_slots, double* h_us_per_gate);
+/* Sets (nslots 2..8) or clears (0: the default of 4) the ring depth of the
+ * small-ciphertext kernel for the current device and ell (32, 64, 96, 128). */
+int sfft_small_kernel_set_slots(uint32_t ell, uint32_t nslots);
+
 int sfft_gate_level(const sfft_params* p, const uint32_t* d_a, const uint32_t* d_b,
                     uint32_t* d_out0, uint32_t* d_out1, const uint16_t* h_code0,
                     const uint16_t* h_code1, const uint8_t* h_flags, uint64_t n_gates,

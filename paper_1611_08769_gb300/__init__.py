@@ -456,6 +456,20 @@ def gate_level(params, d_a, d_b, d_out0, d_out1, code0, code1, flags, stream=Non
                                 _stream(stream)))
 
 
+def autotune_small(params, n_gates=20000, reps=3):
+    """Autotuner of the small-ciphertext kernel (sfft_autotune_small): returns
+    (chosen ring depth, {depth: microseconds per gate})."""
+    best = ctypes.c_uint32(0)
+    us = (ctypes.c_double * 8)()
+    check(lib().sfft_autotune_small(ctypes.byref(params), n_gates, reps, ctypes.byref(best), us))
+    return int(best.value), {k + 1: float(us[k]) for k in range(8) if us[k] > 0}
+
+
+def small_kernel_set_slots(ell, nslots):
+    """Ring depth of the small-ciphertext kernel at ell (0: the default)."""
+    check(lib().sfft_small_kernel_set_slots(ell, nslots))
+
+
 def gate_level_withheld(params, d_a, d_b, d_out0, code0, flags, step, stream=None):
     """Failure-detection test hook (sfft_gate_level_withheld): raises SfftError
     with code SFFT_ETIMEOUT once the kernel's bounded waits have run out."""

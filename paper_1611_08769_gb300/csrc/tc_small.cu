@@ -25,14 +25,15 @@
 // 32-bit word of K from four digit sums and adds c0 P + c1 A + c2 B with the
 // element's limb carries, as the integer kernel does.
 //
-// Roles (one persistent CTA of 16 warps per SM; CTA b takes the gates b,
+// Roles (one persistent CTA of 18 warps per SM; CTA b takes the gates b,
 // b + grid, ...; a gate is one or two 128-row items):
 //   warp 0       MMA issuer: per item Ng / 16 tcgen05.mma (M 128, N the digit
 //                columns, K 16) from the A stage in tensor memory and the B
 //                image in shared memory, then commits
 //   warp 1       producer: bulk copies of A' and B' of each gate into a ring
 //                slot of shared memory
-//   warps 2, 3   B converters: B' -> its 128B-swizzled K-major fp16 image
+//   warps 2, 3, 16, 17  B converters (one per SM sub-partition): B' -> its
+//                128B-swizzled K-major fp16 image
 //   warps 4..7   A expanders, one per tensor-memory lane quarter: thread =
 //                row; complement (P - A) in registers when the gate asks for
 //                it, mask the bits, store them to the item's A stage
@@ -47,6 +48,7 @@
 #include <algorithm>
 #include <cstdint>
 #include <mutex>
+#include <vector>
 
 #include "common.h"
 #include "kargs.h"
@@ -57,10 +59,10 @@ namespace sfft {
 
 namespace {
 
-constexpr int kSmThreads = 512;
+constexpr int kSmThreads = 576;                  // 18 warps
 constexpr uint32_t kSmTmemCols = 512;
 constexpr uint32_t kSmMaxSlots = 8, kSmMaxAStages = 4, kSmMaxAcc = 8;
-constexpr uint32_t kSmConvWarp0 = 2, kSmConvThreads = 64;
+constexpr uint32_t kSmConvWarps = 4, kSmConvThreads = 128;   // warps 2, 3, 16, 17
 constexpr uint32_t kSmExpWarp0 = 4, kSmEpiWarp0 = 8, kSmEpiWarps = 8;
 constexpr uint32_t kSmBars = 64;                 // mbarrier slots (8 bytes each)
 constexpr uint32_t kSmMaxSmem = 232448;          // 227 KB opt-in per CTA
@@ -190,28 +192,84 @@ struct SmShape {
 };
 
 
+// Slot metadata: the gate's descriptor, written by the producer with its
+// bulk copies (visible to every role once raw_full completes).
+struct SlotMeta {
+  uint32_t a, b, o0, o1, code, flags, pad0, pad1;
+};
+
+// Rows of LL-limb elements: aligned vector access where the limb count
+// allows (16-byte for 4 limbs, 8-byte for 2), word by word otherwise.
+template <int LL>
+__device__ __forceinline__ void ld_elem(const uint32_t* p, uint32_t (&v)[LL]) {
+  if constexpr (LL == 4) {
+    const uint4 q = *reinterpret_cast<const uint4*>(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+  } else if constexpr (LL == 2) {
+    const uint2 q = *reinterpret_cast<const uint2*>(p);
+    v[0] = q.x; v[1] = q.y;
+  } else {
+#pragma unroll
+    for (int k = 0; k < LL; k++) v[k] = p[k];
+  }
+}
+
+template <int LL>
+__device__ __forceinline__ void st_elem(uint32_t* p, const uint32_t (&v)[LL]) {
+  if constexpr (LL == 4) {
+    *reinterpret_cast<uint4*>(p) = make_uint4(v[0], v[1], v[2], v[3]);
+  } else if constexpr (LL == 2) {
+    *reinterpret_cast<uint2*>(p) = make_uint2(v[0], v[1]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < LL; k++) p[k] = v[k];
+  }
+}
+
+// A row of W <= 8 words into registers (16-byte loads when W is a multiple of 4).
+__device__ __forceinline__ void ld_row(const uint32_t* row, uint32_t W, uint32_t (&x)[8]) {
+  if ((W & 3u) == 0) {
+#pragma unroll
+    for (uint32_t w = 0; w < 8; w += 4) {
+      if (w < W) {
+        const uint4 q = *reinterpret_cast<const uint4*>(row + w);
+        x[w] = q.x; x[w + 1] = q.y; x[w + 2] = q.z; x[w + 3] = q.w;
+      } else {
+        x[w] = x[w + 1] = x[w + 2] = x[w + 3] = 0u;
+      }
+    }
+  } else {
+#pragma unroll
+    for (uint32_t w = 0; w < 8; w++) x[w] = w < W ? row[w] : 0u;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Shared memory (from a 1024-aligned base):
 //   nslots x slot     [B image | A' rows | B' rows]; the epilogue writes the
 //                     outputs over A' (output 0) and B' (output 1)
-//   mbarriers, the tensor-memory address slot, the stop flag
+//   slot metadata, mbarriers, the tensor-memory address slot, the stop flag
 // Tensor memory (512 columns): nacc accumulators of ncols columns, then
 // nastages A stages of Ng / 2 columns (row i in lane i % 128).
 // Barriers (per ring slot s / A stage / accumulator):
 //   raw_full[s]   the gate's A' and B' landed (producer's transaction count)
-//   img_full[s]   the B image is written (two converter warps)
+//   img_full[s]   the B image is written (four converter warps)
 //   epi_done[s]   every epilogue warp wrote its outputs for the gate
 //   slot_free[s]  the gate's outputs left the slot (bulk stores read it)
 //   afull[a]      an item's A stage is written (four expander warps)
 //   afree[a]      the item's MMAs are done (commit)
 //   accfull[c]    an item's MMAs are done (commit)
 //   accfree[c]    the epilogue read the accumulator (eight warps)
+// Warps: 0 issuer, 1 producer, 2 3 16 17 converters (one per SM
+// sub-partition), 4..7 expanders, 8..15 epilogue.
 // ---------------------------------------------------------------------------
 template <int LL>
 __global__ void __launch_bounds__(kSmThreads, 1) k_gate_sm(KArgs a, SmShape t) {
+  constexpr uint32_t kEll = 32u * LL, kDig = 4u * LL;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* bars = (uint64_t*)(smem + t.nslots * t.slot_bytes);
+  SlotMeta* meta = (SlotMeta*)(smem + t.nslots * t.slot_bytes);
+  uint64_t* bars = (uint64_t*)(meta + kSmMaxSlots);
   uint64_t* raw_full = bars;
   uint64_t* img_full = bars + 8;
   uint64_t* epi_done = bars + 16;
@@ -240,7 +298,7 @@ __global__ void __launch_bounds__(kSmThreads, 1) k_gate_sm(KArgs a, SmShape t) {
   if (tid == 0) {
     for (uint32_t b = 0; b < kSmMaxSlots; b++) {
       mbar_init(&raw_full[b], 1u);
-      mbar_init(&img_full[b], kSmConvThreads / 32);
+      mbar_init(&img_full[b], kSmConvWarps);
       mbar_init(&epi_done[b], kSmEpiWarps);
       mbar_init(&slot_free[b], 1u);
       mbar_init(&accfull[b], 1u);
@@ -301,7 +359,13 @@ __global__ void __launch_bounds__(kSmThreads, 1) k_gate_sm(KArgs a, SmShape t) {
       for (uint32_t j = 0; j < nloc; j++) {
         const uint32_t s = j % t.nslots, use = j / t.nslots;
         if (use && !mbar_wait_flag(&slot_free[s], (use - 1) & 1u, sflag)) { ok = false; break; }
-        const GateDesc gd = a.desc[gate_of(j)];
+        const uint64_t g = gate_of(j);
+        const GateDesc gd = a.desc[g];
+        const GateAux ax = a.aux[g];
+        SlotMeta md;
+        md.a = gd.a; md.b = gd.b; md.o0 = gd.o0; md.o1 = gd.o1;
+        md.code = ax.code; md.flags = ax.flags; md.pad0 = md.pad1 = 0;
+        meta[s] = md;   // published by the arrival below (release)
         mbar_expect_tx(&raw_full[s], 2u * t.raw_bytes);
         bulk_g2s(araw_of(s), ct_ptr(a, gd.a), t.raw_bytes, &raw_full[s]);
         bulk_g2s(braw_of(s), ct_ptr(a, gd.b), t.raw_bytes, &raw_full[s]);
@@ -309,11 +373,12 @@ __global__ void __launch_bounds__(kSmThreads, 1) k_gate_sm(KArgs a, SmShape t) {
       if (!ok) *sflag = 1;
     }
 
-  } else if (warp >= kSmConvWarp0 && warp < kSmExpWarp0) {
+  } else if (warp == 2 || warp == 3 || warp == 16 || warp == 17) {
     // ----------------------------------------------------------- B converters
     // pair P = 16 w + c: rows k0 = 32 w + c and k0 + 16 of B' -> K positions
-    // 2P, 2P + 1 of every digit row n = e dig + t (one 32-bit store each)
-    const uint32_t ct = tid - kSmConvWarp0 * 32;
+    // 2P, 2P + 1 of every digit row n = e dig + t (one 32-bit store each; the
+    // eight swizzled row bases of the pair are formed once)
+    const uint32_t ct = (warp < 4 ? warp - 2u : warp - 14u) * 32u + lane;
     bool ok = true;
     for (uint32_t j = 0; j < nloc; j++) {
       const uint32_t s = j % t.nslots;
@@ -322,23 +387,28 @@ __global__ void __launch_bounds__(kSmThreads, 1) k_gate_sm(KArgs a, SmShape t) {
       uint8_t* img = img_of(s);
       for (uint32_t P = ct; P < Ng / 2; P += kSmConvThreads) {
         const uint32_t w = P >> 4, c = P & 15u;
-        const uint32_t* r0 = B + (32u * w + c) * W;
-        const uint32_t* r1 = r0 + 16u * W;
+        uint32_t x0[8], x1[8];
+        ld_row(B + (32u * w + c) * W, W, x0);
+        ld_row(B + (32u * w + c + 16u) * W, W, x1);
         const uint32_t f2 = b_factor(c);
-        const uint32_t p0 = 2u * P, atom = p0 >> 6, kin = p0 & 63u;
-        uint8_t* base = img + atom * (t.ncols * 128u) + (kin & 7u) * 2u;
-        const uint32_t chunk = kin >> 3;
-        for (uint32_t e = 0; e < NP1; e++) {
+        const uint32_t p0 = 2u * P, kin = p0 & 63u, chunk = kin >> 3;
+        uint8_t* base = img + (p0 >> 6) * (t.ncols * 128u) + (kin & 7u) * 2u;
+        uint8_t* rb[8];
 #pragma unroll
-          for (uint32_t wl = 0; wl < (uint32_t)LL; wl++) {
-            const uint32_t x0 = r0[e * LL + wl], x1 = r1[e * LL + wl];
+        for (uint32_t r = 0; r < 8; r++) rb[r] = base + r * 128u + ((chunk ^ r) << 4);
 #pragma unroll
-            for (uint32_t by = 0; by < 4; by++) {
-              const uint32_t n = e * t.dig + wl * 4u + by;
-              const uint32_t sel = by | (by << 4) | ((4u + by) << 8) | ((4u + by) << 12);
-              const uint32_t v = (__byte_perm(x0, x1, sel) & 0x00FF00FFu) | 0x64006400u;
-              const uint32_t h = hmul2(hsub2(v, 0x64006400u), f2);
-              *(uint32_t*)(base + (n >> 3) * 1024u + (n & 7u) * 128u + ((chunk ^ (n & 7u)) << 4)) = h;
+        for (uint32_t e = 0; e < 8u / LL; e++) {
+          if (e < NP1) {
+#pragma unroll
+            for (uint32_t wl = 0; wl < (uint32_t)LL; wl++) {
+#pragma unroll
+              for (uint32_t by = 0; by < 4; by++) {
+                const uint32_t n = e * kDig + wl * 4u + by;
+                const uint32_t sel = by | (by << 4) | ((4u + by) << 8) | ((4u + by) << 12);
+                const uint32_t v =
+                    (__byte_perm(x0[e * LL + wl], x1[e * LL + wl], sel) & 0x00FF00FFu) | 0x64006400u;
+                *(uint32_t*)(rb[n & 7u] + (n >> 3) * 1024u) = hmul2(hsub2(v, 0x64006400u), f2);
+              }
             }
           }
         }
@@ -362,13 +432,10 @@ __global__ void __launch_bounds__(kSmThreads, 1) k_gate_sm(KArgs a, SmShape t) {
       const uint32_t r0 = m * 128u + q * 32u;
       if (r0 < Ng) {   // warp-uniform: Ng is a multiple of 32
         const uint32_t i = r0 + lane;
-        const uint32_t* row = araw_of(s) + i * W;
-        const bool comp = (a.aux[gate_of(j)].flags & 1u) != 0;
         uint32_t x[8];
-#pragma unroll
-        for (uint32_t w = 0; w < 8; w++) x[w] = w < W ? row[w] : 0u;
-        if (comp) {   // P - A, borrows inside each element
-          const uint32_t pidx = (i / a.ell) * LL + (i % a.ell) / 32, pval = 1u << (i % 32);
+        ld_row(araw_of(s) + i * W, W, x);
+        if (meta[s].flags & 1u) {   // P - A, borrows inside each element
+          const uint32_t pidx = (i / kEll) * LL + (i % kEll) / 32, pval = 1u << (i % 32);
           uint32_t borrow = 0;
 #pragma unroll
           for (uint32_t w = 0; w < 8; w++) {
@@ -399,7 +466,7 @@ __global__ void __launch_bounds__(kSmThreads, 1) k_gate_sm(KArgs a, SmShape t) {
     }
     if (!ok && lane == 0) *sflag = 1;
 
-  } else if (warp >= kSmEpiWarp0) {
+  } else if (warp >= kSmEpiWarp0 && warp < kSmEpiWarp0 + kSmEpiWarps) {
     // -------------------------------------------------------------- epilogue
     // warp (q, h): rows 32 q .. 32 q + 31 of each item, elements h, h + 2, ...
     const uint32_t q = warp & 3u, h = (warp - kSmEpiWarp0) >> 2;
@@ -408,55 +475,63 @@ __global__ void __launch_bounds__(kSmThreads, 1) k_gate_sm(KArgs a, SmShape t) {
     uint32_t j = 0, m = 0, acc = 0, accph = 0;
     for (uint32_t it = 0; it < items; it++) {
       const uint32_t s = j % t.nslots;
-      const uint64_t g = gate_of(j);
+      // the slot's metadata was published with raw_full (still this gate's phase)
+      if (m == 0 && !warp_wait(&raw_full[s], (j / t.nslots) & 1u, sflag)) { ok = false; break; }
       if (!warp_wait(&accfull[acc], accph, sflag)) { ok = false; break; }
       tc_fence_after();
+      const SlotMeta md = meta[s];
       const uint32_t r0 = m * 128u + q * 32u;
       if (r0 < Ng) {
-        const uint32_t code = a.aux[g].code;
+        const uint32_t code = md.code;
+        const bool two = md.o1 != REF_NONE;
         const int c00 = nib(code, 0), c01 = nib(code, 1), c02 = nib(code, 2), c03 = nib(code, 3);
         const int c10 = nib(code, 4), c11 = nib(code, 5), c12 = nib(code, 6), c13 = nib(code, 7);
         // a term c x (c small, x < 2^32) is c (x - 2^31) + c 2^31: one signed
         // 32 x 32 -> 64 multiply-add, the constants summed once per output
         const int64_t bias0 = (int64_t)(c01 + c02 + c03) << 31, bias1 = (int64_t)(c11 + c12 + c13) << 31;
         const uint32_t i = r0 + lane;
-        const uint32_t pe = i / a.ell, pw = (i % a.ell) / 32;
+        const uint32_t pe = i / kEll, pw = (i % kEll) / 32;
         const int64_t pv = (int64_t)1 << (i % 32);
         uint32_t* Arow = araw_of(s) + i * W;
         uint32_t* Brow = braw_of(s) + i * W;
         const uint32_t taddr = tmem + ((q * 32u) << 16) + acc * t.ncols;
         for (uint32_t e = h; e < NP1; e += 2) {
           uint32_t v[16];
-          tmem_ld16(taddr + e * t.dig, v);
+          tmem_ld16(taddr + e * kDig, v);
+          uint32_t av[LL], bv[LL], o0[LL], o1[LL];
+          ld_elem<LL>(Arow + e * LL, av);
+          ld_elem<LL>(Brow + e * LL, bv);
           int32_t carry0 = 0, carry1 = 0;
 #pragma unroll
           for (uint32_t wl = 0; wl < (uint32_t)LL; wl++) {
             // K word = S0 + S1 2^8 + S2 2^16 + S3 2^24 (< 2^41), as lo + 2^32 hi
             const uint32_t s0 = acc_to_sum(v[4 * wl]), s1 = acc_to_sum(v[4 * wl + 1]);
             const uint32_t s2 = acc_to_sum(v[4 * wl + 2]), s3 = acc_to_sum(v[4 * wl + 3]);
-            const uint32_t lo01 = s0 + (s1 << 8), lo23 = s2 + (s3 << 8);   // each < 2^24
+            const uint32_t lo01 = s0 + (s1 << 8), lo23 = s2 + (s3 << 8);   // each < 2^25
             const uint64_t kk = (uint64_t)lo01 + ((uint64_t)lo23 << 16);
-            const uint32_t klo = (uint32_t)kk;
             const int32_t khi = (int32_t)(kk >> 32);
-            const uint32_t aw = Arow[e * LL + wl], bw = Brow[e * LL + wl];
-            const int32_t xa = (int32_t)(aw ^ 0x80000000u), xb = (int32_t)(bw ^ 0x80000000u);
-            const int32_t xk = (int32_t)(klo ^ 0x80000000u);
-            int64_t t0 = bias0 + carry0, t1 = bias1 + carry1;
+            const int32_t xa = (int32_t)(av[wl] ^ 0x80000000u), xb = (int32_t)(bv[wl] ^ 0x80000000u);
+            const int32_t xk = (int32_t)((uint32_t)kk ^ 0x80000000u);
+            const bool pat = e == pe && wl == pw;
+            int64_t t0 = bias0 + carry0;
             t0 += (int64_t)c01 * xa;
             t0 += (int64_t)c02 * xb;
             t0 += (int64_t)c03 * xk;
-            t1 += (int64_t)c11 * xa;
-            t1 += (int64_t)c12 * xb;
-            t1 += (int64_t)c13 * xk;
-            if (e == pe && wl == pw) {
-              t0 += c00 * pv;
-              t1 += c10 * pv;
-            }
+            if (pat) t0 += c00 * pv;
             carry0 = (int32_t)(t0 >> 32) + c03 * khi;
-            carry1 = (int32_t)(t1 >> 32) + c13 * khi;
-            Arow[e * LL + wl] = (uint32_t)t0;   // output 0 over A'
-            Brow[e * LL + wl] = (uint32_t)t1;   // output 1 over B'
+            o0[wl] = (uint32_t)t0;
+            if (two) {
+              int64_t t1 = bias1 + carry1;
+              t1 += (int64_t)c11 * xa;
+              t1 += (int64_t)c12 * xb;
+              t1 += (int64_t)c13 * xk;
+              if (pat) t1 += c10 * pv;
+              carry1 = (int32_t)(t1 >> 32) + c13 * khi;
+              o1[wl] = (uint32_t)t1;
+            }
           }
+          st_elem<LL>(Arow + e * LL, o0);   // output 0 over A'
+          if (two) st_elem<LL>(Brow + e * LL, o1);   // output 1 over B'
         }
       }
       tc_fence_before();
@@ -471,9 +546,8 @@ __global__ void __launch_bounds__(kSmThreads, 1) k_gate_sm(KArgs a, SmShape t) {
         bool bad = false;
         if (storer) {
           if (mbar_wait_flag(&epi_done[s], (j / t.nslots) & 1u, sflag)) {
-            const GateDesc gd = a.desc[g];
-            if (gd.o0 != REF_NONE) bulk_s2g(ct_ptr(a, gd.o0), araw_of(s), t.raw_bytes);
-            if (gd.o1 != REF_NONE) bulk_s2g(ct_ptr(a, gd.o1), braw_of(s), t.raw_bytes);
+            if (md.o0 != REF_NONE) bulk_s2g(ct_ptr(a, md.o0), araw_of(s), t.raw_bytes);
+            if (md.o1 != REF_NONE) bulk_s2g(ct_ptr(a, md.o1), braw_of(s), t.raw_bytes);
             bulk_commit();
             bulk_wait_read();
             mbar_arrive(&slot_free[s]);
@@ -514,7 +588,7 @@ namespace {
 constexpr uint32_t kSmDefaultSlots = 4;
 
 uint32_t sm_smem_bytes(uint32_t slot_bytes, uint32_t nslots) {
-  return 1024u + nslots * slot_bytes + kSmBars * 8u;
+  return 1024u + nslots * slot_bytes + kSmMaxSlots * 32u + kSmBars * 8u;   // + slot metadata
 }
 
 // nslots 0: the tuned or default ring depth.
@@ -632,3 +706,115 @@ int sm_set_tuned_slots(uint32_t L, uint32_t nslots) {
 }
 
 }  // namespace sfft
+
+// ---------------------------------------------------------------------------
+// Autotuner: ring depth (gates in flight per CTA) of the small-ciphertext
+// kernel, timed on one level of random products.
+// ---------------------------------------------------------------------------
+namespace sfft {
+
+namespace {
+
+__global__ void k_fill_random(uint32_t* p, uint64_t n, uint64_t seed) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;   // SplitMix64 finaliser
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    p[i] = (uint32_t)(z ^ (z >> 31));
+  }
+}
+
+struct DevBuf {
+  void* p = nullptr;
+  ~DevBuf() { cudaFree(p); }
+};
+
+}  // namespace
+
+}  // namespace sfft
+
+using namespace sfft;
+
+extern "C" int sfft_small_kernel_set_slots(uint32_t ell, uint32_t nslots) {
+  if (nslots == 1 || nslots > kSmMaxSlots) return fail(SFFT_EINVAL, "ring depth must be 0 or 2..8");
+  if (ell == 0 || ell % 32 || ell > 128) return fail(SFFT_EINVAL, "ell must be 32, 64, 96 or 128");
+  return sm_set_tuned_slots(ell / 32, nslots);
+}
+
+extern "C" int sfft_autotune_small(const sfft_params* p, uint64_t n_gates, uint32_t reps,
+                                   uint32_t* best_slots, double* h_us_per_gate) {
+  Shape s;
+  int rc = make_shape(p, &s, false);
+  if (rc) return rc;
+  KArgs a = make_args(s);
+  SmShape t;
+  if (!make_sm_shape(a, 0, &t)) return fail(SFFT_EPARAM, "the small-ciphertext kernel does not take these parameters");
+  if (n_gates == 0 || n_gates > (1u << 24)) return fail(SFFT_EINVAL, "n_gates must be 1 .. 2^24");
+  if (reps == 0) reps = 3;
+  const uint64_t words = n_gates * s.ctw;
+  DevBuf ab, bb, o0, o1, dd, da, de;
+  std::vector<GateDesc> desc(n_gates);
+  std::vector<GateAux> aux(n_gates);
+  for (uint64_t g = 0; g < n_gates; g++) {   // half adders, every other A complemented
+    desc[g] = GateDesc{make_ref(REG_SCRATCH, (uint32_t)g), make_ref(REG_IN, (uint32_t)g),
+                       make_ref(REG_OUT, (uint32_t)g), make_ref(REG_GEN, (uint32_t)g)};
+    aux[g].code = (uint32_t)pack_code(0, 1, 1, -2) | ((uint32_t)pack_code(0, 0, 0, 1) << 16);
+    aux[g].flags = g & 1u;
+  }
+  cudaError_t e = cudaMalloc(&ab.p, words * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&bb.p, words * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&o0.p, words * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&o1.p, words * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&de.p, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(de.p, 0, sizeof(int));
+  if (e != cudaSuccess) return cuda_fail(e, "autotune buffers");
+  if ((rc = upload(desc.data(), desc.size() * sizeof(GateDesc), &dd.p))) return rc;
+  if ((rc = upload(aux.data(), aux.size() * sizeof(GateAux), &da.p))) return rc;
+  k_fill_random<<<1024, 256>>>((uint32_t*)ab.p, words, 1);
+  k_fill_random<<<1024, 256>>>((uint32_t*)bb.p, words, 2);
+  a.desc = (const GateDesc*)dd.p;
+  a.aux = (const GateAux*)da.p;
+  a.n = n_gates;
+  a.base[REG_SCRATCH] = (uint32_t*)ab.p;
+  a.base[REG_IN] = (uint32_t*)bb.p;
+  a.base[REG_OUT] = (uint32_t*)o0.p;
+  a.base[REG_GEN] = (uint32_t*)o1.p;
+  a.err = (int*)de.p;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  double best = 0;
+  uint32_t best_ns = 0;
+  for (uint32_t ns = 2; ns <= kSmMaxSlots; ns++) {
+    if (h_us_per_gate) h_us_per_gate[ns - 1] = 0;
+    SmShape c;
+    if (!make_sm_shape(a, ns, &c) || c.nslots != ns) continue;
+    if ((rc = launch_gates_sm_slots(a, ns, 0))) break;   // warm-up
+    double ms_min = 1e30;
+    for (uint32_t r = 0; r < reps && !rc; r++) {
+      cudaEventRecord(e0, 0);
+      rc = launch_gates_sm_slots(a, ns, 0);
+      cudaEventRecord(e1, 0);
+      cudaEventSynchronize(e1);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ms_min = std::min<double>(ms_min, ms);
+    }
+    if (rc) break;
+    const double us = ms_min * 1000.0 / (double)n_gates;
+    if (h_us_per_gate) h_us_per_gate[ns - 1] = us;
+    if (!best_ns || us < best) {
+      best = us;
+      best_ns = ns;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  e = cudaDeviceSynchronize();
+  if (!rc && e != cudaSuccess) rc = cuda_fail(e, "autotune");
+  if (!rc) rc = check_device_error(a.err, 0);
+  if (rc) return rc;
+  if (best_slots) *best_slots = best_ns;
+  return sm_set_tuned_slots(s.L, best_ns);
+}

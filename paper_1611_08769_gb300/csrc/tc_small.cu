@@ -21,9 +21,11 @@
 // product is d * 2^-6 exactly and the fp32 accumulator holds S * 2^-6, a
 // multiple of 2^-6 below 2^10: exact. The K order is the same permutation on
 // both sides (K position 32 w + 2 c + h is bit 32 w + c + 16 h of the row).
-// The epilogue reads S back by adding 2^17 (whose ulp is 2^-6), forms each
-// 32-bit word of K from four digit sums and adds c0 P + c1 A + c2 B with the
-// element's limb carries, as the integer kernel does.
+// Every accumulator starts at 2^17 (its ulp is 2^-6), so its bits after the
+// MMAs are those of 2^17 plus the integer S; the epilogue forms each 32-bit
+// word of K from four such digit sums and adds c0 P + c1 A + c2 B with the
+// element's limb carries, as the integer kernel does (half adders and ORs,
+// the codes the circuits mostly use, by shorter dedicated carry chains).
 //
 // Roles (one persistent CTA of 18 warps per SM; CTA b takes the gates b,
 // b + grid, ...; a gate is one or two 128-row items):
@@ -168,12 +170,6 @@ __device__ __forceinline__ uint32_t hmul2(uint32_t a, uint32_t b) {
   return r;
 }
 
-// Digit sum S from the accumulator value S * 2^-6 (S < 2^16): S * 2^-6 + 2^17
-// is exact and its significand field is S.
-__device__ __forceinline__ uint32_t acc_to_sum(uint32_t bits) {
-  return __float_as_uint(__fadd_rn(__uint_as_float(bits), 131072.0f)) - 0x48000000u;
-}
-
 }  // namespace
 
 struct SmShape {
@@ -195,8 +191,27 @@ struct SmShape {
 // Slot metadata: the gate's descriptor, written by the producer with its
 // bulk copies (visible to every role once raw_full completes).
 struct SlotMeta {
-  uint32_t a, b, o0, o1, code, flags, pad0, pad1;
+  uint32_t a, b, o0, o1, code, flags, kind, pad;
 };
+
+// Gate kinds with a specialised epilogue (codes as stored, after the
+// compiler absorbed complemented operands): a half adder (output 0 XOR =
+// A + B - 2K, output 1 AND = K), an OR (A + B - K); every other code runs the
+// general form.
+constexpr uint32_t kKindGeneric = 0, kKindHA = 1, kKindOR = 2;
+constexpr uint32_t kCodeXOR = 0xE110u, kCodeAND = 0x1000u, kCodeOR = 0xF110u;
+
+// Every accumulator starts at 2^17 (fp32 bits 0x48000000) instead of 0, so
+// that its bits after the MMAs are 0x48000000 + S for a digit sum S (S 2^-6
+// < 2^17 keeps the ulp at 2^-6): K words are assembled from the raw bits and
+// the bias of the four digits of a word, 0x48000000 (1 + 2^16) after the
+// byte shifts (the 2^8 and 2^24 copies wrap out of 32 bits), leaves once.
+constexpr uint32_t kAccBiasBits = 0x48000000u;
+constexpr uint64_t kWordBias = 0x480048000000ull;
+
+__device__ __forceinline__ void tmem_st_x4(uint32_t taddr, uint32_t v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%1,%1,%1};" ::"r"(taddr), "r"(v) : "memory");
+}
 
 // Rows of LL-limb elements: aligned vector access where the limb count
 // allows (16-byte for 4 limbs, 8-byte for 2), word by word otherwise.
@@ -326,7 +341,7 @@ __global__ void __launch_bounds__(kSmThreads, 1) k_gate_sm(KArgs a, SmShape t) {
     uint32_t j = 0, m = 0, st = 0, stph = 0, acc = 0, accph = 0;
     for (uint32_t it = 0; it < items; it++) {
       const uint32_t s = j % t.nslots;
-      if (it >= t.nacc && !warp_wait(&accfree[acc], accph ^ 1u, sflag)) { ok = false; break; }
+      if (!warp_wait(&accfree[acc], accph, sflag)) { ok = false; break; }
       if (!warp_wait(&afull[st], stph, sflag)) { ok = false; break; }
       if (m == 0 && !warp_wait(&img_full[s], (j / t.nslots) & 1u, sflag)) { ok = false; break; }
       tc_fence_after();
@@ -337,10 +352,10 @@ __global__ void __launch_bounds__(kSmThreads, 1) k_gate_sm(KArgs a, SmShape t) {
       for (uint32_t atom = 0; atom < t.atoms; atom++) {
         const uint64_t bd = b0 + (uint64_t)atom * atom_units;
         if (k + 4 <= t.ksteps) {
-          mma_atom4(d, at + 8u * k, bd, idesc, k);
+          mma_atom4(d, at + 8u * k, bd, idesc, 1u);
           k += 4;
         } else {
-          for (uint32_t q = 0; k < t.ksteps; q++, k++) mma_one(d, at + 8u * k, bd + 2u * q, idesc, k);
+          for (uint32_t q = 0; k < t.ksteps; q++, k++) mma_one(d, at + 8u * k, bd + 2u * q, idesc, 1u);
         }
       }
       mma_commit_elected(&afree[st]);
@@ -364,7 +379,10 @@ __global__ void __launch_bounds__(kSmThreads, 1) k_gate_sm(KArgs a, SmShape t) {
         const GateAux ax = a.aux[g];
         SlotMeta md;
         md.a = gd.a; md.b = gd.b; md.o0 = gd.o0; md.o1 = gd.o1;
-        md.code = ax.code; md.flags = ax.flags; md.pad0 = md.pad1 = 0;
+        md.code = ax.code; md.flags = ax.flags; md.pad = 0;
+        const uint32_t c0 = ax.code & 0xFFFFu, c1 = ax.code >> 16;
+        md.kind = (c0 == kCodeXOR && c1 == kCodeAND) ? kKindHA
+                  : (c0 == kCodeOR && gd.o1 == REF_NONE) ? kKindOR : kKindGeneric;
         meta[s] = md;   // published by the arrival below (release)
         mbar_expect_tx(&raw_full[s], 2u * t.raw_bytes);
         bulk_g2s(araw_of(s), ct_ptr(a, gd.a), t.raw_bytes, &raw_full[s]);
@@ -471,6 +489,19 @@ __global__ void __launch_bounds__(kSmThreads, 1) k_gate_sm(KArgs a, SmShape t) {
     // warp (q, h): rows 32 q .. 32 q + 31 of each item, elements h, h + 2, ...
     const uint32_t q = warp & 3u, h = (warp - kSmEpiWarp0) >> 2;
     const bool storer = warp == kSmEpiWarp0 && lane == 0;
+    const uint32_t tlane = tmem + ((q * 32u) << 16);
+    // every accumulator slot starts at the bias (this warp's lanes and
+    // elements); the arrival frees each slot for its first item
+    for (uint32_t c = 0; c < t.nacc; c++) {
+      for (uint32_t e = h; e < NP1; e += 2)
+#pragma unroll
+        for (uint32_t k = 0; k < (uint32_t)LL; k++) tmem_st_x4(tlane + c * t.ncols + e * kDig + 4u * k, kAccBiasBits);
+    }
+    tmem_wait_st();
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0)
+      for (uint32_t c = 0; c < t.nacc; c++) mbar_arrive(&accfree[c]);
     bool ok = true;
     uint32_t j = 0, m = 0, acc = 0, accph = 0;
     for (uint32_t it = 0; it < items; it++) {
@@ -481,46 +512,68 @@ __global__ void __launch_bounds__(kSmThreads, 1) k_gate_sm(KArgs a, SmShape t) {
       tc_fence_after();
       const SlotMeta md = meta[s];
       const uint32_t r0 = m * 128u + q * 32u;
+      const uint32_t taddr = tlane + acc * t.ncols;
       if (r0 < Ng) {
-        const uint32_t code = md.code;
-        const bool two = md.o1 != REF_NONE;
-        const int c00 = nib(code, 0), c01 = nib(code, 1), c02 = nib(code, 2), c03 = nib(code, 3);
-        const int c10 = nib(code, 4), c11 = nib(code, 5), c12 = nib(code, 6), c13 = nib(code, 7);
-        // a term c x (c small, x < 2^32) is c (x - 2^31) + c 2^31: one signed
-        // 32 x 32 -> 64 multiply-add, the constants summed once per output
-        const int64_t bias0 = (int64_t)(c01 + c02 + c03) << 31, bias1 = (int64_t)(c11 + c12 + c13) << 31;
+        const bool one = md.o0 != REF_NONE, two = md.o1 != REF_NONE;
         const uint32_t i = r0 + lane;
-        const uint32_t pe = i / kEll, pw = (i % kEll) / 32;
-        const int64_t pv = (int64_t)1 << (i % 32);
         uint32_t* Arow = araw_of(s) + i * W;
         uint32_t* Brow = braw_of(s) + i * W;
-        const uint32_t taddr = tmem + ((q * 32u) << 16) + acc * t.ncols;
         for (uint32_t e = h; e < NP1; e += 2) {
           uint32_t v[16];
           tmem_ld16(taddr + e * kDig, v);
           uint32_t av[LL], bv[LL], o0[LL], o1[LL];
           ld_elem<LL>(Arow + e * LL, av);
           ld_elem<LL>(Brow + e * LL, bv);
-          int32_t carry0 = 0, carry1 = 0;
+          // K words, unnormalised: S0 + S1 2^8 + S2 2^16 + S3 2^24 < 2^41
+          uint64_t kw[LL];
 #pragma unroll
           for (uint32_t wl = 0; wl < (uint32_t)LL; wl++) {
-            // K word = S0 + S1 2^8 + S2 2^16 + S3 2^24 (< 2^41), as lo + 2^32 hi
-            const uint32_t s0 = acc_to_sum(v[4 * wl]), s1 = acc_to_sum(v[4 * wl + 1]);
-            const uint32_t s2 = acc_to_sum(v[4 * wl + 2]), s3 = acc_to_sum(v[4 * wl + 3]);
-            const uint32_t lo01 = s0 + (s1 << 8), lo23 = s2 + (s3 << 8);   // each < 2^25
-            const uint64_t kk = (uint64_t)lo01 + ((uint64_t)lo23 << 16);
-            const int32_t khi = (int32_t)(kk >> 32);
-            const int32_t xa = (int32_t)(av[wl] ^ 0x80000000u), xb = (int32_t)(bv[wl] ^ 0x80000000u);
-            const int32_t xk = (int32_t)((uint32_t)kk ^ 0x80000000u);
-            const bool pat = e == pe && wl == pw;
-            int64_t t0 = bias0 + carry0;
-            t0 += (int64_t)c01 * xa;
-            t0 += (int64_t)c02 * xb;
-            t0 += (int64_t)c03 * xk;
-            if (pat) t0 += c00 * pv;
-            carry0 = (int32_t)(t0 >> 32) + c03 * khi;
-            o0[wl] = (uint32_t)t0;
-            if (two) {
+            const uint32_t lo01 = v[4 * wl] + (v[4 * wl + 1] << 8), lo23 = v[4 * wl + 2] + (v[4 * wl + 3] << 8);
+            kw[wl] = (uint64_t)lo01 + ((uint64_t)lo23 << 16) - kWordBias;
+          }
+          if (md.kind == kKindHA) {   // XOR = A + B - 2K, AND = K
+            int64_t cx = 0;
+            uint64_t ca = 0;
+#pragma unroll
+            for (uint32_t wl = 0; wl < (uint32_t)LL; wl++) {
+              const int64_t tx = (int64_t)av[wl] + (int64_t)bv[wl] - 2 * (int64_t)kw[wl] + cx;
+              o0[wl] = (uint32_t)tx;
+              cx = tx >> 32;
+              const uint64_t ta = kw[wl] + ca;
+              o1[wl] = (uint32_t)ta;
+              ca = ta >> 32;
+            }
+          } else if (md.kind == kKindOR) {   // A + B - K
+            int64_t co = 0;
+#pragma unroll
+            for (uint32_t wl = 0; wl < (uint32_t)LL; wl++) {
+              const int64_t to = (int64_t)av[wl] + (int64_t)bv[wl] - (int64_t)kw[wl] + co;
+              o0[wl] = (uint32_t)to;
+              co = to >> 32;
+            }
+          } else {
+            const uint32_t code = md.code;
+            const int c00 = nib(code, 0), c01 = nib(code, 1), c02 = nib(code, 2), c03 = nib(code, 3);
+            const int c10 = nib(code, 4), c11 = nib(code, 5), c12 = nib(code, 6), c13 = nib(code, 7);
+            // a term c x (c small, x < 2^32) is c (x - 2^31) + c 2^31: one signed
+            // 32 x 32 -> 64 multiply-add, the constants summed once per output
+            const int64_t bias0 = (int64_t)(c01 + c02 + c03) << 31, bias1 = (int64_t)(c11 + c12 + c13) << 31;
+            const uint32_t pe = i / kEll, pw = (i % kEll) / 32;
+            const int64_t pv = (int64_t)1 << (i % 32);
+            int32_t carry0 = 0, carry1 = 0;
+#pragma unroll
+            for (uint32_t wl = 0; wl < (uint32_t)LL; wl++) {
+              const int32_t khi = (int32_t)(kw[wl] >> 32);
+              const int32_t xa = (int32_t)(av[wl] ^ 0x80000000u), xb = (int32_t)(bv[wl] ^ 0x80000000u);
+              const int32_t xk = (int32_t)((uint32_t)kw[wl] ^ 0x80000000u);
+              const bool pat = e == pe && wl == pw;
+              int64_t t0 = bias0 + carry0;
+              t0 += (int64_t)c01 * xa;
+              t0 += (int64_t)c02 * xb;
+              t0 += (int64_t)c03 * xk;
+              if (pat) t0 += c00 * pv;
+              carry0 = (int32_t)(t0 >> 32) + c03 * khi;
+              o0[wl] = (uint32_t)t0;
               int64_t t1 = bias1 + carry1;
               t1 += (int64_t)c11 * xa;
               t1 += (int64_t)c12 * xb;
@@ -530,10 +583,16 @@ __global__ void __launch_bounds__(kSmThreads, 1) k_gate_sm(KArgs a, SmShape t) {
               o1[wl] = (uint32_t)t1;
             }
           }
-          st_elem<LL>(Arow + e * LL, o0);   // output 0 over A'
+          if (one) st_elem<LL>(Arow + e * LL, o0);   // output 0 over A'
           if (two) st_elem<LL>(Brow + e * LL, o1);   // output 1 over B'
         }
       }
+      // the slot's next item starts again from the bias (every warp, its own
+      // lanes and elements, whether or not its rows were live)
+      for (uint32_t e = h; e < NP1; e += 2)
+#pragma unroll
+        for (uint32_t k = 0; k < (uint32_t)LL; k++) tmem_st_x4(taddr + e * kDig + 4u * k, kAccBiasBits);
+      tmem_wait_st();
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&accfree[acc]);

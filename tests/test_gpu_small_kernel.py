@@ -80,6 +80,38 @@ def test_small_kernel_gate_level_matches_oracle(n, ell, G):
             assert np.array_equal(got1[g], _oracle_gate(p, A[g], B[g], _unpack(code1[g]), comp)), g
 
 
+@pytest.mark.parametrize("kind", ["ha", "or"])
+def test_small_kernel_half_adder_and_or_gates(kind):
+    """The codes the FFT circuits mostly use (half adder: XOR and AND from one
+    product; OR alone), with and without a complemented A, against the oracle."""
+    n, ell, G = 1, 128, 400
+    p = gsw.Params(n, ell, (n + 1) * ell, 0)
+    shape = (G, p.Ng, n + 1, p.L)
+    rng = np.random.default_rng(17 if kind == "ha" else 18)
+    A = rng.integers(0, 2**32, size=shape, dtype=np.uint64).astype(np.uint32)
+    B = rng.integers(0, 2**32, size=shape, dtype=np.uint64).astype(np.uint32)
+    A[3] = 0xFFFFFFFF   # maximal digit sums in one gate
+    B[3] = 0xFFFFFFFF
+    xor, and_, or_ = (0, 1, 1, -2), (0, 0, 0, 1), (0, 1, 1, -1)
+    c0 = xor if kind == "ha" else or_
+    code0 = [sf.pack_code(*c0)] * G
+    code1 = [sf.pack_code(*and_)] * G
+    flags = [(g % 2) | (2 if kind == "ha" else 0) for g in range(G)]
+    dA, dB = dev(A), dev(B)
+    o0 = torch.full_like(dA, -1)
+    o1 = torch.full_like(dA, -1)
+    sf.gate_level(sf.Params(n, ell), dA, dB, o0, o1, code0, code1, flags, kernel=sf.KERNEL_SM)
+    torch.cuda.synchronize()
+    got0, got1 = host(o0, shape), host(o1, shape)
+    for g in range(G):
+        comp = bool(flags[g] & 1)
+        assert np.array_equal(got0[g], _oracle_gate(p, A[g], B[g], c0, comp)), g
+        if kind == "ha":
+            assert np.array_equal(got1[g], _oracle_gate(p, A[g], B[g], and_, comp)), g
+        else:
+            assert (got1[g] == 0xFFFFFFFF).all()   # no second output written
+
+
 def test_small_kernel_extreme_digit_sums():
     """All-ones operands: every digit sum reaches Ng * 255 (the exactness bound)."""
     p, A, B, code0, code1, flags, got0, got1 = _run_level(1, 128, 160, sf.KERNEL_SM, 1, extreme=True)

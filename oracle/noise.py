@@ -17,20 +17,31 @@ from . import gsw
 from .evaluate import operands
 
 
+def fresh_bound(p):
+    """Noise bound of a fresh encryption R A + mu P: R e with R binary, m chi."""
+    return p.m * p.chi
+
+
+def gate_bound(code, EA, EB, Ng):
+    """Noise bound of the compressed gate (c0, c1, c2, c3) on operands with
+    bounds EA (the bit-decomposed operand A) and EB."""
+    c0, c1, c2, c3 = code
+    return (abs(c1) + abs(c3)) * EA + (abs(c2) + abs(c3) * Ng) * EB
+
+
 def wire_bounds(c, p):
     """Exact integer noise bound of every wire (list indexed by wire)."""
     E = [0] * len(c.depth)
     for w in c.inputs:
-        E[w] = p.m * p.chi
+        E[w] = fresh_bound(p)
 
     def get(w):
         return 0 if w < 0 else E[w]
 
     for op, a, b, o in c.gates:
-        c0, c1, c2, c3 = gsw.GATE_CODES[op]
         A, B = operands(c, a, b)
         EB = 0 if B is None else get(B)
-        E[o] = (abs(c1) + abs(c3)) * get(A) + (abs(c2) + abs(c3) * p.Ng) * EB
+        E[o] = gate_bound(gsw.GATE_CODES[op], get(A), EB, p.Ng)
     return E
 
 

@@ -272,6 +272,30 @@ int sfft_eval_fft(sfft_plan* plan, const uint32_t* d_in, uint32_t* d_out,
  * last check (the kernel then skipped its outputs and released its TMEM). */
 int sfft_plan_check(sfft_plan* plan, void* stream);
 
+/* Test hooks for parity at full size (the scope's sampled-gate check: gates
+ * across all levels recomputed on a CPU from the GPU's own stored inputs).
+ * sfft_eval_levels runs levels [l0, l1) of the plan's program (each level's
+ * products, then its linear gates) on the caller's buffers, as sfft_eval_fft
+ * does for the whole range, and the output fix-ups when l1 is the level
+ * count; EINVAL unless l0 <= l1 <= levels. A level's gates read only slots
+ * written by earlier levels and never write a slot the level reads, so a
+ * caller may copy a gate's inputs out of the buffers before running its level
+ * and its outputs after. sfft_plan_level returns level `level`'s gates in
+ * launch order (products first, then linear gates; *n_products of them are
+ * products): h_desc gets 4 words per gate (A, B, output 0, output 1), each
+ * a reference with the region in bits 31..30 (0 scratch slot, 1 input, 2
+ * output) and the ciphertext index in bits 29..0, 0xFFFFFFFF for an absent
+ * output; ciphertext index x of a region starts at word x * sfft_ct_words of
+ * its buffer. h_code gets code0 | code1 << 16 (each packs the signed nibbles
+ * c0 | c1 << 4 | c2 << 8 | c3 << 12 of out = c0 P + c1 A + c2 B + c3
+ * BitDecomp(A~) B, mod 2^ell), h_flags bit 0 = A~ is P - A (else A). With
+ * every array NULL only the counts are written; otherwise cap must be at
+ * least the level's gate count (EINVAL). */
+int sfft_eval_levels(sfft_plan* plan, uint32_t l0, uint32_t l1, const uint32_t* d_in, uint32_t* d_out,
+                     uint32_t* d_scratch, uint64_t scratch_bytes, void* stream);
+int sfft_plan_level(const sfft_plan* plan, uint32_t level, uint32_t* h_desc, uint32_t* h_code,
+                    uint8_t* h_flags, uint64_t cap, uint64_t* n_gates, uint64_t* n_products);
+
 /* Same, end to end from host buffers: copies h_in to d_in, evaluates, copies
  * d_out to h_out and waits for the stream. Pinned host memory is fastest. */
 int sfft_eval_fft_host(sfft_plan* plan, const uint32_t* h_in, uint32_t* h_out,

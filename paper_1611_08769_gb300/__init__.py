@@ -297,6 +297,27 @@ class Plan:
         check(lib().sfft_eval_fft(self._h, _dptr(d_in), _dptr(d_out), _dptr(d_scratch), nbytes,
                                   _stream(stream)))
 
+    def eval_levels(self, l0, l1, d_in, d_out, d_scratch, stream=None):
+        """Levels [l0, l1) of the program (sfft_eval_levels, a test hook)."""
+        nbytes = 0 if d_scratch is None else d_scratch.numel() * d_scratch.element_size()
+        check(lib().sfft_eval_levels(self._h, l0, l1, _dptr(d_in), _dptr(d_out), _dptr(d_scratch),
+                                     nbytes, _stream(stream)))
+
+    def level(self, level):
+        """Gates of one level (sfft_plan_level): (desc (n, 4) uint32 references
+        A, B, output 0, output 1; code (n,) uint32; flags (n,) uint8; products)."""
+        n, npr = ctypes.c_uint64(0), ctypes.c_uint64(0)
+        check(lib().sfft_plan_level(self._h, level, None, None, None, 0, ctypes.byref(n),
+                                    ctypes.byref(npr)))
+        desc = np.zeros((max(1, n.value), 4), dtype=np.uint32)
+        code = np.zeros(max(1, n.value), dtype=np.uint32)
+        flags = np.zeros(max(1, n.value), dtype=np.uint8)
+        check(lib().sfft_plan_level(self._h, level, desc.ctypes.data_as(native.c_u32_p),
+                                    code.ctypes.data_as(native.c_u32_p),
+                                    flags.ctypes.data_as(native.c_u8_p), n.value, ctypes.byref(n),
+                                    ctypes.byref(npr)))
+        return desc[:n.value], code[:n.value], flags[:n.value], int(npr.value)
+
     def eval_fft_host(self, h_in, h_out, d_in, d_out, d_scratch, stream=None):
         nbytes = 0 if d_scratch is None else d_scratch.numel() * d_scratch.element_size()
         check(lib().sfft_eval_fft_host(self._h, _dptr(h_in), _dptr(h_out), _dptr(d_in),

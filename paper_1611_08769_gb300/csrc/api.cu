@@ -132,7 +132,15 @@ Timer::~Timer() {
 
 int run_program(const Shape& s, const DeviceProgram& dp, const uint32_t* d_in, uint32_t* d_out,
                 uint32_t* d_scratch, uint64_t scratch_bytes, cudaStream_t st, Timer* tm) {
+  const uint32_t levels = (uint32_t)(dp.level_off.size() - 1);
+  return run_levels(s, dp, 0, levels, d_in, d_out, d_scratch, scratch_bytes, st, tm);
+}
+
+int run_levels(const Shape& s, const DeviceProgram& dp, uint32_t l0, uint32_t l1, const uint32_t* d_in,
+               uint32_t* d_out, uint32_t* d_scratch, uint64_t scratch_bytes, cudaStream_t st, Timer* tm) {
   if (!d_in || !d_out) return fail(SFFT_EINVAL, "null buffer");
+  const uint32_t levels = (uint32_t)(dp.level_off.size() - 1);
+  if (l0 > l1 || l1 > levels) return fail(SFFT_EINVAL, "level range out of bounds");
   if (scratch_bytes < dp.scratch_bytes || (dp.scratch_bytes && !d_scratch))
     return fail(SFFT_EINVAL, "scratch buffer too small");
   KArgs a = make_args(s);
@@ -143,7 +151,7 @@ int run_program(const Shape& s, const DeviceProgram& dp, const uint32_t* d_in, u
   a.base[REG_GEN] = nullptr;
   a.err = dp.err;
   a.kernel = dp.kernel;
-  for (size_t l = 0; l + 1 < dp.level_off.size(); l++) {
+  for (size_t l = l0; l < l1; l++) {
     const uint64_t mid = dp.lin_start[l];
     a.desc = dp.desc + dp.level_off[l];
     a.aux = dp.aux + dp.level_off[l];
@@ -162,7 +170,7 @@ int run_program(const Shape& s, const DeviceProgram& dp, const uint32_t* d_in, u
     a.n = dp.level_off[l + 1] - mid;
     if ((rc = launch_linear(a, st))) return rc;
   }
-  return launch_fixups(dp.fix, dp.n_fix, a, st);
+  return l1 == levels ? launch_fixups(dp.fix, dp.n_fix, a, st) : SFFT_OK;
 }
 
 int launch_linear(const KArgs& a, cudaStream_t st) {
@@ -470,6 +478,38 @@ int sfft_eval_fft_host(sfft_plan* pl, const uint32_t* h_in, uint32_t* h_out, uin
 int sfft_plan_check(sfft_plan* pl, void* stream) {
   if (!pl) return fail(SFFT_EINVAL, "plan is NULL");
   return check_device_error(pl->dev.err, (cudaStream_t)stream);
+}
+
+int sfft_eval_levels(sfft_plan* pl, uint32_t l0, uint32_t l1, const uint32_t* d_in, uint32_t* d_out,
+                     uint32_t* d_scratch, uint64_t scratch_bytes, void* stream) {
+  if (!pl) return fail(SFFT_EINVAL, "plan is NULL");
+  if (pl->dev.n_patch) return fail(SFFT_EINVAL, "a refresh plan runs through sfft_refresh");
+  return run_levels(pl->s, pl->dev, l0, l1, d_in, d_out, d_scratch, scratch_bytes, (cudaStream_t)stream,
+                    nullptr);
+}
+
+int sfft_plan_level(const sfft_plan* pl, uint32_t level, uint32_t* h_desc, uint32_t* h_code,
+                    uint8_t* h_flags, uint64_t cap, uint64_t* n_gates, uint64_t* n_products) {
+  if (!pl || !n_gates) return fail(SFFT_EINVAL, "null argument");
+  const Program& p = pl->prog;
+  if (level + 1 >= p.level_off.size()) return fail(SFFT_EINVAL, "level out of range");
+  const uint64_t g0 = p.level_off[level], g1 = p.level_off[level + 1];
+  *n_gates = g1 - g0;
+  if (n_products) *n_products = p.lin_start[level] - g0;
+  if (!h_desc && !h_code && !h_flags) return SFFT_OK;
+  if (cap < g1 - g0) return fail(SFFT_EINVAL, "arrays too small for the level");
+  for (uint64_t g = g0; g < g1; g++) {
+    const GateDesc& d = p.desc[g];
+    if (h_desc) {
+      h_desc[4 * (g - g0)] = d.a;
+      h_desc[4 * (g - g0) + 1] = d.b;
+      h_desc[4 * (g - g0) + 2] = d.o0;
+      h_desc[4 * (g - g0) + 3] = d.o1;
+    }
+    if (h_code) h_code[g - g0] = p.aux[g].code;
+    if (h_flags) h_flags[g - g0] = (uint8_t)(p.aux[g].flags & 0xFFu);
+  }
+  return SFFT_OK;
 }
 
 int sfft_gate_level(const sfft_params* p, const uint32_t* d_a, const uint32_t* d_b,

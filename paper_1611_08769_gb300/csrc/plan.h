@@ -95,6 +95,10 @@ struct Timer {
 
 int run_program(const Shape& s, const DeviceProgram& dp, const uint32_t* d_in, uint32_t* d_out,
                 uint32_t* d_scratch, uint64_t scratch_bytes, cudaStream_t st, Timer* tm = nullptr);
+// Levels [l0, l1) of a program (the output fix-ups too when l1 is the last).
+int run_levels(const Shape& s, const DeviceProgram& dp, uint32_t l0, uint32_t l1, const uint32_t* d_in,
+               uint32_t* d_out, uint32_t* d_scratch, uint64_t scratch_bytes, cudaStream_t st,
+               Timer* tm = nullptr);
 
 }  // namespace sfft
 

@@ -75,6 +75,8 @@ SIGNATURES = {
     "sfft_refresh": (c_i32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_u64, c_void_p]),
     "sfft_refresh_circuit_info": (c_i32, [P(sfft_params), c_u64, c_u32, P(sfft_plan_info)]),
     "sfft_refresh_eval_plain": (c_i32, [P(sfft_params), c_u64, c_u32, c_u8_p, c_u32_p, c_u8_p]),
+    "sfft_eval_levels": (c_i32, [c_void_p, c_u32, c_u32, c_void_p, c_void_p, c_void_p, c_u64, c_void_p]),
+    "sfft_plan_level": (c_i32, [c_void_p, c_u32, c_u32_p, c_u32_p, c_u8_p, c_u64, P(c_u64), P(c_u64)]),
     "sfft_autotune_small": (c_i32, [P(sfft_params), c_u64, c_u32, c_u32_p, c_double_p]),
     "sfft_small_kernel_set_slots": (c_i32, [c_u32, c_u32]),
     "sfft_gate_level_withheld": (c_i32, [P(sfft_params), c_void_p, c_void_p, c_void_p, c_u16_p,

@@ -22,6 +22,14 @@ multiplier, exclusive-carry adders), refresh32_noisy (refresh by homomorphic
 decryption of 32 ciphertexts at the default workload's ell; metric:
 refreshed ciphertexts/s).
 
+The default run (no --config) adds two blocks measured on the same box
+after the headline: "batch" (batch256_p2, the level-merged batch of 256
+requests replayed as a graph against the plain per-request evaluator, with
+its roofline and the autotuned ring depth of the small-ciphertext kernel) and
+"serve" (serve_p2: Poisson arrivals at 0.8x the measured closed-burst
+capacity into the continuous-batching server, p50/p99 latency); --no-extra
+skips them.
+
 Keys beyond the base contract:
   roofline      the gate-product kernel against its peak (tensor or ALU)
   cpu_baseline  the CPU oracle on a bounded prefix of the same circuit
@@ -46,10 +54,20 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# INT32 ALU peak of one GB300: 152 SMs x 128 INT32 lanes x 2.07 GHz (one
-# 32-bit add or logic op per lane per clock).
-SMS, INT_LANES, SM_MAX_GHZ = 152, 128, 2.070
-ALU_PEAK_OPS = SMS * INT_LANES * SM_MAX_GHZ * 1e9
+# Integer-pipe rates measured on this GPU by the library's microbenchmark
+# (sfft_measure_int_peak: add.u32, lop3, mad.lo, popc; ops/s), filled once
+# per process by int_peaks(); the integer kernel's roofline is taken against
+# the measured add rate.
+_INT_PEAKS = {}
+
+
+def int_peaks(sf):
+    if not _INT_PEAKS:
+        for name in sf.INT_PEAK_OPS:
+            _INT_PEAKS[name] = sf.measure_int_peak(name)
+    return dict(_INT_PEAKS)
+
+DEFAULT_CONFIG = "fft64_16bit_noisy"
 
 CONFIGS = {
     # single-request FFTs: (N1, N2, F, f, lo, hi, parameter set)
@@ -79,7 +97,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="fft64_16bit_noisy", choices=sorted(CONFIGS))
+    ap.add_argument("--config", default=DEFAULT_CONFIG, choices=sorted(CONFIGS))
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="budget of the bounded oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -93,6 +111,10 @@ def parse():
                          "small-ciphertext tensor-core")
     ap.add_argument("--budget-gb", type=float, default=150.0, help="serving HBM admission budget")
     ap.add_argument("--requests", type=int, default=0, help="serving: requests in the trace")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="default workload only: skip the batch and serve blocks")
+    ap.add_argument("--serve-requests", type=int, default=300,
+                    help="requests of the serve block of the default run")
     return ap.parse_args()
 
 
@@ -250,10 +272,13 @@ def roofline(params, gate_kernel, gate_ms, launches, gates_timed, tc_columns=0, 
         return out
     ops = float(Ng) * Ng * (params.n + 1) * L * gates_timed
     achieved = ops / sec
-    return {"bound": "alu", "achieved": achieved / 1e12, "peak": ALU_PEAK_OPS / 1e12,
-            "unit": "Tops/s (32-bit limb adds)", "frac": achieved / ALU_PEAK_OPS, "traffic": None,
+    peak = _INT_PEAKS.get("iadd3")
+    if not peak:
+        raise RuntimeError("integer peak not measured (call int_peaks first)")
+    return {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
+            "unit": "Tops/s (32-bit limb adds)", "frac": achieved / peak, "traffic": None,
             "kernel": "k_gate_generic", "avg_launch_ms": avg_launch_ms,
-            "peak_source": "derived: 152 SMs x 128 INT32 lanes x 2.07 GHz"}
+            "peak_source": "measured on this GPU: add.u32 rate (sfft_measure_int_peak)"}
 
 
 def variant_of(cfg):
@@ -527,6 +552,8 @@ def run_refresh(args):
     sf.encrypt_raw_bits_device(params, pub, src_bits, 13, d_src)
     plan = sf.Plan.refresher(params, count, flags)
     info = plan.info
+    if info["gate_kernel"] == sf.KERNEL_INT:
+        int_peaks(sf)
     d_out = torch.empty((count, cw), dtype=torch.int32, device="cuda")
     scratch = torch.empty(max(1, info["scratch_bytes"] // 4), dtype=torch.int32, device="cuda")
     stream = torch.cuda.Stream()
@@ -632,24 +659,28 @@ def run_gates(args):
     t = statistics.median(ms)
     info = sf.circuit_info(params, 2, 1, 4, 1)
     gk = kern if kern else info["gate_kernel"]
+    if gk == 1:
+        int_peaks(sf)
     print(json.dumps({"mode": "gates", "gates": G, "ms_per_level": t, "gates_per_s": G / t * 1e3,
                       "config": {"workload": args.config, "n": params.n, "ell": params.ell},
                       "note": "includes the test hook's descriptor upload, allocation and sync",
                       "roofline": roofline(params, gk, t, 1, G, info["tc_columns"])}), flush=True)
 
 
-def run_serve(args):
-    """Poisson arrivals into the continuous-batching server (rank 0 only)."""
+def run_serve(args, config=None, requests=0, emit=True):
+    """Poisson arrivals into the continuous-batching server (rank 0 only);
+    returns the JSON line (printed when emit)."""
     import torch
 
     import paper_1611_08769_gb300 as sf
     from paper_1611_08769_gb300 import build as sfbuild
     from synthetic import serving_trace
     sfbuild.build()
-    c = CONFIGS[args.config]
-    params = sf.param_set(c["pset"])
+    config = config or args.config
+    c = CONFIGS[config]
+    params = product_params(sf, config)
     cw = sf.ct_words(params)
-    count = args.requests or c["requests"]
+    count = requests or args.requests or c["requests"]
     # one encrypted input per distinct (shape, key set); outputs rotate per shape
     probe = serving_trace(count + c["calib"], 1.0, seed=5, key_sets=c["key_sets"])
     keys = {ks: sf.keygen(params, 2000 + ks) for ks in range(c["key_sets"])}
@@ -677,7 +708,13 @@ def run_serve(args):
         rot[shape] = k + 1
         return srv.submit(shape, inputs[(shape, r.key_set)], outputs[shape][k % 4])
 
-    # capacity: a closed burst of the same mix
+    # every shape's circuit compiled before the clock starts (a server's
+    # warm-up, like loading a model), then the capacity: a closed burst of
+    # the same mix, on the same server as the timed trace
+    t0 = time.perf_counter()
+    for shape in outputs:
+        srv.prepare(shape)
+    prepare_s = time.perf_counter() - t0
     burst = probe[:c["calib"]]
     t0 = time.perf_counter()
     tickets = [submit(r) for r in burst]
@@ -686,8 +723,7 @@ def run_serve(args):
     cap = len(burst) / (time.perf_counter() - t0)
     rate = 0.8 * cap
     trace = serving_trace(count, rate, seed=6, key_sets=c["key_sets"])
-    srv.close()
-    srv = sf.Server(params, int(args.budget_gb * (1 << 30)), max_active=64)
+    st0 = srv.stats()
     with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
         t0 = time.perf_counter()
         tickets = []
@@ -701,56 +737,54 @@ def run_serve(args):
     st = srv.stats()
     srv.close()
     served_prod = sum(products[(r.N1, r.N2, r.F, r.f)] for r in trace)
+    by_shape = {}
+    for r, x in zip(trace, lat):
+        by_shape.setdefault("%dx%d F%d" % (r.N1, r.N2, r.F), []).append(x)
+    per_shape = {k: {"requests": len(v), "p50_ms": float(np.percentile(v, 50)),
+                     "p99_ms": float(np.percentile(v, 99))} for k, v in sorted(by_shape.items())}
     line = {
         "metric": "encrypted FFTs/s served", "value": len(trace) / wall, "unit": "FFT/s",
         "n_gpus": 1, "steps": len(trace), "warmup": len(burst), "ms_per_step": wall * 1000 / len(trace),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic",
-        "config": {"workload": args.config, "n": params.n, "ell": params.ell, "chi": params.chi,
+        "config": {"workload": config, "n": params.n, "ell": params.ell, "chi": params.chi,
                    "requests": len(trace), "key_sets": c["key_sets"],
                    "arrival_rate_per_s": rate, "capacity_closed_burst_per_s": cap,
                    "hbm_budget_gb": args.budget_gb, "max_active": 64,
                    "mix": "75% 1-D N in {8..256} 8.8, 25% 2-D 8x8/16x16/32x32 at log2(pixels)+2 "
                           "integer bits, F = 16"},
-        "latency_ms": {"p50": st["p50_ms"], "p99": st["p99_ms"], "max": st["max_ms"],
-                       "client_p50": float(np.percentile(lat, 50)),
-                       "client_p99": float(np.percentile(lat, 99))},
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "max": float(max(lat)), "by_shape": per_shape,
+                       "note": "submit to completion, per request of the timed trace"},
         "gates_per_s": served_prod / wall,
-        "server": {k: st[k] for k in ("ticks", "tick_gates", "peak_active")},
+        "server": {"ticks": st["ticks"] - st0["ticks"], "tick_gates": st["tick_gates"] - st0["tick_gates"],
+                   "peak_active": st["peak_active"], "prepare_s": prepare_s,
+                   "admission": "arrival order; a request that does not fit may be passed by up to "
+                                "16 later ones that do"},
         "e2e": {"value": len(trace) / wall, "unit": "FFT/s",
                 "note": "served end to end: host ciphertexts in, host ciphertexts out"},
         "clocks": clk.summary(),
     }
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
 
 
-def main():
-    args = parse()
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if args.impl == "reference":
-        return run_reference(args, rank, world)
-    if args.mode == "gates":
-        return run_gates(args)
-    if CONFIGS[args.config]["kind"] == "serve":
-        return run_serve(args) if rank == 0 else None
-    if CONFIGS[args.config]["kind"] == "refresh":
-        return run_refresh(args)
-
+def run_fft(args, config, steps, warmup, world, rank, local, cpu_leg=True, plain_leg=True):
+    """One FFT or batch workload on this rank's GPU: the batched form (graph
+    replay) timed, per-launch kernel events, the plain evaluator, the host
+    pipeline and (rank 0, one GPU) the CPU oracle baseline. Returns the JSON
+    line on rank 0, None elsewhere."""
     import torch
     import torch.distributed as dist
 
     import paper_1611_08769_gb300 as sf
     from paper_1611_08769_gb300 import build as sfbuild
 
-    if world > 1:
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    torch.cuda.set_device(local)
     sfbuild.build()
-    params, items = workload(sf, args.config)
-    flags = kernel_flags(sf, args.kernel) | flags_of(sf, args.config)
-    enc_tw = variant_of(args.config)["enc_twiddle"]
+    params, items = workload(sf, config)
+    flags = kernel_flags(sf, args.kernel) | flags_of(sf, config)
+    enc_tw = variant_of(config)["enc_twiddle"]
     cw = sf.ct_words(params)
     reqs = [d for d, *_ in items]
 
@@ -759,6 +793,13 @@ def main():
     pubs = {ks: torch.from_numpy(k.public().view(np.int32)).cuda() for ks, k in keys.items()}
     batch = sf.Batch(params, reqs, flags)
     info = batch.info
+    if info["gate_kernel"] == sf.KERNEL_INT:
+        int_peaks(sf)
+    tuned = None
+    if info["gate_kernel"] == sf.KERNEL_SM:   # ring depth of the small-ciphertext kernel
+        depth, us = sf.autotune_small(params, 20000, 3)
+        tuned = {"ring_depth": depth, "ns_per_gate_by_depth": {k: round(v * 1000, 2) for k, v in us.items()},
+                 "level": "20000 random half-adder products"}
     d_in = torch.empty((info["inputs"], cw), dtype=torch.int32, device="cuda")
     for r, ((N1, N2, F, f), re_, im_, ks, seed) in enumerate(items):
         re_all, im_all = fft_inputs(product_twiddles(sf), (N1, N2, F, f), re_, im_, enc_tw)
@@ -789,11 +830,11 @@ def main():
     # batched form (graph replay): the headline
     run_b = lambda: batch.eval(d_in, d_out, scratch, stream)  # noqa: E731
     with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             run_b()
         batch.check(stream)
         with ClockSampler(local) as clk:
-            ms = timed(run_b, args.steps)
+            ms = timed(run_b, steps)
         batch.check(stream)
     ms = max_over_ranks(ms, world, "cuda")
     fft_per_s = replica_throughput(len(items), ms, world)
@@ -809,7 +850,7 @@ def main():
 
     # plain level-by-level evaluator on the same workload (per-request plans)
     plain = None
-    if not args.no_plain:
+    if plain_leg:
         plans = [sf.Plan(params, *d, flags) for d in reqs]
         pscr = torch.empty(max(1, max(p.info["scratch_bytes"] for p in plans) // 4),
                            dtype=torch.int32, device="cuda")
@@ -818,9 +859,9 @@ def main():
             for r, p in enumerate(plans):
                 p.eval_fft(d_in[batch.in_off[r]:], d_out[batch.out_off[r]:], pscr, stream)
         with torch.cuda.stream(stream):
-            for _ in range(min(1, args.warmup)):
+            for _ in range(min(1, warmup)):
                 run_p()
-            pms = timed(run_p, max(1, min(args.steps, 2)))
+            pms = timed(run_p, max(1, steps))
         plain = {"ms_per_step": pms, "value": len(items) * 1000.0 / pms, "unit": "FFT/s",
                  "launches_per_step": sum(p.info["levels"] + 1 for p in plans),
                  "speedup_of_batched": pms / ms}
@@ -840,21 +881,23 @@ def main():
         pipe(2)   # warm-up: both buffer sets' graphs
         barrier()
         t0 = time.perf_counter()
-        pipe(args.steps)
-        e2e_ms = (time.perf_counter() - t0) * 1000.0 / args.steps
+        pipe(steps)
+        e2e_ms = (time.perf_counter() - t0) * 1000.0 / steps
         barrier()
     e2e_ms = max_over_ranks(e2e_ms, world, "cuda")
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        oparams = oracle_params(args.config, items)   # the oracle's own ell
-        fps, gps, detail = cpu_oracle_sample(oparams, items, args.cpu_seconds, variant_of(args.config))
+    if rank == 0 and world == 1 and cpu_leg:
+        oparams = oracle_params(config, items)   # the oracle's own ell
+        fps, gps, detail = cpu_oracle_sample(oparams, items, args.cpu_seconds, variant_of(config))
         cpu = {"value": fps, "unit": "FFT/s", "cores": os.cpu_count(), "kind": "oracle",
                "sample": detail, "gates_per_s": gps, "oracle_ell": oparams.ell,
                "oracle_ell_equals_library": oparams.ell == params.ell}
 
     if rank == 0:
-        cfg = config_json(args.config, params, items)
+        cfg = config_json(config, params, items)
+        if tuned:
+            cfg["autotune"] = tuned
         cfg.update({"products_per_step": info["products"], "levels": info["levels"],
                     "evaluator": "level-merged program replayed as one CUDA graph",
                     "l2": f"inputs {info['inputs'] * cw * 4 / 1e9:.2f} GB (> L2 129 MB)"
@@ -863,7 +906,7 @@ def main():
                           f"{info['scratch_bytes'] / 1e9:.2f} GB of intermediates streamed)"})
         line = {
             "metric": "encrypted FFTs/s", "value": fft_per_s, "unit": "FFT/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "steps": steps, "warmup": warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic", "config": cfg,
             "gates_per_s": world * info["products"] * 1000.0 / ms,
@@ -876,9 +919,55 @@ def main():
                     "d2h_bytes_per_step": info["outputs"] * cw * 4,
                     "api": "sfft_batch_eval_host_pipelined (copies overlapped with the "
                            "neighbouring steps)"},
-            "gpu_launches": args.steps * kernels_per_step,
+            "gpu_launches": steps * kernels_per_step,
             "clocks": clk.summary(),
         }
+        return line
+    return None
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if args.mode == "gates":
+        return run_gates(args)
+    if CONFIGS[args.config]["kind"] == "serve":
+        return run_serve(args) if rank == 0 else None
+    if CONFIGS[args.config]["kind"] == "refresh":
+        return run_refresh(args)
+
+    import torch
+    import torch.distributed as dist
+
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    line = run_fft(args, args.config, args.steps, args.warmup, world, rank, local,
+                   cpu_leg=not args.no_cpu_baseline, plain_leg=not args.no_plain)
+    if rank == 0 and world == 1 and args.config == DEFAULT_CONFIG and not args.no_extra:
+        # the baseline metric's other forms on the same box: batched vs plain
+        # on the 256-request batch, and the continuous-batching server
+        torch.cuda.empty_cache()
+        b = run_fft(args, "batch256_p2", 3, 2, 1, 0, local, cpu_leg=False, plain_leg=True)
+        line["batch"] = {k: b[k] for k in ("metric", "value", "unit", "ms_per_step", "gates_per_s",
+                                           "config", "roofline", "plain", "e2e", "gpu_launches",
+                                           "clocks")}
+        torch.cuda.empty_cache()
+        srv = run_serve(args, "serve_p2", requests=args.serve_requests, emit=False)
+        line["serve"] = {k: srv[k] for k in ("metric", "value", "unit", "config", "latency_ms",
+                                             "gates_per_s", "server", "clocks")}
+        import paper_1611_08769_gb300 as sf
+        with ClockSampler(local) as clk:
+            pk = int_peaks(sf)
+        line["int_peaks"] = {"unit": "Tops/s", **{k: v / 1e12 for k, v in pk.items()},
+                             "how": "8 independent chains per thread of one 32-bit op, all SMs at "
+                                    "full occupancy, CUDA events (popc: popc + xor per step)",
+                             "clocks": clk.summary()}
+    if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -438,6 +438,11 @@ int sfft_server_create(const sfft_params* p, uint64_t hbm_budget_bytes, uint32_t
  * exceeds the budget. */
 int sfft_server_submit(sfft_server* sv, const sfft_request* req, const uint32_t* h_in,
                        uint32_t* h_out, uint64_t* ticket);
+/* Compiles the circuit of a request shape (and uploads its device program)
+ * ahead of its first submission, so that later submissions of this shape only
+ * queue; submit compiles a new shape itself otherwise (seconds for large
+ * circuits, outside the server's lock). Synchronous. */
+int sfft_server_prepare(sfft_server* sv, const sfft_request* req);
 /* Waits up to timeout_ms for the request (ETIMEOUT otherwise), reports its
  * submit-to-completion latency, and forgets the ticket. */
 int sfft_server_wait(sfft_server* sv, uint64_t ticket, uint32_t timeout_ms, double* latency_ms);
@@ -445,15 +450,16 @@ int sfft_server_get_stats(sfft_server* sv, sfft_server_stats* st);
 /* Stops the worker (queued requests are dropped, running ones finish). */
 void sfft_server_free(sfft_server* sv);
 
-/* Evaluates a single level of gates given explicitly (test hook): gate g
- * computes, with A = d_a[g] (complemented to P - A first when
- * (flags[g] & 1)) and B = d_b[g],
- *   d_out0[g] = c0 P + c1 A + c2 B + c3 BitDecomp(A) B    (code0 = c0..c3)
- *   d_out1[g] likewise with code1 when flags[g] & 2.
- * d_a/d_b/d_out0/d_out1 are arrays of n_gates ciphertexts; codes are 4
- * signed nibbles c0 | c1 << 4 | c2 << 8 | c3 << 12 (two's complement).
- * kernel: 0 automatic, 1 integer ALU, 2 tensor cores (EPARAM if unsupported).
- * Synchronises the stream; SFFT_ETIMEOUT if a bounded device wait ran out. */
+/* Measured integer-pipe peak of the current GPU (the integer kernel's
+ * roofline denominator): every SM at full occupancy runs 8 independent chains
+ * per thread of one 32-bit operation, op 0 add.u32 (IADD3), 1 lop3.b32
+ * (LOP3), 2 mad.lo.u32 (IMAD), 3 popc.b32 (POPC; each step also XORs the
+ * count back, so two operations per counted step), `iters` x 32 steps per
+ * chain (0: 4096); *ops_per_s = counted operations per second between CUDA
+ * events on the legacy stream, best of two timed launches after one warm-up.
+ * Allocates a small buffer; synchronises the device. */
+int sfft_measure_int_peak(uint32_t op, uint32_t iters, double* ops_per_s);
+
 /* Autotuner of the small-ciphertext tensor-core kernel (gate kernel 3, used
  * where Ng <= 256): for each ring depth it can run (gates in flight per CTA,
  * 2 to 8 where shared memory allows) it times one level of n_gates half-adder
@@ -470,6 +476,16 @@ int sfft_autotune_small(const sfft_params* p, uint64_t n_gates, uint32_t reps,
  * small-ciphertext kernel for the current device and ell (32, 64, 96, 128). */
 int sfft_small_kernel_set_slots(uint32_t ell, uint32_t nslots);
 
+/* Evaluates a single level of gates given explicitly (test hook): gate g
+ * computes, with A = d_a[g] (complemented to P - A first when
+ * (flags[g] & 1)) and B = d_b[g],
+ *   d_out0[g] = c0 P + c1 A + c2 B + c3 BitDecomp(A) B    (code0 = c0..c3)
+ *   d_out1[g] likewise with code1 when flags[g] & 2.
+ * d_a/d_b/d_out0/d_out1 are arrays of n_gates ciphertexts; codes are 4
+ * signed nibbles c0 | c1 << 4 | c2 << 8 | c3 << 12 (two's complement).
+ * kernel: 0 automatic, 1 integer ALU, 2 general tensor-core kernel, 3 small-
+ * ciphertext tensor-core kernel (Ng <= 256); EPARAM if unsupported.
+ * Synchronises the stream; SFFT_ETIMEOUT if a bounded device wait ran out. */
 int sfft_gate_level(const sfft_params* p, const uint32_t* d_a, const uint32_t* d_b,
                     uint32_t* d_out0, uint32_t* d_out1, const uint16_t* h_code0,
                     const uint16_t* h_code1, const uint8_t* h_flags, uint64_t n_gates,

@@ -435,6 +435,11 @@ class Server:
         self._h = h
         self._held = {}
 
+    def prepare(self, request):
+        """Compile a request shape ahead of its first submission (sfft_server_prepare)."""
+        req = native.sfft_request(*request)
+        check(lib().sfft_server_prepare(self._h, ctypes.byref(req)))
+
     def submit(self, request, h_in, h_out):
         """Queue one request; h_in / h_out stay referenced until wait()."""
         t = ctypes.c_uint64()
@@ -475,6 +480,19 @@ def gate_level(params, d_a, d_b, d_out0, d_out1, code0, code1, flags, stream=Non
                                 code1.ctypes.data_as(native.c_u16_p),
                                 flags.ctypes.data_as(native.c_u8_p), len(code0), kernel,
                                 _stream(stream)))
+
+
+INT_PEAK_OPS = ("iadd3", "lop3", "imad", "popc")
+
+
+def measure_int_peak(op, iters=4096):
+    """Measured integer-pipe rate of the current GPU (sfft_measure_int_peak),
+    operations per second; op is an index into INT_PEAK_OPS or its name."""
+    if isinstance(op, str):
+        op = INT_PEAK_OPS.index(op)
+    v = ctypes.c_double(0)
+    check(lib().sfft_measure_int_peak(op, iters, ctypes.byref(v)))
+    return float(v.value)
 
 
 def autotune_small(params, n_gates=20000, reps=3):

@@ -39,6 +39,10 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
+// Later requests that may be admitted past one that waits at the head of the
+// queue for room.
+constexpr uint32_t kMaxBypass = 16;
+
 // First-fit allocator of ranges [0, capacity) with coalescing frees.
 class RangeAlloc {
  public:
@@ -85,10 +89,20 @@ struct Shape4 {
   }
 };
 
+// A shape's compiled program: host copy (levels, counts) and device copy
+// (descriptors, coefficients, fix-ups) that admission remaps on the device.
+struct ShapeProgram {
+  Program host;
+  DeviceProgram dev;
+  ~ShapeProgram() { free_device_program(&dev); }
+};
+
 struct Request {
   uint64_t ticket = 0;
   Shape4 shape{};
   const Program* prog = nullptr;
+  const DeviceProgram* dprog = nullptr;
+  uint32_t bypassed = 0;                   // later requests admitted while this one waited at the head
   const uint32_t* h_in = nullptr;
   uint32_t* h_out = nullptr;
   uint64_t base = 0, nslots = 0;          // arena range (ciphertexts)
@@ -118,17 +132,21 @@ struct sfft_server {
   sfft::FixDesc* fpool = nullptr;
   uint64_t fpool_cap = 0;
   sfft::RangeAlloc fpool_alloc;
-  // per-tick gathered level
+  // per-tick gathered level (written in stream order by the gather kernel);
+  // tick_ev[k] marks the end of the last tick with parity k, so the host runs
+  // at most two ticks ahead of the device
   sfft::GateDesc* tick_desc = nullptr;
   sfft::GateAux* tick_aux = nullptr;
   uint64_t tick_cap = 0;
+  cudaEvent_t tick_ev[2] = {nullptr, nullptr};
+  bool tick_ev_used[2] = {false, false};
   uint8_t* bx = nullptr;
   int* err = nullptr;
   cudaStream_t stream = nullptr;
   bool tc = false;
   uint32_t variant = 0;            // circuit variant flags of every request
 
-  std::map<sfft::Shape4, std::unique_ptr<sfft::Program>> programs;
+  std::map<sfft::Shape4, std::unique_ptr<sfft::ShapeProgram>> programs;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::deque<std::shared_ptr<sfft::Request>> queue;
@@ -148,14 +166,59 @@ namespace sfft {
 
 namespace {
 
-uint32_t remap(uint32_t ref, uint64_t scr, uint64_t in, uint64_t out) {
+// A program-relative reference -> an absolute arena slot (region 0).
+__host__ __device__ __forceinline__ uint32_t remap(uint32_t ref, uint64_t scr, uint64_t in, uint64_t out) {
   if (ref == REF_NONE) return ref;
   const uint32_t region = ref >> 30, slot = ref & SLOT_MASK;
   const uint64_t base = region == REG_SCRATCH ? scr : region == REG_IN ? in : out;
-  return make_ref(REG_SCRATCH, (uint32_t)(base + slot));
+  return (uint32_t)(base + slot);   // region bits 0: the arena
 }
 
-// Admission (under the lock): arena range, descriptor upload, input copy.
+// Admission: a request's descriptors and fix-ups, remapped to its arena range,
+// written into its pool ranges (grid-stride over gates, then fix-ups).
+__global__ void k_admit_remap(const GateDesc* src, const GateAux* asrc, uint64_t n, GateDesc* dst,
+                              GateAux* adst, const FixDesc* fsrc, uint64_t nf, FixDesc* fdst,
+                              uint64_t scr, uint64_t in, uint64_t out) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += stride) {
+    const GateDesc d = src[g];
+    dst[g] = GateDesc{remap(d.a, scr, in, out), remap(d.b, scr, in, out), remap(d.o0, scr, in, out),
+                      remap(d.o1, scr, in, out)};
+    adst[g] = asrc[g];
+  }
+  for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nf; k += stride) {
+    FixDesc f = fsrc[k];
+    f.dst = (uint32_t)(out + f.dst);   // absolute arena slot (REG_OUT base = arena)
+    if (f.kind <= 1) f.src = remap(f.src, scr, in, out);
+    fdst[k] = f;
+  }
+}
+
+// A tick's level: up to kTickJobs contiguous descriptor runs (every active
+// request's products, then their linear gates) gathered into the tick buffer
+// by one launch; job j copies cnt[j] gates from pool index src[j] to dst[j].
+constexpr uint32_t kTickJobs = 128;
+struct TickJobs {
+  uint32_t n, pad;
+  uint64_t src[kTickJobs], dst[kTickJobs], cnt[kTickJobs];
+};
+
+__global__ void k_tick_gather(TickJobs jobs, const GateDesc* dpool, const GateAux* apool, GateDesc* tdesc,
+                              GateAux* taux) {
+  const uint32_t j = blockIdx.y;
+  if (j >= jobs.n) return;
+  const uint64_t cnt = jobs.cnt[j], src = jobs.src[j], dst = jobs.dst[j];
+  for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < cnt;
+       g += (uint64_t)gridDim.x * blockDim.x) {
+    tdesc[dst + g] = dpool[src + g];
+    taux[dst + g] = apool[src + g];
+  }
+}
+
+// Admission (under the lock): arena and pool ranges, then, on the server
+// stream, the device remap of the shape's program into the pools and the copy
+// of the client's inputs (h_in stays valid until the request's wait returns,
+// so nothing here waits for the copies).
 int admit(sfft_server* sv, Request* r) {
   const Program& p = *r->prog;
   r->nslots = p.scratch_slots + p.n_inputs + p.n_outputs;
@@ -172,37 +235,20 @@ int admit(sfft_server* sv, Request* r) {
     return 1;
   }
   const uint64_t scr = r->base, in = r->base + p.scratch_slots, out = in + p.n_inputs;
-  std::vector<GateDesc> d(p.desc.size());
-  for (size_t g = 0; g < d.size(); g++) {
-    d[g].a = remap(p.desc[g].a, scr, in, out);
-    d[g].b = remap(p.desc[g].b, scr, in, out);
-    d[g].o0 = remap(p.desc[g].o0, scr, in, out);
-    d[g].o1 = remap(p.desc[g].o1, scr, in, out);
-  }
-  std::vector<FixDesc> fx(p.fix.size());
-  for (size_t k = 0; k < fx.size(); k++) {
-    fx[k] = p.fix[k];
-    fx[k].dst = (uint32_t)(out + p.fix[k].dst);   // absolute arena slot (REG_OUT base = arena)
-    if (fx[k].kind <= 1) fx[k].src = remap(p.fix[k].src, scr, in, out);
-  }
   cudaStream_t st = sv->stream;
-  cudaError_t e = cudaSuccess;
-  if (r->ndesc) {
-    e = cudaMemcpyAsync(sv->dpool + r->dbase, d.data(), d.size() * sizeof(GateDesc),
-                        cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(sv->apool + r->dbase, p.aux.data(), p.aux.size() * sizeof(GateAux),
-                          cudaMemcpyHostToDevice, st);
+  const uint64_t work = std::max<uint64_t>(r->ndesc, r->nfix);
+  if (work) {
+    const unsigned blocks = (unsigned)std::min<uint64_t>((work + 255) / 256, 1024);
+    k_admit_remap<<<blocks, 256, 0, st>>>(r->dprog->desc, r->dprog->aux, r->ndesc, sv->dpool + r->dbase,
+                                          sv->apool + r->dbase, r->dprog->fix, r->nfix,
+                                          sv->fpool + r->fbase, scr, in, out);
+    count_launches(1);
   }
-  if (e == cudaSuccess && r->nfix)
-    e = cudaMemcpyAsync(sv->fpool + r->fbase, fx.data(), fx.size() * sizeof(FixDesc),
-                        cudaMemcpyHostToDevice, st);
+  cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(sv->arena + in * sv->s.ctw, r->h_in, p.n_inputs * sv->s.ctw * 4,
                         cudaMemcpyHostToDevice, st);
-  // the host vectors above die with this function: the copies must finish first
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return cuda_fail(e, "server admission copies");
+  if (e != cudaSuccess) return cuda_fail(e, "server admission");
   r->level = 0;
   r->state = 1;
   r->t_admit = Clock::now();
@@ -211,7 +257,7 @@ int admit(sfft_server* sv, Request* r) {
 
 int ensure_tick_capacity(sfft_server* sv, uint64_t n) {
   if (n <= sv->tick_cap) return SFFT_OK;
-  cudaStreamSynchronize(sv->stream);
+  cudaStreamSynchronize(sv->stream);   // the old buffers may still be read
   cudaFree(sv->tick_desc);
   cudaFree(sv->tick_aux);
   uint64_t cap = std::max<uint64_t>(n, 2 * sv->tick_cap);
@@ -222,7 +268,9 @@ int ensure_tick_capacity(sfft_server* sv, uint64_t n) {
   return SFFT_OK;
 }
 
-// One tick (worker thread, lock not held): the next level of every active request.
+// One tick (worker thread, lock not held): the next level of every active
+// request, gathered on the device by one launch and evaluated by one launch
+// of products (and one of linear gates).
 int tick(sfft_server* sv, std::vector<std::shared_ptr<Request>>& act) {
   cudaStream_t st = sv->stream;
   // the level's products of every active request, then their linear gates
@@ -235,22 +283,32 @@ int tick(sfft_server* sv, std::vector<std::shared_ptr<Request>>& act) {
   }
   int rc = ensure_tick_capacity(sv, n);
   if (rc) return rc;
-  uint64_t at[2] = {0, nprod};
-  for (auto& r : act) {
-    const Program& p = *r->prog;
-    if (r->level + 1 >= p.level_off.size()) continue;
-    const uint64_t cut[3] = {p.level_off[r->level], p.lin_start[r->level], p.level_off[r->level + 1]};
-    for (int ph = 0; ph < 2; ph++) {
-      const uint64_t b = cut[ph], cnt = cut[ph + 1] - cut[ph];
-      if (cnt) {
-        cudaMemcpyAsync(sv->tick_desc + at[ph], sv->dpool + r->dbase + b, cnt * sizeof(GateDesc),
-                        cudaMemcpyDeviceToDevice, st);
-        cudaMemcpyAsync(sv->tick_aux + at[ph], sv->apool + r->dbase + b, cnt * sizeof(GateAux),
-                        cudaMemcpyDeviceToDevice, st);
-      }
+  TickJobs jobs;
+  jobs.n = 0;
+  jobs.pad = 0;
+  uint64_t at[2] = {0, nprod}, most = 0;
+  for (int ph = 0; ph < 2; ph++) {
+    for (auto& r : act) {
+      const Program& p = *r->prog;
+      if (r->level + 1 >= p.level_off.size()) continue;
+      const uint64_t cut[3] = {p.level_off[r->level], p.lin_start[r->level], p.level_off[r->level + 1]};
+      const uint64_t cnt = cut[ph + 1] - cut[ph];
+      if (!cnt) continue;
+      if (jobs.n == kTickJobs) return fail(SFFT_EINVAL, "too many descriptor runs in one tick");
+      jobs.src[jobs.n] = r->dbase + cut[ph];
+      jobs.dst[jobs.n] = at[ph];
+      jobs.cnt[jobs.n] = cnt;
+      jobs.n++;
       at[ph] += cnt;
+      most = std::max(most, cnt);
     }
-    r->level++;
+  }
+  for (auto& r : act)
+    if (r->level + 1 < r->prog->level_off.size()) r->level++;
+  if (jobs.n) {
+    const dim3 grid((unsigned)std::min<uint64_t>((most + 255) / 256, 64), jobs.n);
+    k_tick_gather<<<grid, 256, 0, st>>>(jobs, sv->dpool, sv->apool, sv->tick_desc, sv->tick_aux);
+    count_launches(1);
   }
   if (n) {
     KArgs a = make_args(sv->s);
@@ -296,19 +354,27 @@ int tick(sfft_server* sv, std::vector<std::shared_ptr<Request>>& act) {
 void worker_main(sfft_server* sv) {
   std::unique_lock<std::mutex> lk(sv->mu);
   while (true) {
-    // admission: FIFO while the head fits
-    while (!sv->queue.empty() && sv->active.size() < sv->max_active) {
-      auto r = sv->queue.front();
+    // admission in arrival order; a request that does not fit yet is passed
+    // by later ones that do, until kMaxBypass of them have passed it, after
+    // which nothing is admitted before it (no starvation of large requests)
+    for (auto it = sv->queue.begin(); it != sv->queue.end() && sv->active.size() < sv->max_active;) {
+      const bool head = it == sv->queue.begin();
+      auto r = *it;
       const int rc = admit(sv, r.get());
-      if (rc == 1) break;
       if (rc < 0) {
         sv->worker_error = rc;
         sv->worker_msg = sfft_last_error();
         sv->stop = true;
         break;
       }
-      sv->queue.pop_front();
+      if (rc == 1) {
+        if (head && r->bypassed >= kMaxBypass) break;
+        ++it;
+        continue;
+      }
+      if (!head) sv->queue.front()->bypassed++;
       sv->active.push_back(r);
+      it = sv->queue.erase(it);
     }
     sv->peak_active = std::max<uint64_t>(sv->peak_active, sv->active.size());
     // completions
@@ -346,9 +412,12 @@ void worker_main(sfft_server* sv) {
       continue;
     }
     lk.unlock();
+    // at most two ticks in flight: wait for the tick before last
+    const int k = (int)(sv->ticks & 1);
+    if (sv->tick_ev_used[k]) cudaEventSynchronize(sv->tick_ev[k]);
     const int rc = tick(sv, running);
-    // bound how far the host runs ahead of the device
-    cudaStreamSynchronize(sv->stream);
+    cudaEventRecord(sv->tick_ev[k], sv->stream);
+    sv->tick_ev_used[k] = true;
     lk.lock();
     if (rc) {
       sv->worker_error = rc;
@@ -397,6 +466,8 @@ int sfft_server_create(const sfft_params* p, uint64_t hbm_budget_bytes, uint32_t
   if (e == cudaSuccess) e = cudaMalloc((void**)&sv->err, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(sv->err, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sv->stream, cudaStreamNonBlocking);
+  for (int k = 0; k < 2 && e == cudaSuccess; k++)
+    e = cudaEventCreateWithFlags(&sv->tick_ev[k], cudaEventDisableTiming);
   if (e != cudaSuccess) {
     cudaFree(sv->arena);
     cudaFree(sv->dpool);
@@ -414,30 +485,69 @@ int sfft_server_create(const sfft_params* p, uint64_t hbm_budget_bytes, uint32_t
   return SFFT_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// The shape's compiled program, compiled on first use without holding the
+// server's lock (a large circuit takes seconds on the host; the worker keeps
+// ticking meanwhile). On return the lock is held.
+int shape_program(sfft_server* sv, const sfft_request* req, std::unique_lock<std::mutex>& lk,
+                  ShapeProgram** out) {
+  const Shape4 shape{req->N1, req->N2, req->F, req->f};
+  lk.lock();
+  auto it = sv->programs.find(shape);
+  if (it != sv->programs.end()) {
+    *out = it->second.get();
+    return SFFT_OK;
+  }
+  lk.unlock();
+  Circuit c;
+  c.set_variant(sv->variant);
+  if (!build_fft(&c, req->N1, req->N2, req->F, req->f)) {
+    lk.lock();
+    return fail(SFFT_EINVAL, "invalid FFT shape");
+  }
+  std::unique_ptr<ShapeProgram> prog(new ShapeProgram);
+  compile(c, sv->s, &prog->host);
+  int rc = prog->host.noise_ok ? SFFT_OK : fail(SFFT_EPARAM, "static noise bound reaches q/4 for this shape");
+  if (!rc) rc = make_device_program(prog->host, &prog->dev);
+  lk.lock();
+  if (rc) return rc;
+  it = sv->programs.find(shape);   // another thread may have compiled it meanwhile
+  if (it == sv->programs.end()) it = sv->programs.emplace(shape, std::move(prog)).first;
+  *out = it->second.get();
+  return SFFT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sfft_server_prepare(sfft_server* sv, const sfft_request* req) {
+  if (!sv || !req) return fail(SFFT_EINVAL, "null argument");
+  std::unique_lock<std::mutex> lk(sv->mu, std::defer_lock);
+  ShapeProgram* sp = nullptr;
+  return shape_program(sv, req, lk, &sp);
+}
+
 int sfft_server_submit(sfft_server* sv, const sfft_request* req, const uint32_t* h_in, uint32_t* h_out,
                        uint64_t* ticket) {
   if (!sv || !req || !h_in || !h_out || !ticket) return fail(SFFT_EINVAL, "null argument");
   const Shape4 shape{req->N1, req->N2, req->F, req->f};
-  std::unique_lock<std::mutex> lk(sv->mu);
+  std::unique_lock<std::mutex> lk(sv->mu, std::defer_lock);
+  ShapeProgram* sprog = nullptr;
+  const int rc = shape_program(sv, req, lk, &sprog);
+  if (rc) return rc;
   if (sv->worker_error) return fail(sv->worker_error, "server stopped: " + sv->worker_msg);
-  auto it = sv->programs.find(shape);
-  if (it == sv->programs.end()) {
-    Circuit c;
-    c.set_variant(sv->variant);
-    if (!build_fft(&c, req->N1, req->N2, req->F, req->f))
-      return fail(SFFT_EINVAL, "invalid FFT shape");
-    std::unique_ptr<Program> prog(new Program);
-    compile(c, sv->s, prog.get());
-    if (!prog->noise_ok) return fail(SFFT_EPARAM, "static noise bound reaches q/4 for this shape");
-    it = sv->programs.emplace(shape, std::move(prog)).first;
-  }
-  const Program* p = it->second.get();
+  const Program* p = &sprog->host;
   if (p->scratch_slots + p->n_inputs + p->n_outputs > sv->arena_cts || p->desc.size() > sv->dpool_cap)
     return fail(SFFT_ENOMEM, "request larger than the whole HBM budget");
   auto r = std::make_shared<Request>();
   r->ticket = sv->next_ticket++;
   r->shape = shape;
   r->prog = p;
+  r->dprog = &sprog->dev;
   r->h_in = h_in;
   r->h_out = h_out;
   r->t_submit = Clock::now();
@@ -503,6 +613,9 @@ void sfft_server_free(sfft_server* sv) {
   cudaFree(sv->tick_aux);
   cudaFree(sv->bx);
   cudaFree(sv->err);
+  for (cudaEvent_t ev : sv->tick_ev)
+    if (ev) cudaEventDestroy(ev);
+  sv->programs.clear();   // device copies of the shape programs
   cudaStreamDestroy(sv->stream);
   delete sv;
 }

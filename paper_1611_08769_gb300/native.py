@@ -77,6 +77,7 @@ SIGNATURES = {
     "sfft_refresh_eval_plain": (c_i32, [P(sfft_params), c_u64, c_u32, c_u8_p, c_u32_p, c_u8_p]),
     "sfft_eval_levels": (c_i32, [c_void_p, c_u32, c_u32, c_void_p, c_void_p, c_void_p, c_u64, c_void_p]),
     "sfft_plan_level": (c_i32, [c_void_p, c_u32, c_u32_p, c_u32_p, c_u8_p, c_u64, P(c_u64), P(c_u64)]),
+    "sfft_measure_int_peak": (c_i32, [c_u32, c_u32, c_double_p]),
     "sfft_autotune_small": (c_i32, [P(sfft_params), c_u64, c_u32, c_u32_p, c_double_p]),
     "sfft_small_kernel_set_slots": (c_i32, [c_u32, c_u32]),
     "sfft_gate_level_withheld": (c_i32, [P(sfft_params), c_void_p, c_void_p, c_void_p, c_u16_p,
@@ -113,6 +114,7 @@ class sfft_server_stats(ctypes.Structure):
 SIGNATURES.update({
     "sfft_server_create": (c_i32, [P(sfft_params), c_u64, c_u32, c_u32, P(c_void_p)]),
     "sfft_server_submit": (c_i32, [c_void_p, P(sfft_request), c_void_p, c_void_p, P(c_u64)]),
+    "sfft_server_prepare": (c_i32, [c_void_p, P(sfft_request)]),
     "sfft_server_wait": (c_i32, [c_void_p, c_u64, c_u32, c_double_p]),
     "sfft_server_get_stats": (c_i32, [c_void_p, P(sfft_server_stats)]),
     "sfft_server_free": (None, [c_void_p]),

@@ -83,3 +83,51 @@ def test_request_beyond_budget_is_rejected():
             srv.wait(12345, timeout_ms=10)          # unknown ticket
     finally:
         srv.close()
+
+
+def test_served_request_matches_oracle():
+    """One request served in a mix of others (different shapes and client
+    keys, a budget that makes later requests wait, one large request that
+    the admission lets smaller ones pass) is compared ciphertext for
+    ciphertext with the oracle's encrypted evaluation of the same circuit on
+    the same encryptions (toy noise-free parameters)."""
+    from oracle import circuit, evaluate, fixedpoint as fx, gsw
+    sp = sf.param_set("P0")
+    p = gsw.Params(sp.n, sp.ell, sp.m, sp.chi)
+    shape = (8, 1, 8, 4)
+    key_seed, enc_seed = 77, 13
+    re_, im_ = signal_1d(8, -1, 1, 5)
+    keys = sf.keygen(sp, key_seed)
+    pub = torch.from_numpy(keys.public().view(np.int32)).cuda()
+    d_in = torch.empty((8 * 2 * 8, sf.ct_words(sp)), dtype=torch.int32, device="cuda")
+    sf.encrypt_bits_device(sp, pub, re_, im_, 8, 4, enc_seed, d_in)
+    target = (shape, d_in.cpu().pin_memory(), torch.zeros((8 * 2 * 8, sf.ct_words(sp)), dtype=torch.int32).pin_memory())
+    mix = [((16, 16, 12, 2), None)] + [(SHAPES[k % len(SHAPES)], None) for k in range(8)]
+    others = []
+    for k, (sh, _) in enumerate(mix):
+        di = _request_inputs(sp, sh, k % 3, 90 + k)
+        others.append((sh, di.cpu().pin_memory(),
+                       torch.zeros((sh[0] * sh[1] * 2 * sh[2], sf.ct_words(sp)), dtype=torch.int32).pin_memory()))
+    # 23 MB: the 16 x 16 image (21.6 MB of ciphertexts) fits only once the
+    # first small requests have left, and the later small ones pass it
+    srv = sf.Server(sp, 23 << 20, max_active=8)
+    try:
+        tickets = [srv.submit(sh, hi, ho) for sh, hi, ho in others[1:4]]
+        tickets.append(srv.submit(*others[0]))
+        t_target = srv.submit(*target)
+        tickets += [srv.submit(sh, hi, ho) for sh, hi, ho in others[4:]]
+        srv.wait(t_target)
+        for t in tickets:
+            srv.wait(t)
+    finally:
+        srv.close()
+    got = target[2].numpy().view(np.uint32).reshape(-1, p.Ng, p.n + 1, p.L)
+    ko = gsw.Keys(p, key_seed)
+    c = circuit.fft_circuit(*shape)
+    cts = []
+    for k in range(8):
+        for part, x in enumerate((re_[k], im_[k])):
+            for b, bit in enumerate(fx.to_bits(fx.quantize(x, 8, 4), 8)):
+                cts.append(gsw.encrypt(ko, bit, enc_seed, (2 * k + part) * 8 + b))
+    want = evaluate.eval_encrypted(c, p, cts)
+    assert np.array_equal(got, want)

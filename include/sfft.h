@@ -14,7 +14,9 @@
  *  - Pointers named h_* are host memory, d_* are device memory on the
  *    current CUDA device; neither is retained after the call returns.
  *  - Opaque handles (sfft_keys, sfft_plan, sfft_batch, sfft_server) are
- *    owned by the library and released with the matching *_free call.
+ *    owned by the library and released with the matching *_free call. A plan
+ *    or batch lives on the CUDA device current when it was created; evaluating
+ *    it with another device current fails with EINVAL.
  *  - Scheme parameters: q = 2^ell with ell a multiple of 32; Ng = (n+1) ell.
  *    A ciphertext is stored compressed, C' = BitDecomp^-1(C): Ng rows of
  *    (n+1) elements of Z_q, each as L = ell/32 uint32 limbs, least

@@ -141,6 +141,9 @@ int run_levels(const Shape& s, const DeviceProgram& dp, uint32_t l0, uint32_t l1
   if (!d_in || !d_out) return fail(SFFT_EINVAL, "null buffer");
   const uint32_t levels = (uint32_t)(dp.level_off.size() - 1);
   if (l0 > l1 || l1 > levels) return fail(SFFT_EINVAL, "level range out of bounds");
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess || cur != dp.device)
+    return fail(SFFT_EINVAL, "the current CUDA device is not the one the plan was created on");
   if (scratch_bytes < dp.scratch_bytes || (dp.scratch_bytes && !d_scratch))
     return fail(SFFT_EINVAL, "scratch buffer too small");
   KArgs a = make_args(s);
@@ -205,6 +208,7 @@ int make_device_program(const Program& p, DeviceProgram* dp) {
     dp->patch = (PatchDesc*)ptr;
     dp->n_patch = p.patch.size();
   }
+  if (cudaGetDevice(&dp->device) != cudaSuccess) dp->device = -1;
   dp->level_off = p.level_off;
   dp->lin_start = p.lin_start;
   dp->scratch_slots = p.scratch_slots;

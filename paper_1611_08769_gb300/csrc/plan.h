@@ -28,6 +28,7 @@ struct DeviceProgram {
   bool tc = false;               // levels run on the tensor-core kernel
   uint64_t scratch_bytes = 0;    // wire slots + expanded B operands
   uint64_t bx_off = 0;           // offset of the expanded B operands in scratch
+  int device = -1;               // CUDA device that holds the program (current at creation)
 };
 
 // Reads and clears the device error word (synchronises the stream).

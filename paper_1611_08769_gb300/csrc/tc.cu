@@ -760,15 +760,29 @@ bool make_tc_shape(const KArgs& a, TcShape* t) {
   return true;
 }
 
+// Per device: SM count, and whether the kernels' shared-memory opt-in is set
+// (a function attribute holds per device).
+struct TcDevice {
+  int sms = 0;
+  bool configured = false;
+};
+std::mutex g_tc_mu;
+TcDevice g_tc_dev[64];
+
+TcDevice* tc_device() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(g_tc_mu);
+  TcDevice& d = g_tc_dev[dev];
+  if (d.sms == 0 && (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+                     d.sms <= 0))
+    d.sms = 0;
+  return &d;
+}
+
 int sm_count() {
-  static int n = 0;
-  if (n == 0) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
-      n = 148;
-  }
-  return n;
+  TcDevice* d = tc_device();
+  return d && d->sms > 0 ? d->sms : 148;
 }
 
 }  // namespace
@@ -859,17 +873,21 @@ int launch_tc(const KArgs& a, cudaStream_t st, bool withhold) {
   TcShape t{};
   if (!make_tc_shape(a, &t)) return fail(SFFT_EPARAM, "tensor-core kernel does not support this shape");
   if (!a.bx) return fail(SFFT_EINVAL, "tensor-core kernel needs its B expansion buffer");
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_gate_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kMaxSmem);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_gate_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)kMaxSmem);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_expand_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
-    if (e != cudaSuccess) return cuda_fail(e, "tc smem attribute");
-    configured = true;
+  TcDevice* dev = tc_device();
+  if (!dev) return fail(SFFT_ECUDA, "no current CUDA device");
+  {
+    std::lock_guard<std::mutex> lk(g_tc_mu);
+    if (!dev->configured) {
+      cudaError_t e = cudaFuncSetAttribute(k_gate_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)kMaxSmem);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_gate_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kMaxSmem);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_expand_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+      if (e != cudaSuccess) return cuda_fail(e, "tc smem attribute");
+      dev->configured = true;
+    }
   }
   const uint64_t chunk = a.bx_shared ? a.n : tc_chunk_gates(a);
   for (uint64_t c0 = 0; c0 < a.n; c0 += chunk) {

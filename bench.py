@@ -851,6 +851,28 @@ def run_fft(args, config, steps, warmup, world, rank, local, cpu_leg=True, plain
     gate_ms, expand_ms, launches, gates_timed = batch.timing()
     batch.set_timing(False)
 
+    # the persistent form (one launch across levels) on the same inputs, where
+    # the small-ciphertext kernel runs a circuit without linear gates
+    persistent = None
+    if info["gate_kernel"] == sf.KERNEL_SM and not variant_of(config)["xcarry"]:
+        pbatch = sf.Batch(params, reqs, flags | sf.BATCH_PERSISTENT)
+        pscr = torch.empty(max(1, pbatch.info["scratch_bytes"] // 4), dtype=torch.int32, device="cuda")
+        p_out = torch.empty_like(d_out)
+        run_pb = lambda: pbatch.eval(d_in, p_out, pscr, stream)  # noqa: E731
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                run_pb()
+            pbatch.check(stream)
+            pms = timed(run_pb, steps)
+            pbatch.check(stream)
+            run_b()
+        torch.cuda.synchronize()
+        persistent = {"ms_per_step": pms, "value": len(items) * 1000.0 / pms, "unit": "FFT/s",
+                      "launches_per_step": 3, "scratch_bytes": pbatch.info["scratch_bytes"],
+                      "speedup_vs_level_launches": ms / pms,
+                      "outputs_equal_level_by_level": bool(torch.equal(p_out, d_out))}
+        del pbatch, pscr, p_out
+
     # plain level-by-level evaluator on the same workload (per-request plans)
     plain = None
     if plain_leg:
@@ -916,6 +938,7 @@ def run_fft(args, config, steps, warmup, world, rank, local, cpu_leg=True, plain
             "roofline": roofline(params, info["gate_kernel"], gate_ms, launches, gates_timed,
                                  info["tc_columns"], expand_ms),
             "plain": plain,
+            "persistent": persistent,
             "cpu_baseline": cpu,
             "e2e": {"value": world * len(items) * 1000.0 / e2e_ms, "unit": "FFT/s",
                     "h2d_bytes_per_step": info["inputs"] * cw * 4,
@@ -957,8 +980,8 @@ def main():
         torch.cuda.empty_cache()
         b = run_fft(args, "batch256_p2", 3, 2, 1, 0, local, cpu_leg=False, plain_leg=True)
         line["batch"] = {k: b[k] for k in ("metric", "value", "unit", "ms_per_step", "gates_per_s",
-                                           "config", "roofline", "plain", "e2e", "gpu_launches",
-                                           "clocks")}
+                                           "config", "roofline", "plain", "persistent", "e2e",
+                                           "gpu_launches", "clocks")}
         torch.cuda.empty_cache()
         srv = run_serve(args, "serve_p2", requests=args.serve_requests, emit=False)
         line["serve"] = {k: srv[k] for k in ("metric", "value", "unit", "config", "latency_ms",

@@ -384,6 +384,18 @@ typedef struct sfft_request {
  * re-captured when a third appears or the stream changes; needs a non-default
  * stream). flags: SFFT_PLAN_* too. */
 #define SFFT_BATCH_NO_GRAPH 4u
+/* Persistent form: every product of the batch runs in ONE launch of the
+ * small-ciphertext kernel (Ng <= 256; EPARAM otherwise, and for circuits with
+ * linear gates such as SFFT_PLAN_XCARRY). Its CTAs claim gates in program
+ * order; a gate starts once the gates that produced its two operands have
+ * stored them and every gate two levels up is done (scratch slots are reused
+ * two levels after their last read, so neighbouring levels overlap), and
+ * publishes itself when its outputs are written. Every wait is bounded; one
+ * that runs out stops the launch with SFFT_ETIMEOUT (sfft_batch_check).
+ * Per evaluation one small launch restarts the claim counter and the level
+ * counts first and the output fix-ups follow: three launches in all, graph-
+ * replayed like the level-by-level form. Results are identical. */
+#define SFFT_BATCH_PERSISTENT 128u
 int sfft_batch_create(const sfft_params* p, const sfft_request* reqs, uint32_t count,
                       uint32_t flags, sfft_batch** out);
 int sfft_batch_info_get(const sfft_batch* b, sfft_plan_info* info);

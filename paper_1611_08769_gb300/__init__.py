@@ -351,6 +351,7 @@ class Plan:
 
 
 BATCH_NO_GRAPH = 4
+BATCH_PERSISTENT = 128   # one persistent launch across levels (sfft.h SFFT_BATCH_PERSISTENT)
 
 
 class Batch:

@@ -17,6 +17,7 @@
 #include <cstring>
 #include <memory>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "common.h"
@@ -104,8 +105,82 @@ struct GraphCache {
   }
 };
 
-int run_graph(GraphCache* cache, const Shape& s, const DeviceProgram& dp, const uint32_t* d_in,
-              uint32_t* d_out, uint32_t* d_scratch, uint64_t scratch_bytes, cudaStream_t st) {
+// Persistent form, per run: the epoch advances (gate flags of earlier runs stay
+// behind it), the claim counter and the per-level counts restart.
+__global__ void k_persist_begin(uint32_t* epoch, uint32_t* claim, unsigned long long* ldone, uint32_t levels) {
+  if (threadIdx.x == 0) {
+    *epoch += 1u;
+    *claim = 0u;
+  }
+  for (uint32_t l = threadIdx.x; l < levels; l += blockDim.x) ldone[l] = 0ull;
+}
+
+// Device state of the persistent form (sfft_batch with SFFT_BATCH_PERSISTENT).
+struct PersistState {
+  uint32_t* glev = nullptr;       // level of every gate
+  GateDeps* gdep = nullptr;       // the gates that produced its A and B (0xFFFFFFFF: an input)
+  uint32_t* lwidth = nullptr;     // gates per level
+  unsigned long long* ldone = nullptr;
+  uint32_t* gflag = nullptr;
+  uint32_t* claim = nullptr;
+  uint32_t* epoch = nullptr;
+  uint32_t levels = 0;
+  ~PersistState() {
+    cudaFree(glev);
+    cudaFree(gdep);
+    cudaFree(lwidth);
+    cudaFree(ldone);
+    cudaFree(gflag);
+    cudaFree(claim);
+    cudaFree(epoch);
+  }
+};
+
+// Every product of the program in one launch of the small-ciphertext kernel
+// (gates claimed in program order, levels overlapping by one), then the
+// output fix-ups.
+int run_persistent(const Shape& s, const DeviceProgram& dp, const PersistState& ps, const uint32_t* d_in,
+                   uint32_t* d_out, uint32_t* d_scratch, uint64_t scratch_bytes, cudaStream_t st,
+                   Timer* tm) {
+  if (!d_in || !d_out) return fail(SFFT_EINVAL, "null buffer");
+  if (scratch_bytes < dp.scratch_bytes || (dp.scratch_bytes && !d_scratch))
+    return fail(SFFT_EINVAL, "scratch buffer too small");
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess || cur != dp.device)
+    return fail(SFFT_EINVAL, "the current CUDA device is not the one the batch was created on");
+  k_persist_begin<<<1, 256, 0, st>>>(ps.epoch, ps.claim, ps.ldone, ps.levels);
+  count_launches(1);
+  KArgs a = make_args(s);
+  a.base[REG_SCRATCH] = d_scratch;
+  a.base[REG_IN] = const_cast<uint32_t*>(d_in);
+  a.base[REG_OUT] = d_out;
+  a.err = dp.err;
+  a.kernel = KERNEL_SM;
+  a.desc = dp.desc;
+  a.aux = dp.aux;
+  a.n = dp.level_off.back();
+  a.glev = ps.glev;
+  a.gdep = ps.gdep;
+  a.lwidth = ps.lwidth;
+  a.ldone = ps.ldone;
+  a.gflag = ps.gflag;
+  a.claim = ps.claim;
+  a.epoch = ps.epoch;
+  const bool timed = tm && tm->on && a.n;
+  a.timer = timed ? tm : nullptr;
+  int rc = launch_gates(a, st);
+  if (rc) return rc;
+  if (timed) {
+    tm->launches++;
+    tm->products += a.n;
+  }
+  a.timer = nullptr;
+  return launch_fixups(dp.fix, dp.n_fix, a, st);
+}
+
+int run_graph(GraphCache* cache, const Shape& s, const DeviceProgram& dp, const PersistState* ps,
+              const uint32_t* d_in, uint32_t* d_out, uint32_t* d_scratch, uint64_t scratch_bytes,
+              cudaStream_t st) {
   if (!st) return fail(SFFT_EINVAL, "graph replay needs a non-default stream");
   const void* key[4] = {d_in, d_out, d_scratch, st};
   GraphEntry* gc = nullptr;
@@ -125,7 +200,8 @@ int run_graph(GraphCache* cache, const Shape& s, const DeviceProgram& dp, const 
     cudaGraph_t graph;
     cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
-    int rc = run_program(s, dp, d_in, d_out, d_scratch, scratch_bytes, st, nullptr);
+    int rc = ps ? run_persistent(s, dp, *ps, d_in, d_out, d_scratch, scratch_bytes, st, nullptr)
+                : run_program(s, dp, d_in, d_out, d_scratch, scratch_bytes, st, nullptr);
     e = cudaStreamEndCapture(st, &graph);
     if (rc) return rc;
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
@@ -150,6 +226,7 @@ struct sfft_batch {
   sfft::DeviceProgram dev;
   sfft::GraphCache graph;
   sfft::Timer timer;
+  std::unique_ptr<sfft::PersistState> persist;   // one launch across levels, when requested
   bool use_graph = true;
   uint64_t fft_products = 0;
   // host pipeline: copy streams and the events that order them with the
@@ -158,6 +235,7 @@ struct sfft_batch {
   cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_done[2] = {nullptr, nullptr},
               ev_out[2] = {nullptr, nullptr};
   ~sfft_batch() {
+    sfft::free_device_program(&dev);
     for (int k = 0; k < 2; k++)
       for (cudaEvent_t ev : {ev_in[k], ev_done[k], ev_out[k]})
         if (ev) cudaEventDestroy(ev);
@@ -167,6 +245,67 @@ struct sfft_batch {
 };
 
 using namespace sfft;
+
+namespace {
+
+// The persistent form's device state: every gate's level and the gates that
+// produced its operands (the last writer of each slot before it, in program
+// order), the level widths, and zeroed flags and counters.
+int make_persistent(sfft_batch* b) {
+  const Program& m = b->merged;
+  KArgs k = make_args(b->s);
+  k.kernel = b->dev.kernel;
+  if (gate_kernel_for(k) != KERNEL_SM)
+    return fail(SFFT_EPARAM, "the persistent form runs on the small-ciphertext kernel (Ng <= 256)");
+  const uint32_t levels = (uint32_t)(m.level_off.size() - 1);
+  for (uint32_t l = 0; l < levels; l++)
+    if (m.lin_start[l] != m.level_off[l + 1])
+      return fail(SFFT_EPARAM, "the persistent form takes circuits without linear gates");
+  const uint64_t n = m.desc.size();
+  if (n >= 0xFFFFFFFFull) return fail(SFFT_EINVAL, "batch too large for the persistent form");
+  std::vector<uint32_t> glev(n), lwidth(levels);
+  std::vector<GateDeps> gdep(n);
+  std::unordered_map<uint32_t, uint32_t> writer;   // slot reference -> last gate that wrote it
+  writer.reserve(2 * n);
+  auto dep_of = [&](uint32_t ref) -> uint32_t {
+    if ((ref >> 30) == REG_IN) return 0xFFFFFFFFu;   // a program input
+    auto it = writer.find(ref);
+    return it == writer.end() ? 0xFFFFFFFFu : it->second;
+  };
+  for (uint32_t l = 0; l < levels; l++) {
+    lwidth[l] = (uint32_t)(m.level_off[l + 1] - m.level_off[l]);
+    for (uint64_t g = m.level_off[l]; g < m.level_off[l + 1]; g++) {
+      glev[g] = l;
+      gdep[g] = GateDeps{dep_of(m.desc[g].a), dep_of(m.desc[g].b)};
+    }
+    // writes after every read of the level (a level never writes what it reads)
+    for (uint64_t g = m.level_off[l]; g < m.level_off[l + 1]; g++) {
+      if (m.desc[g].o0 != REF_NONE) writer[m.desc[g].o0] = (uint32_t)g;
+      if (m.desc[g].o1 != REF_NONE) writer[m.desc[g].o1] = (uint32_t)g;
+    }
+  }
+  std::unique_ptr<PersistState> ps(new PersistState);
+  ps->levels = levels;
+  int rc;
+  void* p = nullptr;
+  if ((rc = upload(glev.data(), n * sizeof(uint32_t), &p))) return rc;
+  ps->glev = (uint32_t*)p;
+  if ((rc = upload(gdep.data(), n * sizeof(GateDeps), &p))) return rc;
+  ps->gdep = (GateDeps*)p;
+  if ((rc = upload(lwidth.data(), levels * sizeof(uint32_t), &p))) return rc;
+  ps->lwidth = (uint32_t*)p;
+  cudaError_t e = cudaMalloc((void**)&ps->ldone, std::max<uint32_t>(levels, 1) * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&ps->gflag, std::max<uint64_t>(n, 1) * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&ps->claim, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&ps->epoch, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMemset(ps->gflag, 0, std::max<uint64_t>(n, 1) * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMemset(ps->epoch, 0, sizeof(uint32_t));
+  if (e != cudaSuccess) return cuda_fail(e, "persistent batch state");
+  b->persist = std::move(ps);
+  return SFFT_OK;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -187,7 +326,9 @@ int sfft_batch_create(const sfft_params* p, const sfft_request* reqs, uint32_t c
     if (!build_fft(&c, reqs[r].N1, reqs[r].N2, reqs[r].F, reqs[r].f))
       return fail(SFFT_EINVAL, "request " + std::to_string(r) + ": invalid FFT shape");
     Program prog;
-    compile(c, b->s, &prog);
+    // the persistent form overlaps neighbouring levels: slots are reused two
+    // levels after their last read
+    compile(c, b->s, &prog, 0, (flags & SFFT_BATCH_PERSISTENT) ? 2u : 1u);
     if (!prog.noise_ok && !(flags & SFFT_PLAN_ALLOW_NOISY))
       return fail(SFFT_EPARAM, "request " + std::to_string(r) + ": static noise bound reaches q/4");
     std::array<uint64_t, 4> o = {scr, in, outp, 0};
@@ -219,6 +360,7 @@ int sfft_batch_create(const sfft_params* p, const sfft_request* reqs, uint32_t c
   b->dev.scratch_bytes =
       scratch_layout(b->s, scr, b->merged.max_width, b->dev.tc, &b->dev.bx_off);
   b->use_graph = !(flags & SFFT_BATCH_NO_GRAPH);
+  if ((flags & SFFT_BATCH_PERSISTENT) && (rc = make_persistent(b.get()))) return rc;
   *out = b.release();
   return SFFT_OK;
 }
@@ -257,7 +399,9 @@ int sfft_batch_eval(sfft_batch* b, const uint32_t* d_in, uint32_t* d_out, uint32
   if (!b) return fail(SFFT_EINVAL, "batch is NULL");
   cudaStream_t st = (cudaStream_t)stream;
   if (b->use_graph && !b->timer.on)
-    return run_graph(&b->graph, b->s, b->dev, d_in, d_out, d_scratch, scratch_bytes, st);
+    return run_graph(&b->graph, b->s, b->dev, b->persist.get(), d_in, d_out, d_scratch, scratch_bytes, st);
+  if (b->persist)
+    return run_persistent(b->s, b->dev, *b->persist, d_in, d_out, d_scratch, scratch_bytes, st, &b->timer);
   return run_program(b->s, b->dev, d_in, d_out, d_scratch, scratch_bytes, st, &b->timer);
 }
 

@@ -7,6 +7,11 @@
 
 namespace sfft {
 
+// Producers of a gate's two operands (persistent launch; 0xFFFFFFFF: an input).
+struct GateDeps {
+  uint32_t a, b;
+};
+
 struct KArgs {
   const GateDesc* desc;
   const GateAux* aux;
@@ -20,6 +25,19 @@ struct KArgs {
   uint8_t* bx;           // tensor-core kernel: expanded B operands (scratch)
   uint32_t bx_shared;    // 1: every gate has the same B operand (expanded once)
   void* timer;           // host: the Timer recording this launch's kernels, or null
+  // Persistent launch across levels (small-ciphertext kernel, batches): gates
+  // are claimed in program order from *claim; gate g waits until its
+  // operands' producers are done (gflag[dep] >= *epoch; dep 0xFFFFFFFF: a
+  // program input) and every gate of level glev[g] - 2 is done (ldone[l] >=
+  // *epoch x lwidth[l]), then publishes gflag[g] = *epoch and counts itself in
+  // ldone[glev[g]] once its outputs are stored. Null glev: one level per launch.
+  const uint32_t* glev;
+  const GateDeps* gdep;
+  const uint32_t* lwidth;
+  unsigned long long* ldone;
+  uint32_t* gflag;
+  uint32_t* claim;
+  const uint32_t* epoch;
 };
 
 // KERNEL_TC: the general tensor-core kernel (B expanded by a separate pass);

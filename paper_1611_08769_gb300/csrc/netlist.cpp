@@ -636,7 +636,8 @@ uint16_t adjusted(Code k, bool negA, bool negB) {
 
 uint64_t level_cap(const CircuitSpec& spec) { return spec.op == kOpRefresh ? kRefreshLevelCap : 0; }
 
-void compile(const Circuit& c, const Shape& s, Program* prog, uint64_t width_cap) {
+void compile(const Circuit& c, const Shape& s, Program* prog, uint64_t width_cap, uint32_t reuse_gap) {
+  if (reuse_gap < 1) reuse_gap = 1;
   std::vector<char> ln, lp;
   liveness(c, &ln, &lp);
   const size_t nn = c.depth.size();
@@ -705,7 +706,7 @@ void compile(const Circuit& c, const Shape& s, Program* prog, uint64_t width_cap
     if (!lp[p]) continue;
     (c.products[p].is_add ? lin_level : by_level)[plev[p]].push_back((uint32_t)p);
   }
-  std::vector<std::vector<uint32_t>> release(maxlev + 2);
+  std::vector<std::vector<uint32_t>> release(maxlev + reuse_gap + 1);
   std::vector<uint32_t> free_slots;
   uint32_t next_slot = 0;
   prog->desc.clear();
@@ -730,7 +731,7 @@ void compile(const Circuit& c, const Shape& s, Program* prog, uint64_t width_cap
             slot = next_slot++;
           }
           home[node] = make_ref(REG_SCRATCH, slot);
-          release[last[node]].push_back(node);
+          release[last[node] + reuse_gap - 1].push_back(node);   // free from level last + gap
         }
         GateDesc d;
         GateAux x;

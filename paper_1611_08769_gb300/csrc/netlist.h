@@ -175,8 +175,11 @@ struct Program {
 // width_cap > 0 bounds the products of a level: a product whose inputs are
 // ready at level l runs at the first level >= l with room (creation order),
 // which bounds the ciphertexts alive at once for circuits whose ready set is
-// very wide (refresh).
-void compile(const Circuit& c, const Shape& s, Program* prog, uint64_t width_cap = 0);
+// very wide (refresh). A scratch slot last read at level l is reused from
+// level l + reuse_gap on (1: the next level; 2 for programs whose levels
+// overlap by one on the device, the persistent batch).
+void compile(const Circuit& c, const Shape& s, Program* prog, uint64_t width_cap = 0,
+             uint32_t reuse_gap = 1);
 
 // The level width cap a plan of this kind compiles with (0: none).
 uint64_t level_cap(const CircuitSpec& spec);

@@ -27,8 +27,9 @@
 // element's limb carries, as the integer kernel does (half adders and ORs,
 // the codes the circuits mostly use, by shorter dedicated carry chains).
 //
-// Roles (one persistent CTA of 18 warps per SM; CTA b takes the gates b,
-// b + grid, ...; a gate is one or two 128-row items):
+// Roles (one persistent CTA of 18 warps per SM, 19 in the persistent form;
+// CTA b takes the gates b, b + grid, ..., or in the persistent form claims
+// chunks of gates in program order; a gate is one or two 128-row items):
 //   warp 0       MMA issuer: per item Ng / 16 tcgen05.mma (M 128, N the digit
 //                columns, K 16) from the A stage in tensor memory and the B
 //                image in shared memory, then commits
@@ -41,7 +42,11 @@
 //                it, mask the bits, store them to the item's A stage
 //   warps 8..15  epilogue: accumulators -> output words, written in place
 //                over the slot's A' and B' rows; the gate's outputs then leave
-//                by two bulk stores
+//                by two bulk stores (lane 0 of warp 8). In the persistent form
+//                the outputs go straight to their global rows and
+//   warp 18      (persistent form) publishes each finished gate: one
+//                gpu-scope fence, the gate's done flag and its level's count,
+//                off the epilogue's path
 // Every wait is bounded (about 2 s); on timeout the kernel records
 // KERR_MMA_TIMEOUT, drains its own MMAs and bulk stores, frees its tensor
 // memory and returns.
@@ -62,11 +67,13 @@ namespace sfft {
 namespace {
 
 constexpr int kSmThreads = 576;                  // 18 warps
+constexpr int kSmThreadsPersist = 608;           // + the publishing warp
 constexpr uint32_t kSmTmemCols = 512;
 constexpr uint32_t kSmMaxSlots = 8, kSmMaxAStages = 4, kSmMaxAcc = 8;
 constexpr uint32_t kSmConvWarps = 4, kSmConvThreads = 128;   // warps 2, 3, 16, 17
-constexpr uint32_t kSmExpWarp0 = 4, kSmEpiWarp0 = 8, kSmEpiWarps = 8;
+constexpr uint32_t kSmExpWarp0 = 4, kSmEpiWarp0 = 8, kSmEpiWarps = 8, kSmPubWarp = 18;
 constexpr uint32_t kSmBars = 64;                 // mbarrier slots (8 bytes each)
+constexpr uint32_t kClaim = 4;                   // gates per claim of the persistent launch
 constexpr uint32_t kSmMaxSmem = 232448;          // 227 KB opt-in per CTA
 
 // Bounded wait on every lane of the warp; true on every lane iff all saw the
@@ -191,8 +198,46 @@ struct SmShape {
 // Slot metadata: the gate's descriptor, written by the producer with its
 // bulk copies (visible to every role once raw_full completes).
 struct SlotMeta {
-  uint32_t a, b, o0, o1, code, flags, kind, pad;
+  uint32_t a, b, o0, o1, code, flags, kind, gate;   // gate kNoGate: no more gates (persistent form)
 };
+constexpr uint32_t kNoGate = 0xFFFFFFFFu;
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Persistent launch: waits (bounded, ~2 s, also ending once `flag` is set)
+// until *p >= target, with acquire semantics.
+__device__ __forceinline__ bool wait_at_least32(const uint32_t* p, uint32_t target, volatile int* flag) {
+  if (ld_acquire_u32(p) >= target) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 0; it < kSpinLimit; it++) {
+    __nanosleep(64);
+    if (ld_acquire_u32(p) >= target) return true;
+    if ((it & 63u) == 63u && (*flag || global_ns() - t0 > kWaitNs)) return false;
+  }
+  return false;
+}
+
+__device__ __forceinline__ bool wait_at_least64(const unsigned long long* p, unsigned long long target,
+                                                volatile int* flag) {
+  if (ld_acquire_u64(p) >= target) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 0; it < kSpinLimit; it++) {
+    __nanosleep(64);
+    if (ld_acquire_u64(p) >= target) return true;
+    if ((it & 63u) == 63u && (*flag || global_ns() - t0 > kWaitNs)) return false;
+  }
+  return false;
+}
 
 // Gate kinds with a specialised epilogue (codes as stored, after the
 // compiler absorbed complemented operands): a half adder (output 0 XOR =
@@ -241,6 +286,21 @@ __device__ __forceinline__ void st_elem(uint32_t* p, const uint32_t (&v)[LL]) {
   }
 }
 
+// One element of LL words to a global row (explicit global stores; the
+// shared-memory rows go through st_elem).
+template <int LL>
+__device__ __forceinline__ void st_elem_global(uint32_t* p, const uint32_t (&v)[LL]) {
+  if constexpr (LL == 4) {
+    asm volatile("st.global.v4.u32 [%0], {%1, %2, %3, %4};" ::"l"(p), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3])
+                 : "memory");
+  } else if constexpr (LL == 2) {
+    asm volatile("st.global.v2.u32 [%0], {%1, %2};" ::"l"(p), "r"(v[0]), "r"(v[1]) : "memory");
+  } else {
+#pragma unroll
+    for (int k = 0; k < LL; k++) asm volatile("st.global.u32 [%0], %1;" ::"l"(p + k), "r"(v[k]) : "memory");
+  }
+}
+
 // A row of W <= 8 words into registers (16-byte loads when W is a multiple of 4).
 __device__ __forceinline__ void ld_row(const uint32_t* row, uint32_t W, uint32_t (&x)[8]) {
   if ((W & 3u) == 0) {
@@ -270,16 +330,19 @@ __device__ __forceinline__ void ld_row(const uint32_t* row, uint32_t W, uint32_t
 //   raw_full[s]   the gate's A' and B' landed (producer's transaction count)
 //   img_full[s]   the B image is written (four converter warps)
 //   epi_done[s]   every epilogue warp wrote its outputs for the gate
-//   slot_free[s]  the gate's outputs left the slot (bulk stores read it)
+//   slot_free[s]  the gate's outputs left the slot (bulk stores read it), or
+//                 were published (persistent form); the storer arrives
 //   afull[a]      an item's A stage is written (four expander warps)
 //   afree[a]      the item's MMAs are done (commit)
 //   accfull[c]    an item's MMAs are done (commit)
 //   accfree[c]    the epilogue read the accumulator (eight warps)
 // Warps: 0 issuer, 1 producer, 2 3 16 17 converters (one per SM
-// sub-partition), 4..7 expanders, 8..15 epilogue.
+// sub-partition), 4..7 expanders, 8..15 epilogue, 18 publisher (persistent
+// form). The level form knows its gate count; the persistent form's roles
+// stop at an end marker in the ring.
 // ---------------------------------------------------------------------------
-template <int LL>
-__global__ void __launch_bounds__(kSmThreads, 1) k_gate_sm(KArgs a, SmShape t) {
+template <int LL, bool PERSIST>
+__global__ void __launch_bounds__(PERSIST ? kSmThreadsPersist : kSmThreads, 1) k_gate_sm(KArgs a, SmShape t) {
   constexpr uint32_t kEll = 32u * LL, kDig = 4u * LL;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -300,10 +363,10 @@ __global__ void __launch_bounds__(kSmThreads, 1) k_gate_sm(KArgs a, SmShape t) {
   const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint64_t ngates = a.n;
   if (blockIdx.x >= ngates) return;
-  const uint32_t nloc = (uint32_t)((ngates - 1 - blockIdx.x) / gridDim.x + 1);
+  constexpr bool persist = PERSIST;   // one launch across levels
+  const uint32_t nloc = persist ? 0u : (uint32_t)((ngates - 1 - blockIdx.x) / gridDim.x + 1);
   const uint32_t items = nloc * t.mt;
   const uint32_t W = a.W, Ng = a.Ng, NP1 = W / LL;
-  auto gate_of = [&](uint32_t j) { return (uint64_t)blockIdx.x + (uint64_t)j * gridDim.x; };
   auto img_of = [&](uint32_t s) { return smem + s * t.slot_bytes; };
   auto araw_of = [&](uint32_t s) { return (uint32_t*)(smem + s * t.slot_bytes + t.img_bytes); };
   auto braw_of = [&](uint32_t s) {
@@ -339,11 +402,16 @@ __global__ void __launch_bounds__(kSmThreads, 1) k_gate_sm(KArgs a, SmShape t) {
     const uint32_t atom_units = (t.ncols * 128u) >> 4;   // descriptor units between atoms
     bool ok = true;
     uint32_t j = 0, m = 0, st = 0, stph = 0, acc = 0, accph = 0;
-    for (uint32_t it = 0; it < items; it++) {
+    for (uint32_t it = 0;; it++) {
+      if (!persist && it >= items) break;
       const uint32_t s = j % t.nslots;
+      if (persist && m == 0) {   // a gate's image (the end marker's slot is released too)
+        if (!warp_wait(&img_full[s], (j / t.nslots) & 1u, sflag)) { ok = false; break; }
+        if (meta[s].gate == kNoGate) break;
+      }
       if (!warp_wait(&accfree[acc], accph, sflag)) { ok = false; break; }
       if (!warp_wait(&afull[st], stph, sflag)) { ok = false; break; }
-      if (m == 0 && !warp_wait(&img_full[s], (j / t.nslots) & 1u, sflag)) { ok = false; break; }
+      if (!persist && m == 0 && !warp_wait(&img_full[s], (j / t.nslots) & 1u, sflag)) { ok = false; break; }
       tc_fence_after();
       const uint32_t d = tmem + acc * t.ncols;
       const uint32_t at = tmem + t.acc0 + st * t.acols;
@@ -369,27 +437,100 @@ __global__ void __launch_bounds__(kSmThreads, 1) k_gate_sm(KArgs a, SmShape t) {
 
   } else if (warp == 1) {
     // -------------------------------------------------------------- producer
-    if (lane == 0) {
-      bool ok = true;
-      for (uint32_t j = 0; j < nloc; j++) {
-        const uint32_t s = j % t.nslots, use = j / t.nslots;
-        if (use && !mbar_wait_flag(&slot_free[s], (use - 1) & 1u, sflag)) { ok = false; break; }
-        const uint64_t g = gate_of(j);
-        const GateDesc gd = a.desc[g];
-        const GateAux ax = a.aux[g];
-        SlotMeta md;
-        md.a = gd.a; md.b = gd.b; md.o0 = gd.o0; md.o1 = gd.o1;
-        md.code = ax.code; md.flags = ax.flags; md.pad = 0;
-        const uint32_t c0 = ax.code & 0xFFFFu, c1 = ax.code >> 16;
-        md.kind = (c0 == kCodeXOR && c1 == kCodeAND) ? kKindHA
-                  : (c0 == kCodeOR && gd.o1 == REF_NONE) ? kKindOR : kKindGeneric;
-        meta[s] = md;   // published by the arrival below (release)
-        mbar_expect_tx(&raw_full[s], 2u * t.raw_bytes);
-        bulk_g2s(araw_of(s), ct_ptr(a, gd.a), t.raw_bytes, &raw_full[s]);
-        bulk_g2s(braw_of(s), ct_ptr(a, gd.b), t.raw_bytes, &raw_full[s]);
+    // a gate into ring slot s: its descriptor to the slot's metadata, its two
+    // operands by bulk copies completing on raw_full[s]
+    auto load_gate = [&](uint32_t s, uint64_t g, const GateDesc& gd, const GateAux& ax) {
+      SlotMeta md;
+      md.a = gd.a; md.b = gd.b; md.o0 = gd.o0; md.o1 = gd.o1;
+      md.code = ax.code; md.flags = ax.flags;
+      const uint32_t c0 = ax.code & 0xFFFFu, c1 = ax.code >> 16;
+      md.kind = (c0 == kCodeXOR && c1 == kCodeAND) ? kKindHA
+                : (c0 == kCodeOR && gd.o1 == REF_NONE) ? kKindOR : kKindGeneric;
+      md.gate = (uint32_t)g;
+      meta[s] = md;   // published by the arrival below (release)
+      mbar_expect_tx(&raw_full[s], 2u * t.raw_bytes);
+      bulk_g2s(araw_of(s), ct_ptr(a, gd.a), t.raw_bytes, &raw_full[s]);
+      bulk_g2s(braw_of(s), ct_ptr(a, gd.b), t.raw_bytes, &raw_full[s]);
+    };
+    auto end_marker = [&](uint32_t s) {   // the other roles stop at this slot
+      meta[s].gate = kNoGate;
+      mbar_arrive(&raw_full[s]);
+    };
+    bool ok = true;
+    if constexpr (!persist) {
+      // gates b, b + grid, b + 2 grid, ... (one lane)
+      if (lane == 0) {
+        for (uint32_t j = 0; j < nloc; j++) {
+          const uint32_t s = j % t.nslots, use = j / t.nslots;
+          if (use && !mbar_wait_flag(&slot_free[s], (use - 1) & 1u, sflag)) { ok = false; break; }
+          const uint64_t g = blockIdx.x + (uint64_t)j * gridDim.x;
+          load_gate(s, g, a.desc[g], a.aux[g]);
+        }
       }
-      if (!ok) *sflag = 1;
+    } else {
+      // chunks of kClaim consecutive gates claimed in program order; lane k
+      // fetches gate k's descriptor and checks its readiness, all lanes at
+      // once; the gates are loaded in order, waiting (bounded) only for one
+      // whose operands' producers, or whose level two up, were not done yet
+      const uint32_t ep = *a.epoch;
+      uint32_t j = 0;
+      bool done = false;
+      while (ok && !done) {
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(a.claim, kClaim);
+        base = __shfl_sync(0xFFFFFFFFu, base, 0);
+        const uint64_t gk = (uint64_t)base + lane;
+        const bool mine = lane < kClaim && gk < ngates;
+        GateDesc gd{0, 0, REF_NONE, REF_NONE};
+        GateAux ax{0, 0};
+        uint32_t lev = 0;
+        GateDeps dep{kNoGate, kNoGate};
+        bool ready = true;
+        if (mine) {
+          gd = a.desc[gk];
+          ax = a.aux[gk];
+          lev = a.glev[gk];
+          dep = a.gdep[gk];
+          const uint32_t need = lev >= 2 ? a.lwidth[lev - 2] : 0u;
+          ready = (lev < 2 || ld_acquire_u64(&a.ldone[lev - 2]) >= need) &&
+                  (dep.a == kNoGate || ld_acquire_u32(&a.gflag[dep.a]) >= ep) &&
+                  (dep.b == kNoGate || ld_acquire_u32(&a.gflag[dep.b]) >= ep);
+        }
+        for (uint32_t k = 0; k < kClaim; k++) {
+          const uint32_t s = j % t.nslots, use = j / t.nslots;
+          bool sok = true;
+          if (lane == 0 && use) sok = mbar_wait_flag(&slot_free[s], (use - 1) & 1u, sflag);
+          if (!__shfl_sync(0xFFFFFFFFu, (int)sok, 0)) { ok = false; break; }
+          const uint64_t g = (uint64_t)base + k;
+          if (g >= ngates) {
+            if (lane == 0) end_marker(s);
+            done = true;
+            break;
+          }
+          bool dok = true;
+          if (lane == k && !ready)
+            dok = (lev < 2 || wait_at_least64(&a.ldone[lev - 2], a.lwidth[lev - 2], sflag)) &&
+                  (dep.a == kNoGate || wait_at_least32(&a.gflag[dep.a], ep, sflag)) &&
+                  (dep.b == kNoGate || wait_at_least32(&a.gflag[dep.b], ep, sflag));
+          if (!__shfl_sync(0xFFFFFFFFu, (int)dok, k)) { ok = false; break; }
+          GateDesc d;
+          d.a = __shfl_sync(0xFFFFFFFFu, gd.a, k);
+          d.b = __shfl_sync(0xFFFFFFFFu, gd.b, k);
+          d.o0 = __shfl_sync(0xFFFFFFFFu, gd.o0, k);
+          d.o1 = __shfl_sync(0xFFFFFFFFu, gd.o1, k);
+          GateAux x;
+          x.code = __shfl_sync(0xFFFFFFFFu, ax.code, k);
+          x.flags = __shfl_sync(0xFFFFFFFFu, ax.flags, k);
+          __syncwarp();   // lane k's acquire before lane 0's loads
+          if (lane == 0) {
+            asm volatile("fence.proxy.async.global;" ::: "memory");   // before the bulk loads read them
+            load_gate(s, g, d, x);
+          }
+          j++;
+        }
+      }
     }
+    if (!ok && lane == 0) *sflag = 1;
 
   } else if (warp == 2 || warp == 3 || warp == 16 || warp == 17) {
     // ----------------------------------------------------------- B converters
@@ -398,9 +539,15 @@ __global__ void __launch_bounds__(kSmThreads, 1) k_gate_sm(KArgs a, SmShape t) {
     // eight swizzled row bases of the pair are formed once)
     const uint32_t ct = (warp < 4 ? warp - 2u : warp - 14u) * 32u + lane;
     bool ok = true;
-    for (uint32_t j = 0; j < nloc; j++) {
+    for (uint32_t j = 0;; j++) {
+      if (!persist && j >= nloc) break;
       const uint32_t s = j % t.nslots;
       if (!warp_wait(&raw_full[s], (j / t.nslots) & 1u, sflag)) { ok = false; break; }
+      if (persist && meta[s].gate == kNoGate) {   // release the issuer's wait on this slot, then stop
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&img_full[s]);
+        break;
+      }
       const uint32_t* B = braw_of(s);
       uint8_t* img = img_of(s);
       for (uint32_t P = ct; P < Ng / 2; P += kSmConvThreads) {
@@ -442,9 +589,13 @@ __global__ void __launch_bounds__(kSmThreads, 1) k_gate_sm(KArgs a, SmShape t) {
     const uint32_t q = warp & 3u;
     bool ok = true;
     uint32_t j = 0, m = 0, st = 0, stph = 0;
-    for (uint32_t it = 0; it < items; it++) {
+    for (uint32_t it = 0;; it++) {
+      if (!persist && it >= items) break;
       const uint32_t s = j % t.nslots;
-      if (m == 0 && !warp_wait(&raw_full[s], (j / t.nslots) & 1u, sflag)) { ok = false; break; }
+      if (m == 0) {
+        if (!warp_wait(&raw_full[s], (j / t.nslots) & 1u, sflag)) { ok = false; break; }
+        if (persist && meta[s].gate == kNoGate) break;
+      }
       if (it >= t.nastages && !warp_wait(&afree[st], stph ^ 1u, sflag)) { ok = false; break; }
       tc_fence_after();
       const uint32_t r0 = m * 128u + q * 32u;
@@ -488,7 +639,7 @@ __global__ void __launch_bounds__(kSmThreads, 1) k_gate_sm(KArgs a, SmShape t) {
     // -------------------------------------------------------------- epilogue
     // warp (q, h): rows 32 q .. 32 q + 31 of each item, elements h, h + 2, ...
     const uint32_t q = warp & 3u, h = (warp - kSmEpiWarp0) >> 2;
-    const bool storer = warp == kSmEpiWarp0 && lane == 0;
+    const bool storer = !persist && warp == kSmEpiWarp0 && lane == 0;
     const uint32_t tlane = tmem + ((q * 32u) << 16);
     // every accumulator slot starts at the bias (this warp's lanes and
     // elements); the arrival frees each slot for its first item
@@ -504,10 +655,14 @@ __global__ void __launch_bounds__(kSmThreads, 1) k_gate_sm(KArgs a, SmShape t) {
       for (uint32_t c = 0; c < t.nacc; c++) mbar_arrive(&accfree[c]);
     bool ok = true;
     uint32_t j = 0, m = 0, acc = 0, accph = 0;
-    for (uint32_t it = 0; it < items; it++) {
+    for (uint32_t it = 0;; it++) {
+      if (!persist && it >= items) break;
       const uint32_t s = j % t.nslots;
       // the slot's metadata was published with raw_full (still this gate's phase)
-      if (m == 0 && !warp_wait(&raw_full[s], (j / t.nslots) & 1u, sflag)) { ok = false; break; }
+      if (m == 0) {
+        if (!warp_wait(&raw_full[s], (j / t.nslots) & 1u, sflag)) { ok = false; break; }
+        if (persist && meta[s].gate == kNoGate) break;
+      }
       if (!warp_wait(&accfull[acc], accph, sflag)) { ok = false; break; }
       tc_fence_after();
       const SlotMeta md = meta[s];
@@ -518,6 +673,11 @@ __global__ void __launch_bounds__(kSmThreads, 1) k_gate_sm(KArgs a, SmShape t) {
         const uint32_t i = r0 + lane;
         uint32_t* Arow = araw_of(s) + i * W;
         uint32_t* Brow = braw_of(s) + i * W;
+        // persistent form: outputs straight to their global rows (published
+        // after a fence, no bulk-store completion to wait for); otherwise in
+        // place over the slot's rows, leaving by bulk stores
+        uint32_t* G0 = persist && one ? ct_ptr(a, md.o0) + (uint64_t)i * W : nullptr;
+        uint32_t* G1 = persist && two ? ct_ptr(a, md.o1) + (uint64_t)i * W : nullptr;
         for (uint32_t e = h; e < NP1; e += 2) {
           uint32_t v[16];
           tmem_ld16(taddr + e * kDig, v);
@@ -583,8 +743,13 @@ __global__ void __launch_bounds__(kSmThreads, 1) k_gate_sm(KArgs a, SmShape t) {
               o1[wl] = (uint32_t)t1;
             }
           }
-          if (one) st_elem<LL>(Arow + e * LL, o0);   // output 0 over A'
-          if (two) st_elem<LL>(Brow + e * LL, o1);   // output 1 over B'
+          if (persist) {
+            if (one) st_elem_global<LL>(G0 + e * LL, o0);   // output 0
+            if (two) st_elem_global<LL>(G1 + e * LL, o1);   // output 1
+          } else {
+            if (one) st_elem<LL>(Arow + e * LL, o0);
+            if (two) st_elem<LL>(Brow + e * LL, o1);
+          }
         }
       }
       // the slot's next item starts again from the bias (every warp, its own
@@ -598,8 +763,10 @@ __global__ void __launch_bounds__(kSmThreads, 1) k_gate_sm(KArgs a, SmShape t) {
       if (lane == 0) mbar_arrive(&accfree[acc]);
       if (++acc == t.nacc) { acc = 0; accph ^= 1u; }
       if (++m == t.mt) {
-        // the gate is complete: its outputs leave by bulk stores
-        fence_proxy_async_smem();
+        // the gate is complete; the arrival orders this warp's output stores
+        // before the publisher's gpu-scope fence (persistent form), or the
+        // in-place outputs before the bulk stores read them
+        if (!persist) fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) mbar_arrive(&epi_done[s]);
         bool bad = false;
@@ -614,12 +781,38 @@ __global__ void __launch_bounds__(kSmThreads, 1) k_gate_sm(KArgs a, SmShape t) {
             bad = true;
           }
         }
-        if (__any_sync(0xFFFFFFFFu, bad)) { ok = false; break; }   // the whole warp leaves together
+        if (!persist && __any_sync(0xFFFFFFFFu, bad)) { ok = false; break; }   // the whole warp leaves together
         m = 0;
         j++;
       }
     }
     if (storer) bulk_wait_all();
+    if (!ok && lane == 0) *sflag = 1;
+
+  } else if (persist && warp == kSmPubWarp) {
+    // -------------------------------------------------------------- publisher
+    // gates in ring order (lane 0 works, the warp keeps step)
+    bool ok = true;
+    const uint32_t ep = persist ? *a.epoch : 0u;
+    for (uint32_t j = 0;; j++) {
+      const uint32_t s = j % t.nslots, ph = (j / t.nslots) & 1u;
+      if (!warp_wait(&raw_full[s], ph, sflag)) { ok = false; break; }
+      if (meta[s].gate == kNoGate) break;
+      if (!warp_wait(&epi_done[s], ph, sflag)) { ok = false; break; }
+      if (lane == 0) {
+        const uint32_t gate = meta[s].gate;
+        const uint32_t lev = a.glev[gate];
+        // every epilogue warp's output stores happen before its arrival on
+        // epi_done, observed above; one gpu-scope fence makes both writes
+        // below release patterns (flag for the gate's readers, count for the
+        // level window)
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
+        asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(a.gflag + gate), "r"(ep) : "memory");
+        asm volatile("red.relaxed.gpu.global.add.u64 [%0], 1;" ::"l"(a.ldone + lev) : "memory");
+        mbar_arrive(&slot_free[s]);
+      }
+      __syncwarp();
+    }
     if (!ok && lane == 0) *sflag = 1;
   }
 
@@ -698,10 +891,12 @@ int sm_device(SmDevice** out, int* ordinal) {
   SmDevice& d = g_sm_dev[dev];
   if (!d.configured) {
     e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gate_sm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmMaxSmem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gate_sm<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmMaxSmem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gate_sm<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmMaxSmem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gate_sm<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmMaxSmem);
+    const void* fns[] = {(const void*)k_gate_sm<1, false>, (const void*)k_gate_sm<2, false>,
+                         (const void*)k_gate_sm<3, false>, (const void*)k_gate_sm<4, false>,
+                         (const void*)k_gate_sm<1, true>,  (const void*)k_gate_sm<2, true>,
+                         (const void*)k_gate_sm<3, true>,  (const void*)k_gate_sm<4, true>};
+    for (const void* fn : fns)
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmMaxSmem);
     if (e != cudaSuccess) return cuda_fail(e, "small-ciphertext kernel attributes");
     d.configured = true;
   }
@@ -739,11 +934,20 @@ int launch_gates_sm_slots(const KArgs& a, uint32_t nslots, cudaStream_t st) {
   const uint64_t blocks = std::min<uint64_t>(a.n, (uint64_t)dev->sms);
   Timer* tm = static_cast<Timer*>(a.timer);
   if (tm) cudaEventRecord(tm->next(kTimeGate), st);
-  switch (a.L) {
-    case 1: k_gate_sm<1><<<(unsigned)blocks, kSmThreads, t.smem_bytes, st>>>(a, t); break;
-    case 2: k_gate_sm<2><<<(unsigned)blocks, kSmThreads, t.smem_bytes, st>>>(a, t); break;
-    case 3: k_gate_sm<3><<<(unsigned)blocks, kSmThreads, t.smem_bytes, st>>>(a, t); break;
-    default: k_gate_sm<4><<<(unsigned)blocks, kSmThreads, t.smem_bytes, st>>>(a, t); break;
+  if (a.glev) {   // one launch across levels
+    switch (a.L) {
+      case 1: k_gate_sm<1, true><<<(unsigned)blocks, kSmThreadsPersist, t.smem_bytes, st>>>(a, t); break;
+      case 2: k_gate_sm<2, true><<<(unsigned)blocks, kSmThreadsPersist, t.smem_bytes, st>>>(a, t); break;
+      case 3: k_gate_sm<3, true><<<(unsigned)blocks, kSmThreadsPersist, t.smem_bytes, st>>>(a, t); break;
+      default: k_gate_sm<4, true><<<(unsigned)blocks, kSmThreadsPersist, t.smem_bytes, st>>>(a, t); break;
+    }
+  } else {
+    switch (a.L) {
+      case 1: k_gate_sm<1, false><<<(unsigned)blocks, kSmThreads, t.smem_bytes, st>>>(a, t); break;
+      case 2: k_gate_sm<2, false><<<(unsigned)blocks, kSmThreads, t.smem_bytes, st>>>(a, t); break;
+      case 3: k_gate_sm<3, false><<<(unsigned)blocks, kSmThreads, t.smem_bytes, st>>>(a, t); break;
+      default: k_gate_sm<4, false><<<(unsigned)blocks, kSmThreads, t.smem_bytes, st>>>(a, t); break;
+    }
   }
   if (tm) cudaEventRecord(tm->next(kTimeGate), st);
   count_launches(1);

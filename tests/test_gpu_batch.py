@@ -157,3 +157,69 @@ def test_pipelined_host_evaluation(pset):
         batch.check(stream)
         torch.cuda.synchronize()
         assert torch.equal(h_out, ref_out.cpu())
+
+
+PERSIST_REQS = [(16, 1, 16, 8), (8, 1, 8, 4), (4, 4, 8, 3), (32, 1, 16, 8), (8, 8, 16, 8),
+                (64, 1, 16, 8), (4, 1, 6, 2)]
+
+
+@pytest.mark.parametrize("graph", [True, False])
+def test_persistent_batch_equals_level_by_level(graph):
+    """One persistent launch across all levels (gates claimed in program
+    order, levels overlapping by one) against the level-by-level batch on the
+    same inputs: identical ciphertexts, on three evaluations in a row (the
+    epochs of the gates' done flags advance)."""
+    sp = sf.param_set("P2")
+    _, cts, _ = _inputs(sp, PERSIST_REQS)
+    d_in = torch.cat(cts)
+    stream = torch.cuda.Stream()
+    ref_b = sf.Batch(sp, PERSIST_REQS)
+    ref = torch.empty((ref_b.info["outputs"], ref_b.info["ct_words"]), dtype=torch.int32, device="cuda")
+    scr = torch.empty(max(1, ref_b.info["scratch_bytes"] // 4), dtype=torch.int32, device="cuda")
+    with torch.cuda.stream(stream):
+        ref_b.eval(d_in, ref, scr, stream)
+        ref_b.check(stream)
+    pb = sf.Batch(sp, PERSIST_REQS, sf.BATCH_PERSISTENT | (0 if graph else sf.BATCH_NO_GRAPH))
+    assert pb.info["gate_kernel"] == sf.KERNEL_SM and pb.info["products"] == ref_b.info["products"]
+    pscr = torch.empty(max(1, pb.info["scratch_bytes"] // 4), dtype=torch.int32, device="cuda")
+    for _ in range(3):
+        out = torch.full_like(ref, -1)
+        with torch.cuda.stream(stream):
+            pb.eval(d_in, out, pscr, stream)
+            pb.check(stream)
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref)
+
+
+def test_persistent_batch_request_matches_oracle():
+    sp = sf.param_set("P2")
+    p = gsw.Params(sp.n, sp.ell, sp.m, sp.chi)
+    reqs = [(8, 1, 8, 4), (16, 1, 8, 4), (4, 1, 6, 2)]
+    keys, cts, sigs = _inputs(sp, reqs)
+    b = sf.Batch(sp, reqs, sf.BATCH_PERSISTENT)
+    d_in = torch.cat(cts)
+    out = torch.empty((b.info["outputs"], b.info["ct_words"]), dtype=torch.int32, device="cuda")
+    scr = torch.empty(max(1, b.info["scratch_bytes"] // 4), dtype=torch.int32, device="cuda")
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        b.eval(d_in, out, scr, stream)
+        b.check(stream)
+    r = 0
+    N, _, F, f = reqs[r]
+    re_, im_ = sigs[r]
+    ko = gsw.Keys(p, 100 + r % 3)
+    ins = []
+    for k in range(N):
+        for part, x in enumerate((re_[k], im_[k])):
+            for bit_i, bit in enumerate(fx.to_bits(fx.quantize(x, F, f), F)):
+                ins.append(gsw.encrypt(ko, bit, 7 + r, (2 * k + part) * F + bit_i))
+    want = evaluate.eval_encrypted(circuit.fft_circuit(N, 1, F, f), p, ins)
+    got = out[b.out_off[r]:b.out_off[r] + len(want)].cpu().numpy().view(np.uint32)
+    assert np.array_equal(got.reshape(want.shape), want)
+
+
+def test_persistent_batch_rejects_unsupported_forms():
+    with pytest.raises(sf.SfftError):   # general tensor-core kernel (Ng > 256)
+        sf.Batch(sf.param_set("P1", 224), [(8, 1, 8, 4)], sf.BATCH_PERSISTENT)
+    with pytest.raises(sf.SfftError):   # linear (exclusive-carry) gates
+        sf.Batch(sf.param_set("P2"), [(8, 1, 8, 4)], sf.BATCH_PERSISTENT | sf.PLAN_XCARRY)

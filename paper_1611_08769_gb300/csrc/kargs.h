@@ -29,8 +29,9 @@ struct KArgs {
   // are claimed in program order from *claim; gate g waits until its
   // operands' producers are done (gflag[dep] >= *epoch; dep 0xFFFFFFFF: a
   // program input) and every gate of level glev[g] - 2 is done (ldone[l] >=
-  // *epoch x lwidth[l]), then publishes gflag[g] = *epoch and counts itself in
-  // ldone[glev[g]] once its outputs are stored. Null glev: one level per launch.
+  // lwidth[l]; the counts and the claim are reset before each run), then
+  // publishes gflag[g] = *epoch and counts itself in ldone[glev[g]] once its
+  // outputs are stored. Null glev: one level per launch.
   const uint32_t* glev;
   const GateDeps* gdep;
   const uint32_t* lwidth;

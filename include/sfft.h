@@ -319,6 +319,29 @@ int sfft_program_eval_plain(const sfft_params* p, uint32_t N1, uint32_t N2, uint
                             uint32_t f, uint32_t flags, const uint8_t* h_in_bits,
                             uint8_t* h_out_bits);
 
+/* Host-only listing of the compiled device program of the FFT (N1 x N2
+ * points, F-bit words with f fraction bits; Sec. 5's circuit, its gates
+ * grouped into the levels that run in parallel, Sec. 7), gate by gate in
+ * program order (level by level; no device memory touched). flags:
+ * SFFT_PLAN_* as for sfft_plan_create; with SFFT_BATCH_PERSISTENT the circuit
+ * is compiled as the persistent batch form compiles it (scratch slots reused
+ * two levels after their last read) and dep_a / dep_b name the gates the
+ * persistent launch waits for. Call with h_gates NULL for *count, then with
+ * capacity >= *count. EPARAM: SFFT_BATCH_PERSISTENT with a circuit that has
+ * linear gates. */
+typedef struct sfft_gate_record {
+  uint32_t a, b;          /* operands: region << 30 | slot (0 scratch, 1 inputs, 2 outputs) */
+  uint32_t o0, o1;        /* outputs in the same form; 0xFFFFFFFF: none */
+  uint32_t code;          /* nibbles c0..c3 of output 0 in bits 0..15, of output 1 in 16..31 */
+  uint32_t flags;         /* bit 0: A complemented (A~ = P - A) */
+  uint32_t level;         /* the gate's level, from 0 */
+  uint32_t dep_a, dep_b;  /* gates that last wrote a / b before this level (0xFFFFFFFF: a
+                             program input, or no persistent schedule was asked for) */
+} sfft_gate_record;
+int sfft_program_gates(const sfft_params* p, uint32_t N1, uint32_t N2, uint32_t F, uint32_t f,
+                       uint32_t flags, sfft_gate_record* h_gates, uint64_t capacity,
+                       uint64_t* count);
+
 /* Host-only hooks of a refresh program: statistics, and a plaintext run with
  * key bits h_key_bits (n ell + 1 bytes) and the rows ell - 1 of the count
  * refreshed ciphertexts h_rows ((n + 1) ell / 32 words each), writing count

@@ -186,6 +186,22 @@ def program_eval_plain(params, N1, N2, F, f, in_bits, xcarry=False, nand=False, 
     return out
 
 
+# one sfft_gate_record (include/sfft.h)
+GATE_RECORD = np.dtype([("a", "<u4"), ("b", "<u4"), ("o0", "<u4"), ("o1", "<u4"), ("code", "<u4"),
+                        ("flags", "<u4"), ("level", "<u4"), ("dep_a", "<u4"), ("dep_b", "<u4")])
+
+
+def program_gates(params, N1, N2, F, f, flags=0):
+    """Host-only listing of the compiled FFT program, one GATE_RECORD per gate
+    in program order (sfft_program_gates); flags as for sfft_program_gates."""
+    n = ctypes.c_uint64(0)
+    check(lib().sfft_program_gates(ctypes.byref(params), N1, N2, F, f, flags, None, 0, ctypes.byref(n)))
+    out = np.zeros(n.value, dtype=GATE_RECORD)
+    check(lib().sfft_program_gates(ctypes.byref(params), N1, N2, F, f, flags,
+                                   ctypes.c_void_p(out.ctypes.data), n.value, ctypes.byref(n)))
+    return out
+
+
 def word_min_ell(op, F, f, n=1, chi=1, xcarry=False, nand=False):
     return int(lib().sfft_word_min_ell(op, F, f, n, chi, _variant(xcarry, nand)))
 

@@ -258,32 +258,13 @@ int make_persistent(sfft_batch* b) {
   if (gate_kernel_for(k) != KERNEL_SM)
     return fail(SFFT_EPARAM, "the persistent form runs on the small-ciphertext kernel (Ng <= 256)");
   const uint32_t levels = (uint32_t)(m.level_off.size() - 1);
-  for (uint32_t l = 0; l < levels; l++)
-    if (m.lin_start[l] != m.level_off[l + 1])
-      return fail(SFFT_EPARAM, "the persistent form takes circuits without linear gates");
   const uint64_t n = m.desc.size();
   if (n >= 0xFFFFFFFFull) return fail(SFFT_EINVAL, "batch too large for the persistent form");
-  std::vector<uint32_t> glev(n), lwidth(levels);
+  std::vector<uint32_t> glev, dep_a, dep_b, lwidth;
+  if (!persistent_schedule(m, &glev, &dep_a, &dep_b, &lwidth))
+    return fail(SFFT_EPARAM, "the persistent form takes circuits without linear gates");
   std::vector<GateDeps> gdep(n);
-  std::unordered_map<uint32_t, uint32_t> writer;   // slot reference -> last gate that wrote it
-  writer.reserve(2 * n);
-  auto dep_of = [&](uint32_t ref) -> uint32_t {
-    if ((ref >> 30) == REG_IN) return 0xFFFFFFFFu;   // a program input
-    auto it = writer.find(ref);
-    return it == writer.end() ? 0xFFFFFFFFu : it->second;
-  };
-  for (uint32_t l = 0; l < levels; l++) {
-    lwidth[l] = (uint32_t)(m.level_off[l + 1] - m.level_off[l]);
-    for (uint64_t g = m.level_off[l]; g < m.level_off[l + 1]; g++) {
-      glev[g] = l;
-      gdep[g] = GateDeps{dep_of(m.desc[g].a), dep_of(m.desc[g].b)};
-    }
-    // writes after every read of the level (a level never writes what it reads)
-    for (uint64_t g = m.level_off[l]; g < m.level_off[l + 1]; g++) {
-      if (m.desc[g].o0 != REF_NONE) writer[m.desc[g].o0] = (uint32_t)g;
-      if (m.desc[g].o1 != REF_NONE) writer[m.desc[g].o1] = (uint32_t)g;
-    }
-  }
+  for (uint64_t g = 0; g < n; g++) gdep[g] = GateDeps{dep_a[g], dep_b[g]};
   std::unique_ptr<PersistState> ps(new PersistState);
   ps->levels = levels;
   int rc;

@@ -792,4 +792,37 @@ void compile(const Circuit& c, const Shape& s, Program* prog, uint64_t width_cap
   prog->noise_ok = prog->noise_bits <= s.ell - 2;
 }
 
+bool persistent_schedule(const Program& m, std::vector<uint32_t>* glev, std::vector<uint32_t>* dep_a,
+                         std::vector<uint32_t>* dep_b, std::vector<uint32_t>* lwidth) {
+  const uint32_t levels = (uint32_t)(m.level_off.size() - 1);
+  for (uint32_t l = 0; l < levels; l++)
+    if (m.lin_start[l] != m.level_off[l + 1]) return false;
+  const uint64_t n = m.desc.size();
+  glev->assign(n, 0);
+  dep_a->assign(n, 0xFFFFFFFFu);
+  dep_b->assign(n, 0xFFFFFFFFu);
+  lwidth->assign(levels, 0);
+  std::unordered_map<uint32_t, uint32_t> writer;   // slot reference -> last gate that wrote it
+  writer.reserve(2 * n);
+  auto dep_of = [&](uint32_t ref) -> uint32_t {
+    if ((ref >> 30) == REG_IN) return 0xFFFFFFFFu;   // a program input
+    auto it = writer.find(ref);
+    return it == writer.end() ? 0xFFFFFFFFu : it->second;
+  };
+  for (uint32_t l = 0; l < levels; l++) {
+    (*lwidth)[l] = (uint32_t)(m.level_off[l + 1] - m.level_off[l]);
+    for (uint64_t g = m.level_off[l]; g < m.level_off[l + 1]; g++) {
+      (*glev)[g] = l;
+      (*dep_a)[g] = dep_of(m.desc[g].a);
+      (*dep_b)[g] = dep_of(m.desc[g].b);
+    }
+    // writes after every read of the level (a level never writes what it reads)
+    for (uint64_t g = m.level_off[l]; g < m.level_off[l + 1]; g++) {
+      if (m.desc[g].o0 != REF_NONE) writer[m.desc[g].o0] = (uint32_t)g;
+      if (m.desc[g].o1 != REF_NONE) writer[m.desc[g].o1] = (uint32_t)g;
+    }
+  }
+  return true;
+}
+
 }  // namespace sfft

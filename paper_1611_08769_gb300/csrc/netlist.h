@@ -181,6 +181,15 @@ struct Program {
 void compile(const Circuit& c, const Shape& s, Program* prog, uint64_t width_cap = 0,
              uint32_t reuse_gap = 1);
 
+// The persistent form's schedule of a compiled program (one launch across
+// levels): each gate's level, the gates that last wrote its two operands
+// before its level (0xFFFFFFFF: a program input), and each level's width. A
+// gate may start once both producers are done and every gate two levels up
+// is done; with reuse_gap 2 that window also orders every slot's reuse after
+// its last read. False (nothing written) for programs with linear gates.
+bool persistent_schedule(const Program& m, std::vector<uint32_t>* glev, std::vector<uint32_t>* dep_a,
+                         std::vector<uint32_t>* dep_b, std::vector<uint32_t>* lwidth);
+
 // The level width cap a plan of this kind compiles with (0: none).
 uint64_t level_cap(const CircuitSpec& spec);
 

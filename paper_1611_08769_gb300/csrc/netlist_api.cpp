@@ -216,6 +216,42 @@ int sfft_refresh_eval_plain(const sfft_params* p, uint64_t count, uint32_t flags
   return program_eval_plain(p, refresh_spec(p, count), flags, h_key_bits, h_out_bits, h_rows);
 }
 
+int sfft_program_gates(const sfft_params* p, uint32_t N1, uint32_t N2, uint32_t F, uint32_t f,
+                       uint32_t flags, sfft_gate_record* h_gates, uint64_t capacity, uint64_t* count) {
+  if (!count) return fail(SFFT_EINVAL, "count is NULL");
+  const CircuitSpec spec = fft_spec(N1, N2, F, f);
+  Shape s;
+  Circuit c;
+  Program prog;
+  int rc = make_shape(p, &s, false);
+  if (rc) return rc;
+  if ((rc = build_circuit(&c, spec, flags))) return rc;
+  const bool persist = (flags & SFFT_BATCH_PERSISTENT) != 0;
+  compile(c, s, &prog, level_cap(spec), persist ? 2u : 1u);
+  const uint64_t n = prog.desc.size();
+  *count = n;
+  if (!h_gates) return SFFT_OK;
+  if (capacity < n) return fail(SFFT_EINVAL, "capacity below the gate count");
+  std::vector<uint32_t> glev, dep_a, dep_b, lwidth;
+  if (persist && !persistent_schedule(prog, &glev, &dep_a, &dep_b, &lwidth))
+    return fail(SFFT_EPARAM, "the persistent form takes circuits without linear gates");
+  const uint32_t levels = (uint32_t)(prog.level_off.size() - 1);
+  for (uint32_t l = 0; l < levels; l++)
+    for (uint64_t g = prog.level_off[l]; g < prog.level_off[l + 1]; g++) {
+      sfft_gate_record& r = h_gates[g];
+      r.a = prog.desc[g].a;
+      r.b = prog.desc[g].b;
+      r.o0 = prog.desc[g].o0;
+      r.o1 = prog.desc[g].o1;
+      r.code = prog.aux[g].code;
+      r.flags = prog.aux[g].flags;
+      r.level = l;
+      r.dep_a = persist ? dep_a[g] : 0xFFFFFFFFu;
+      r.dep_b = persist ? dep_b[g] : 0xFFFFFFFFu;
+    }
+  return SFFT_OK;
+}
+
 int sfft_twiddles(uint32_t M, uint32_t f, int64_t* h_wr, int64_t* h_wi) {
   if (M < 2 || (M & (M - 1)) || f > 62) return fail(SFFT_EINVAL, "M must be a power of two >= 2, f <= 62");
   if (!h_wr || !h_wi) return fail(SFFT_EINVAL, "null argument");

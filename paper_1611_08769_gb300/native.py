@@ -59,6 +59,8 @@ SIGNATURES = {
                                   P(sfft_plan_info)]),
     "sfft_program_eval_plain": (c_i32, [P(sfft_params), c_u32, c_u32, c_u32, c_u32, c_u32, c_u8_p,
                                         c_u8_p]),
+    "sfft_program_gates": (c_i32, [P(sfft_params), c_u32, c_u32, c_u32, c_u32, c_u32, c_void_p, c_u64,
+                                   P(c_u64)]),
     "sfft_word_plan_create": (c_i32, [P(sfft_params), c_u32, c_u64, c_u32, c_u32, c_u32,
                                       P(c_void_p)]),
     "sfft_word_min_ell": (c_u32, [c_u32, c_u32, c_u32, c_u32, c_u32, c_u32]),

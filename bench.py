@@ -976,12 +976,19 @@ def main():
                    cpu_leg=not args.no_cpu_baseline, plain_leg=not args.no_plain)
     if rank == 0 and world == 1 and args.config == DEFAULT_CONFIG and not args.no_extra:
         # the baseline metric's other forms on the same box: batched vs plain
-        # on the 256-request batch, and the continuous-batching server
+        # on the 256-request batch, one narrow program, and the
+        # continuous-batching server
         torch.cuda.empty_cache()
         b = run_fft(args, "batch256_p2", 3, 2, 1, 0, local, cpu_leg=False, plain_leg=True)
         line["batch"] = {k: b[k] for k in ("metric", "value", "unit", "ms_per_step", "gates_per_s",
                                            "config", "roofline", "plain", "persistent", "e2e",
                                            "gpu_launches", "clocks")}
+        torch.cuda.empty_cache()
+        # a narrow program: one 64-point FFT at ell 128, level by level and as
+        # one persistent launch (where the one-launch form pays)
+        nb = run_fft(args, "fft64_16bit_p2", 10, 3, 1, 0, local, cpu_leg=False, plain_leg=False)
+        line["narrow"] = {k: nb[k] for k in ("metric", "value", "unit", "ms_per_step", "gates_per_s",
+                                             "config", "persistent", "gpu_launches", "clocks")}
         torch.cuda.empty_cache()
         srv = run_serve(args, "serve_p2", requests=args.serve_requests, emit=False)
         line["serve"] = {k: srv[k] for k in ("metric", "value", "unit", "config", "latency_ms",

@@ -845,7 +845,9 @@ uint32_t sm_smem_bytes(uint32_t slot_bytes, uint32_t nslots) {
 
 // nslots 0: the tuned or default ring depth.
 bool make_sm_shape(const KArgs& a, uint32_t nslots, SmShape* t) {
-  if (a.Ng < 128 || a.Ng > 256 || a.L == 0 || a.L > 4 || a.ell != 32 * a.L || a.W % a.L) return false;
+  // Ng 64 or 96: one 128-row item whose upper lane quarters carry no rows
+  // (their expanders and epilogue warps skip the work, not the barriers)
+  if (a.Ng < 64 || a.Ng > 256 || a.L == 0 || a.L > 4 || a.ell != 32 * a.L || a.W % a.L) return false;
   const uint32_t NP1 = a.W / a.L;
   if (NP1 < 2 || a.W > 8) return false;
   t->mt = (a.Ng + 127) / 128;

@@ -29,13 +29,14 @@ def built():
     sfbuild.build()
 
 
-@pytest.mark.parametrize("pset,kernel", [("P0", sf.KERNEL_INT), ("P2", sf.KERNEL_SM),
-                                         ("P1", sf.KERNEL_TC)])
-def test_noalloc_matches_regular_entry_point_twice(pset, kernel):
+@pytest.mark.parametrize("pset,flags,kernel", [("P0", sf.PLAN_INT_KERNEL, sf.KERNEL_INT),
+                                               ("P0", 0, sf.KERNEL_SM), ("P2", 0, sf.KERNEL_SM),
+                                               ("P1", 0, sf.KERNEL_TC)])
+def test_noalloc_matches_regular_entry_point_twice(pset, flags, kernel):
     """Each gate kernel through the fixed array: the integer kernel (toy
-    parameters), the small-ciphertext tensor-core kernel (ell 128) and the
-    general tensor-core kernel with its B expansion inside the array (noisy
-    ell 224, the 8-point circuit's smallest)."""
+    parameters, forced), the small-ciphertext tensor-core kernel (ell 32 and
+    128) and the general tensor-core kernel with its B expansion inside the
+    array (noisy ell 224, the 8-point circuit's smallest)."""
     N, F, f = 8, 8, 4
     sp = sf.param_set(pset, sf.min_ell(N, 1, F, f, n=1, chi=1) if pset == "P1" else None)
     keys = sf.keygen(sp, 21)
@@ -44,7 +45,7 @@ def test_noalloc_matches_regular_entry_point_twice(pset, kernel):
     pub = torch.from_numpy(keys.public().view(np.int32)).cuda()
     d_in = torch.empty((N * 2 * F, cw), dtype=torch.int32, device="cuda")
     sf.encrypt_bits_device(sp, pub, re_, im_, F, f, 22, d_in)
-    plan = sf.Plan(sp, N, 1, F, f)
+    plan = sf.Plan(sp, N, 1, F, f, flags)
     assert plan.info["gate_kernel"] == kernel
     assert plan.info["scratch_bytes"] <= sf.lib().sfft_noalloc_scratch_bytes()
     ref = torch.empty((plan.info["outputs"], cw), dtype=torch.int32, device="cuda")

@@ -196,13 +196,13 @@ def measured_peaks():
 # a 512-gate level at n = 1, ell = 1056, inputs larger than L2), keyed by
 # (n, ell). The algorithmic bytes of a product at these parameters are 3.07 MB:
 # the expanded B operand once, the A and B rows, the two output rows.
-TC_DRAM_BYTES_PER_PRODUCT = {(1, 1056): 3.120e6}
+TC_DRAM_BYTES_PER_PRODUCT = {(1, 1056): 3.101e6}
 # The same for the small-ciphertext kernel (k_gate_sm), from an ncu capture of
 # one launch over a 40,000-gate level of half adders at n = 1, ell = 128 (1.31
-# GB, larger than L2): 656.4 MB read + 608.9 MB written. Half adders write two
+# GB, larger than L2): 656.4 MB read + 608.4 MB written. Half adders write two
 # outputs; an FFT level mixes in single-output gates, so this figure is an
 # upper estimate for FFT levels.
-SM_DRAM_BYTES_PER_PRODUCT = {(1, 128): 31632.0}
+SM_DRAM_BYTES_PER_PRODUCT = {(1, 128): 31620.0}
 
 
 def expand_bytes_per_product(params):

@@ -442,6 +442,11 @@ int sfft_batch_eval_host_pipelined(sfft_batch* b, const uint32_t* const* h_in,
                                    uint32_t* const* d_in, uint32_t* const* d_out,
                                    uint32_t* d_scratch, uint64_t scratch_bytes, void* stream);
 int sfft_batch_check(sfft_batch* b, void* stream);
+/* Test hook of the persistent form: sets its 32-bit run counter (the epoch
+ * that readiness flags are compared with) and waits for the copy on stream.
+ * Each run first advances the counter; at its wrap the flags are cleared and
+ * the counter restarts at 1. EINVAL for a batch without SFFT_BATCH_PERSISTENT. */
+int sfft_batch_set_epoch(sfft_batch* b, uint32_t epoch, void* stream);
 /* Per-launch event timing (graph replay is bypassed while timing is on). */
 int sfft_batch_set_timing(sfft_batch* b, int on);
 int sfft_batch_timing(sfft_batch* b, double* gate_ms, double* expand_ms, uint64_t* launches,

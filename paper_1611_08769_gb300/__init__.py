@@ -415,6 +415,10 @@ class Batch:
     def check(self, stream=None):
         check(lib().sfft_batch_check(self._h, _stream(stream)))
 
+    def set_epoch(self, epoch, stream=None):
+        """Test hook: the persistent form's run counter (sfft_batch_set_epoch)."""
+        check(lib().sfft_batch_set_epoch(self._h, epoch, _stream(stream)))
+
     def set_timing(self, on):
         check(lib().sfft_batch_set_timing(self._h, 1 if on else 0))
 

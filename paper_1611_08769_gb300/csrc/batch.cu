@@ -107,9 +107,18 @@ struct GraphCache {
 
 // Persistent form, per run: the epoch advances (gate flags of earlier runs stay
 // behind it), the claim counter and the per-level counts restart.
-__global__ void k_persist_begin(uint32_t* epoch, uint32_t* claim, unsigned long long* ldone, uint32_t levels) {
+// Before each persistent run: the next epoch, the claim counter and the level
+// counts restarted. Gates compare their producers' flags with the epoch, so a
+// wrap of the 32-bit epoch would make old flags look current: at the wrap the
+// flags are cleared and the epoch restarts at 1 (once in 2^32 runs).
+__global__ void k_persist_begin(uint32_t* epoch, uint32_t* claim, unsigned long long* ldone, uint32_t levels,
+                                uint32_t* gflag, uint64_t n) {
+  const uint32_t e = *epoch;
+  __syncthreads();   // every thread has read the old epoch
+  if (e == 0xFFFFFFFFu)
+    for (uint64_t g = threadIdx.x; g < n; g += blockDim.x) gflag[g] = 0u;
   if (threadIdx.x == 0) {
-    *epoch += 1u;
+    *epoch = e == 0xFFFFFFFFu ? 1u : e + 1u;
     *claim = 0u;
   }
   for (uint32_t l = threadIdx.x; l < levels; l += blockDim.x) ldone[l] = 0ull;
@@ -148,7 +157,7 @@ int run_persistent(const Shape& s, const DeviceProgram& dp, const PersistState& 
   int cur = -1;
   if (cudaGetDevice(&cur) != cudaSuccess || cur != dp.device)
     return fail(SFFT_EINVAL, "the current CUDA device is not the one the batch was created on");
-  k_persist_begin<<<1, 256, 0, st>>>(ps.epoch, ps.claim, ps.ldone, ps.levels);
+  k_persist_begin<<<1, 256, 0, st>>>(ps.epoch, ps.claim, ps.ldone, ps.levels, ps.gflag, dp.level_off.back());
   count_launches(1);
   KArgs a = make_args(s);
   a.base[REG_SCRATCH] = d_scratch;
@@ -460,6 +469,15 @@ int sfft_batch_eval_host_pipelined(sfft_batch* b, const uint32_t* const* h_in,
 int sfft_batch_check(sfft_batch* b, void* stream) {
   if (!b) return fail(SFFT_EINVAL, "batch is NULL");
   return check_device_error(b->dev.err, (cudaStream_t)stream);
+}
+
+int sfft_batch_set_epoch(sfft_batch* b, uint32_t epoch, void* stream) {
+  if (!b) return fail(SFFT_EINVAL, "batch is NULL");
+  if (!b->persist) return fail(SFFT_EINVAL, "not a persistent batch");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(b->persist->epoch, &epoch, sizeof(epoch), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e == cudaSuccess ? SFFT_OK : cuda_fail(e, "set epoch");
 }
 
 int sfft_batch_set_timing(sfft_batch* b, int on) {

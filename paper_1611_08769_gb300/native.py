@@ -92,6 +92,7 @@ SIGNATURES = {
     "sfft_batch_offsets": (c_i32, [c_void_p, P(c_u64), P(c_u64)]),
     "sfft_batch_eval": (c_i32, [c_void_p, c_void_p, c_void_p, c_void_p, c_u64, c_void_p]),
     "sfft_batch_check": (c_i32, [c_void_p, c_void_p]),
+    "sfft_batch_set_epoch": (c_i32, [c_void_p, c_u32, c_void_p]),
     "sfft_batch_eval_host_pipelined": (c_i32, [c_void_p, P(c_void_p), P(c_void_p), c_u32,
                                                P(c_void_p), P(c_void_p), c_void_p, c_u64,
                                                c_void_p]),

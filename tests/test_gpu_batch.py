@@ -191,6 +191,35 @@ def test_persistent_batch_equals_level_by_level(graph):
         assert torch.equal(out, ref)
 
 
+def test_persistent_batch_across_the_epoch_wrap():
+    """The run counter that the gates' done flags are compared with is 32
+    bits; across its wrap the flags are cleared, so that the runs on either
+    side of it still wait for their producers: identical outputs each time."""
+    sp = sf.param_set("P2")
+    reqs = PERSIST_REQS[:4]
+    _, cts, _ = _inputs(sp, reqs)
+    d_in = torch.cat(cts)
+    stream = torch.cuda.Stream()
+    ref_b = sf.Batch(sp, reqs)
+    ref = torch.empty((ref_b.info["outputs"], ref_b.info["ct_words"]), dtype=torch.int32, device="cuda")
+    scr = torch.empty(max(1, ref_b.info["scratch_bytes"] // 4), dtype=torch.int32, device="cuda")
+    with torch.cuda.stream(stream):
+        ref_b.eval(d_in, ref, scr, stream)
+        ref_b.check(stream)
+    pb = sf.Batch(sp, reqs, sf.BATCH_PERSISTENT)
+    pscr = torch.empty(max(1, pb.info["scratch_bytes"] // 4), dtype=torch.int32, device="cuda")
+    pb.set_epoch(0xFFFFFFFD, stream)
+    for _ in range(4):   # epochs 0xFFFFFFFE, 0xFFFFFFFF, then 1 (flags cleared), 2
+        out = torch.full_like(ref, -1)
+        with torch.cuda.stream(stream):
+            pb.eval(d_in, out, pscr, stream)
+            pb.check(stream)
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref)
+    with pytest.raises(sf.SfftError):   # the hook is for persistent batches only
+        ref_b.set_epoch(1, stream)
+
+
 def test_persistent_batch_request_matches_oracle():
     sp = sf.param_set("P2")
     p = gsw.Params(sp.n, sp.ell, sp.m, sp.chi)

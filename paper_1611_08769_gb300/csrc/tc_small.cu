@@ -330,8 +330,9 @@ __device__ __forceinline__ void ld_row(const uint32_t* row, uint32_t W, uint32_t
 //   raw_full[s]   the gate's A' and B' landed (producer's transaction count)
 //   img_full[s]   the B image is written (four converter warps)
 //   epi_done[s]   every epilogue warp wrote its outputs for the gate
-//   slot_free[s]  the gate's outputs left the slot (bulk stores read it), or
-//                 were published (persistent form); the storer arrives
+//   slot_free[s]  the gate's outputs left the slot (bulk stores read it;
+//                 lane 0 of warp 8 arrives), or were published (persistent
+//                 form; the publishing warp arrives)
 //   afull[a]      an item's A stage is written (four expander warps)
 //   afree[a]      the item's MMAs are done (commit)
 //   accfull[c]    an item's MMAs are done (commit)

@@ -154,7 +154,7 @@ typedef struct sfft_plan_info {
   uint32_t noise_bits;          /* bit length of the largest wire noise bound */
   uint32_t noise_ok;            /* bound < q/4 */
   uint32_t gate_kernel;         /* 1 integer-ALU kernel, 2 general tensor-core kernel,
-                                   3 small-ciphertext tensor-core kernel (Ng <= 256) */
+                                   3 small-ciphertext tensor-core kernel (64 <= Ng <= 256) */
   uint32_t tc_columns;          /* tensor-core kernels: digit columns of a product row,
                                    (n+1) ceil(ell / dw) with dw = 11 bits (kernel 2) or
                                    8 bits (kernel 3); 0 otherwise */
@@ -170,7 +170,7 @@ typedef struct sfft_plan_info {
 #define SFFT_PLAN_ALLOW_NOISY 1u   /* build even if the noise bound fails */
 #define SFFT_PLAN_INT_KERNEL 2u    /* integer-ALU gate kernel even where tensor cores apply */
 /* The general tensor-core kernel (B operands expanded by a separate pass)
- * even where the small-ciphertext kernel applies (Ng <= 256); for
+ * even where the small-ciphertext kernel applies (64 <= Ng <= 256); for
  * comparisons. EPARAM where the general kernel does not apply. */
 #define SFFT_PLAN_TC_KERNEL 64u
 /* Circuit variant (not the paper's): the full adder's carry is the sum of its
@@ -408,7 +408,7 @@ typedef struct sfft_request {
  * stream). flags: SFFT_PLAN_* too. */
 #define SFFT_BATCH_NO_GRAPH 4u
 /* Persistent form: every product of the batch runs in ONE launch of the
- * small-ciphertext kernel (Ng <= 256; EPARAM otherwise, and for circuits with
+ * small-ciphertext kernel (64 <= Ng <= 256; EPARAM otherwise, and for circuits with
  * linear gates such as SFFT_PLAN_XCARRY). Its CTAs claim gates in program
  * order; a gate starts once the gates that produced its two operands have
  * stored them and every gate two levels up is done (scratch slots are reused
@@ -503,7 +503,7 @@ void sfft_server_free(sfft_server* sv);
 int sfft_measure_int_peak(uint32_t op, uint32_t iters, double* ops_per_s);
 
 /* Autotuner of the small-ciphertext tensor-core kernel (gate kernel 3, used
- * where Ng <= 256): for each ring depth it can run (gates in flight per CTA,
+ * where 64 <= Ng <= 256): for each ring depth it can run (gates in flight per CTA,
  * 2 to 8 where shared memory allows) it times one level of n_gates half-adder
  * products of random ciphertexts at p with CUDA events on the legacy stream
  * (best of reps; 0 means 3), then keeps the fastest depth for the current
@@ -526,7 +526,7 @@ int sfft_small_kernel_set_slots(uint32_t ell, uint32_t nslots);
  * d_a/d_b/d_out0/d_out1 are arrays of n_gates ciphertexts; codes are 4
  * signed nibbles c0 | c1 << 4 | c2 << 8 | c3 << 12 (two's complement).
  * kernel: 0 automatic, 1 integer ALU, 2 general tensor-core kernel, 3 small-
- * ciphertext tensor-core kernel (Ng <= 256); EPARAM if unsupported.
+ * ciphertext tensor-core kernel (64 <= Ng <= 256); EPARAM if unsupported.
  * Synchronises the stream; SFFT_ETIMEOUT if a bounded device wait ran out. */
 int sfft_gate_level(const sfft_params* p, const uint32_t* d_a, const uint32_t* d_b,
                     uint32_t* d_out0, uint32_t* d_out1, const uint16_t* h_code0,

@@ -265,7 +265,7 @@ int make_persistent(sfft_batch* b) {
   KArgs k = make_args(b->s);
   k.kernel = b->dev.kernel;
   if (gate_kernel_for(k) != KERNEL_SM)
-    return fail(SFFT_EPARAM, "the persistent form runs on the small-ciphertext kernel (Ng <= 256)");
+    return fail(SFFT_EPARAM, "the persistent form runs on the small-ciphertext kernel (64 <= Ng <= 256)");
   const uint32_t levels = (uint32_t)(m.level_off.size() - 1);
   const uint64_t n = m.desc.size();
   if (n >= 0xFFFFFFFFull) return fail(SFFT_EINVAL, "batch too large for the persistent form");

@@ -42,7 +42,7 @@ struct KArgs {
 };
 
 // KERNEL_TC: the general tensor-core kernel (B expanded by a separate pass);
-// KERNEL_SM: the small-ciphertext tensor-core kernel (Ng <= 256, whole gates
+// KERNEL_SM: the small-ciphertext tensor-core kernel (64 <= Ng <= 256, whole gates
 // per CTA, B converted in the kernel).
 constexpr uint32_t KERNEL_AUTO = 0, KERNEL_INT = 1, KERNEL_TC = 2, KERNEL_SM = 3;
 

@@ -1,10 +1,10 @@
-// Gate product for small ciphertexts (Ng <= 256) on the tensor cores.
+// Gate product for small ciphertexts (64 <= Ng <= 256) on the tensor cores.
 //
 // The GSW product K = BitDecomp(A~) B' (Sec. 7: an N x N matrix product per
 // gate) is a {0,1} matrix times the entries of B'. For Ng <= 256 a whole
 // gate fits in one CTA: A~ and B' (Ng^2 / 8 bytes each, 8 KB at n = 1,
 // ell = 128) and the tensor-core image of B' stay in shared memory, and the
-// gate's two 128-row output tiles are multiplied back to back, so B' is
+// gate's one or two 128-row output tiles are multiplied back to back, so B' is
 // converted once per gate inside the kernel (no separate expansion pass)
 // and nothing but the operands and the outputs crosses HBM.
 //

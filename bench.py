@@ -218,13 +218,15 @@ def roofline(params, gate_kernel, gate_ms, launches, gates_timed, tc_columns=0, 
     """Roofline of the dominant kernel (the gate product) from CUDA-event times.
 
     Integer kernel: unit = one product = Ng^2 (n+1) L 32-bit limb additions,
-    against the derived INT32 ALU peak. Tensor-core kernel: unit = one product
-    = the dense contraction 2 Ng Ng C flops (bits x 11-bit digits, C = (n+1)
-    ceil(ell / 11) digit columns per row), against the measured dense bf16
-    rate (kind::f16 runs fp16 at the bf16 rate); the sustained figure, since
-    the kernel runs inside a long step. With the tensor-core path, `expand`
-    gives the B expansion (k_expand_b, HBM-bound) against the measured copy
-    rate from its own events.
+    against the measured add rate. Tensor-core kernel: unit = one product =
+    the scope table's algorithmic contraction, 2 Ng^2 (n+1) ell / 8 flops (the
+    bits times byte digits of B'), against the measured dense bf16 rate
+    (kind::f16 runs fp16 at the bf16 rate); the sustained figure, since the
+    kernel runs inside a long step. The kernel computes the same sums with
+    11-bit digits, fewer flops: `executed` gives its own MMA flops (2 Ng^2 C,
+    C = (n+1) ceil(ell / 11) digit columns per row) against the same peak.
+    With the tensor-core path, `expand` gives the B expansion (k_expand_b,
+    HBM-bound) against the measured copy rate from its own events.
     """
     Ng, L = (params.n + 1) * params.ell, params.ell // 32
     W = (params.n + 1) * L
@@ -254,16 +256,22 @@ def roofline(params, gate_kernel, gate_ms, launches, gates_timed, tc_columns=0, 
     if gate_kernel == 2:
         peaks, src = measured_peaks()
         cols = tc_columns or (params.n + 1) * -(-params.ell // 11)
-        flops = 2.0 * Ng * Ng * cols * gates_timed
-        achieved = flops / sec / 1e12
+        fpp = 2.0 * Ng * Ng * (params.n + 1) * params.ell / 8
+        achieved = fpp * gates_timed / sec / 1e12
+        executed = 2.0 * Ng * Ng * cols * gates_timed / sec / 1e12
         peak = float(peaks["bf16_tflops_sustained"])
         per = TC_DRAM_BYTES_PER_PRODUCT.get((params.n, params.ell))
         traffic = per * gates_timed / max(1, launches) if per else None
         out = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per launch",
                "kernel": "k_gate_tc", "avg_launch_ms": avg_launch_ms,
-               "flops_per_product": 2.0 * Ng * Ng * cols,
-               "peak_source": f"bf16_tflops_sustained {src}"}
+               "flops_per_product": fpp,
+               "flops_definition": "2 Ng^2 (n+1) ell / 8 per product (bits x byte digits of B')",
+               "peak_source": f"bf16_tflops_sustained {src}",
+               "executed": {"achieved": executed, "frac": executed / peak,
+                            "flops_per_product": 2.0 * Ng * Ng * cols,
+                            "definition": "the kernel's MMA flops: 2 Ng^2 x digit columns "
+                                          "(11-bit digits)"}}
         if expand_ms:
             xb = expand_bytes_per_product(params)
             xa = xb * gates_timed / (expand_ms / 1000.0) / 1e9

@@ -33,8 +33,10 @@ def test_reference_line_keys(config, metric):
 
 
 def test_roofline_arithmetic():
-    """The roofline's per-product figures: the contraction's flops and the B
-    expansion's algorithmic bytes at ell 1056 (Ng 2112, 192 digit columns)."""
+    """The roofline's per-product figures at ell 1056 (Ng 2112, 192 digit
+    columns): the scope table's algorithmic flops 2 Ng^2 (n+1) ell / 8 for
+    `achieved`, the kernel's own MMA flops for `executed`, and the B
+    expansion's algorithmic bytes."""
     sys.path.insert(0, ROOT)
     import bench
 
@@ -43,9 +45,13 @@ def test_roofline_arithmetic():
     assert bench.expand_bytes_per_product(P) == 2112 * 2112 // 8 + 17 * 192 * 256
     r = bench.roofline(P, 2, gate_ms=1000.0, launches=1, gates_timed=1000, tc_columns=192,
                        expand_ms=500.0)
-    flops = 2.0 * 2112 * 2112 * 192
+    flops = 2.0 * 2112 * 2112 * 2 * 1056 / 8
     assert r["flops_per_product"] == flops
     assert abs(r["achieved"] - flops * 1000 / 1.0 / 1e12) < 1e-9
+    executed = 2.0 * 2112 * 2112 * 192
+    assert r["executed"]["flops_per_product"] == executed
+    assert abs(r["executed"]["achieved"] - executed * 1000 / 1e12) < 1e-9
+    assert abs(r["frac"] / r["executed"]["frac"] - 264 / 192) < 1e-12
     assert abs(r["expand"]["achieved"] - (2112 * 2112 // 8 + 17 * 192 * 256) * 1000 / 0.5 / 1e9) < 1e-6
     assert r["bound"] == "tensor" and r["expand"]["bound"] == "hbm"
 

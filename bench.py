@@ -18,7 +18,8 @@ adders, a circuit variant: fewer products, its own smaller ell),
 fft8_8bit_nand (8-point 8-bit FFT built from NAND gates only, the paper's
 literal gate construction, at its own smallest ell), fft64_16bit_enctw_xcarry
 (the default workload with encrypted twiddles and the encrypted-operand
-multiplier, exclusive-carry adders), refresh32_noisy (refresh by homomorphic
+multiplier, exclusive-carry adders), fft64_16bit_enctw (the same with the
+paper's adders, ell 1440), refresh32_noisy (refresh by homomorphic
 decryption of 32 ciphertexts at the default workload's ell; metric:
 refreshed ciphertexts/s).
 
@@ -84,6 +85,9 @@ CONFIGS = {
     # encrypted twiddles (encrypted-operand Wallace multiplier), exclusive-carry adders
     "fft64_16bit_enctw_xcarry": dict(kind="fft", N1=64, N2=1, F=16, f=8, lo=-8.0, hi=8.0,
                                      pset="P1", xcarry=True, enc_twiddle=True),
+    # encrypted twiddles with the paper's adders (ell 1440, 288 digit columns)
+    "fft64_16bit_enctw": dict(kind="fft", N1=64, N2=1, F=16, f=8, lo=-8.0, hi=8.0,
+                              pset="P1", enc_twiddle=True),
     # refresh of 32 ciphertexts at the ell of the 64-point 16-bit workload
     "refresh32_noisy": dict(kind="refresh", count=32, pset="P1", ell_of=(64, 1, 16, 8)),
     "batch256_p2": dict(kind="batch", count=256, pset="P2", key_sets=4),

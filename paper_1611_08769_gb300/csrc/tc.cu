@@ -174,6 +174,7 @@ struct TcShape {
   uint32_t btile;            // bytes of one expanded B step (kAtoms atoms of ndpad x 128)
   uint32_t G;                // digit groups of 32 per element (epilogue units)
   uint32_t nacc;             // accumulator slots in tensor memory
+  uint32_t ntb;              // A-tile buffers: 2 (next item's rows prefetched) or 1
   uint32_t smem_bytes;
 };
 
@@ -283,8 +284,10 @@ __global__ void __launch_bounds__(kExpandThreads) k_expand_b(KArgs a, TcShape t)
 //
 // Shared memory (offsets from a 1024-aligned base):
 //   ring    nstages x btile            expanded B slices (bulk copies)
-//   tiles   2 x 128 x W words          A~ rows of two items (double buffer),
-//                                      complemented in place or generated
+//   tiles   ntb x 128 x W words        A~ rows of the items in flight (two,
+//                                      or one where two do not fit beside
+//                                      the ring), complemented in place or
+//                                      generated
 //   ebuf    8 warps x 2 x 32 x 11 words  epilogue staging: a group's A and B
 //                                      words, then its two output blocks
 //   then the mbarriers, the TMEM address slot and the stop flag
@@ -370,7 +373,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gate_tc(KArgs a, TcShape t) {
   const uint32_t W = a.W, L = a.L, NP1 = W / L, G = t.G;
   uint8_t* ring = smem;
   uint32_t* tiles = (uint32_t*)(ring + t.nstages * t.btile);
-  uint32_t* ebuf = tiles + 2 * kTileM * W;
+  uint32_t* ebuf = tiles + t.ntb * kTileM * W;
   uint64_t* bars = (uint64_t*)(ebuf + kEpiWarps * kEbufWords);
   uint64_t* full = bars;          // [8]
   uint64_t* bfree = bars + 8;     // [8]
@@ -457,25 +460,31 @@ __global__ void __launch_bounds__(kThreads, 1) k_gate_tc(KArgs a, TcShape t) {
   } else if (warp == 1) {
     // -------------------------------------------------------------- producer
     if (lane == 0) {
-      // A tile of item jl into buffer jl % 2, once the expanders left item jl - 2
+      // A tile of item jl into buffer jl % ntb, once the expanders left item
+      // jl - ntb
+      const uint32_t ntb = t.ntb;
       auto load_tile = [&](uint32_t jl) -> bool {
         if (gen) return true;
         const ItemInfo it(item_of(jl), Ng, mtiles, kblocks);
-        const uint32_t buf = jl & 1u;
-        if (jl >= 2 && !mbar_wait_flag(&tfree[buf], ((jl - 2) >> 1) & 1u, sflag)) return false;
+        const uint32_t buf = ntb == 2 ? (jl & 1u) : 0u;
+        const uint32_t prev = ntb == 2 ? ((jl - 2) >> 1) : jl - 1;
+        if (jl >= ntb && !mbar_wait_flag(&tfree[buf], prev & 1u, sflag)) return false;
         mbar_expect_tx(&tfull[buf], it.rows * W * 4u);
         bulk_g2s(tiles + buf * kTileM * W, ct_ptr(a, a.desc[it.gate].a) + (uint64_t)it.row0 * W,
                  it.rows * W * 4u, &tfull[buf]);
         return true;
       };
-      bool ok = load_tile(0) && (nloc < 2 || load_tile(1));
+      bool ok = load_tile(0) && (ntb == 1 || nloc < 2 || load_tile(1));
       StepPos p;
       p.start(0, t.nstages, t.kblocks);
       ItemInfo it(item_of(0), Ng, mtiles, kblocks);
       const uint8_t* bx = a.bx + (a.bx_shared ? 0 : (uint64_t)it.gate) * t.kblocks * (uint64_t)t.btile;
       for (uint32_t st = 0; ok && st < steps; st++) {
-        // the next item's tile, halfway through this one
-        if (p.kb == t.kblocks / 2 && p.j >= 1 && p.j + 1 < nloc && !load_tile(p.j + 1)) {
+        // two buffers: the next item's tile, halfway through this one; one
+        // buffer: an item's tile at its first step, once every step of the
+        // previous item is issued (the expanders can then finish it)
+        if (ntb == 2 ? (p.kb == t.kblocks / 2 && p.j >= 1 && p.j + 1 < nloc && !load_tile(p.j + 1))
+                     : (p.kb == 0 && p.j >= 1 && !load_tile(p.j))) {
           ok = false;
           break;
         }
@@ -512,18 +521,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_gate_tc(KArgs a, TcShape t) {
       if (p.j != jcur) {
         if (jcur != 0xFFFFFFFFu) {   // done with the previous item's tile
           __syncwarp();
-          if (lane == 0) mbar_arrive(&tfree[jcur & 1u]);
+          if (lane == 0) mbar_arrive(&tfree[t.ntb == 2 ? (jcur & 1u) : 0u]);
         }
         jcur = p.j;
         const ItemInfo it(item_of(jcur), Ng, mtiles, kblocks);
         rot = it.rot;
-        uint32_t* trow = tiles + ((jcur & 1u) * kTileM + r) * W;
+        const uint32_t tb = t.ntb == 2 ? (jcur & 1u) : 0u, tph = (t.ntb == 2 ? (jcur >> 1) : jcur) & 1u;
+        uint32_t* trow = tiles + (tb * kTileM + r) * W;
         if (gen) {
           const uint64_t gst = stream_out(a.gen_state, a.desc[it.gate].a & SLOT_MASK);
           for (uint32_t w = 0; w < W; w++)
             trow[w] = r < it.rows ? r_word(gst, (uint64_t)(it.row0 + r) * W + w) : 0u;
         } else {
-          if (!__all_sync(0xFFFFFFFFu, mbar_wait_flag(&tfull[jcur & 1u], (jcur >> 1) & 1u, sflag))) {
+          if (!__all_sync(0xFFFFFFFFu, mbar_wait_flag(&tfull[tb], tph, sflag))) {
             ok = false;
             break;
           }
@@ -725,8 +735,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gate_tc(KArgs a, TcShape t) {
 
 namespace {
 
-uint32_t tc_smem_bytes(uint32_t W, uint32_t btile, uint32_t ns) {
-  return 1024u + ns * btile + 2u * (uint32_t)kTileM * W * 4u + kEpiWarps * kEbufWords * 4u +
+uint32_t tc_smem_bytes(uint32_t W, uint32_t btile, uint32_t ns, uint32_t ntb) {
+  return 1024u + ns * btile + ntb * (uint32_t)kTileM * W * 4u + kEpiWarps * kEbufWords * 4u +
          kBars * 8u;
 }
 
@@ -749,14 +759,18 @@ bool make_tc_shape(const KArgs& a, TcShape* t) {
   t->kblocks = (a.Ng + kBK - 1) / kBK;
   t->btile = t->ndpad * 128u * kAtoms;
   t->G = (t->dpad + kGroupDigits - 1) / kGroupDigits;
+  // the deepest ring beside two A-tile buffers; else one buffer (wide rows,
+  // many digit columns: the next item's rows then load when it starts)
   t->nstages = 0;
-  for (uint32_t ns = 8; ns >= kAStages; ns--)
-    if (tc_smem_bytes(a.W, t->btile, ns) <= kMaxSmem) {
-      t->nstages = ns;
-      break;
-    }
+  for (t->ntb = 2; t->ntb >= 1 && !t->nstages; t->ntb--)
+    for (uint32_t ns = 8; ns >= kAStages; ns--)
+      if (tc_smem_bytes(a.W, t->btile, ns, t->ntb) <= kMaxSmem) {
+        t->nstages = ns;
+        break;
+      }
   if (!t->nstages) return false;
-  t->smem_bytes = tc_smem_bytes(a.W, t->btile, t->nstages);
+  t->ntb++;   // the loop stepped past the count that fit
+  t->smem_bytes = tc_smem_bytes(a.W, t->btile, t->nstages, t->ntb);
   return true;
 }
 

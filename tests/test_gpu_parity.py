@@ -39,7 +39,8 @@ CODES = {"XOR": (0, 1, 1, -2), "AND": (0, 0, 0, 1), "OR": (0, 1, 1, -1), "NAND":
 GATE_CASES = [(1, 32, sf.KERNEL_INT), (1, 128, sf.KERNEL_INT), (1, 224, sf.KERNEL_INT),
               (2, 64, sf.KERNEL_INT), (1, 1056, sf.KERNEL_INT),
               (1, 128, sf.KERNEL_TC), (1, 224, sf.KERNEL_TC), (2, 64, sf.KERNEL_TC),
-              (1, 1056, sf.KERNEL_TC), (1, 1216, sf.KERNEL_TC), (1, 1984, sf.KERNEL_AUTO)]
+              (1, 1056, sf.KERNEL_TC), (1, 1216, sf.KERNEL_TC), (1, 1440, sf.KERNEL_TC),
+              (1, 1984, sf.KERNEL_AUTO)]
 
 
 @pytest.mark.parametrize("n,ell,kernel", GATE_CASES)
@@ -48,8 +49,9 @@ def test_gate_level_matches_oracle(n, ell, kernel):
     sp = sf.Params(n, ell)
     shape = (p.Ng, n + 1, p.L)
     # ell 1056 and 1216: 24 gates of 17 and 19 tiles, more than one tile per CTA of the
-    # persistent kernel (152 SMs), so both accumulator slots are compared
-    G = 37 if ell <= 256 else (24 if ell <= 1216 else 3)
+    # persistent kernel (152 SMs), so both accumulator slots are compared; ell 1440: 8 gates
+    # of 23 tiles, one A-tile buffer reloaded between a CTA's items (288 digit columns)
+    G = 37 if ell <= 256 else (24 if ell <= 1216 else (8 if ell <= 1440 else 3))
     rng = np.random.default_rng(ell + n)
     A = rng.integers(0, 2**32, size=(G,) + shape, dtype=np.uint64).astype(np.uint32)
     B = rng.integers(0, 2**32, size=(G,) + shape, dtype=np.uint64).astype(np.uint32)

@@ -163,13 +163,14 @@ PERSIST_REQS = [(16, 1, 16, 8), (8, 1, 8, 4), (4, 4, 8, 3), (32, 1, 16, 8), (8, 
                 (64, 1, 16, 8), (4, 1, 6, 2)]
 
 
-@pytest.mark.parametrize("graph", [True, False])
-def test_persistent_batch_equals_level_by_level(graph):
+@pytest.mark.parametrize("pset,graph", [("P2", True), ("P2", False), ("P0", True)])
+def test_persistent_batch_equals_level_by_level(pset, graph):
     """One persistent launch across all levels (gates claimed in program
     order, levels overlapping by one) against the level-by-level batch on the
     same inputs: identical ciphertexts, on three evaluations in a row (the
-    epochs of the gates' done flags advance)."""
-    sp = sf.param_set("P2")
+    epochs of the gates' done flags advance); at ell 128 and at the toy
+    parameters (Ng 64)."""
+    sp = sf.param_set(pset)
     _, cts, _ = _inputs(sp, PERSIST_REQS)
     d_in = torch.cat(cts)
     stream = torch.cuda.Stream()

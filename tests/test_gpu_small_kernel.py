@@ -71,7 +71,7 @@ def _unpack(code):
 
 @pytest.mark.parametrize("n,ell,G", [(1, 128, 461), (1, 64, 333), (1, 96, 170), (2, 64, 310),
                                      (3, 32, 157), (1, 128, 1), (1, 128, 153),
-                                     (1, 32, 401), (2, 32, 229)])
+                                     (1, 32, 401), (2, 32, 229), (3, 64, 211), (7, 32, 173)])
 def test_small_kernel_gate_level_matches_oracle(n, ell, G):
     p, A, B, code0, code1, flags, got0, got1 = _run_level(n, ell, G, sf.KERNEL_SM, 7 * ell + n + G)
     for g in range(G):

@@ -253,3 +253,54 @@ def test_persistent_batch_rejects_unsupported_forms():
         sf.Batch(sf.param_set("P1", 224), [(8, 1, 8, 4)], sf.BATCH_PERSISTENT)
     with pytest.raises(sf.SfftError):   # linear (exclusive-carry) gates
         sf.Batch(sf.param_set("P2"), [(8, 1, 8, 4)], sf.BATCH_PERSISTENT | sf.PLAN_XCARRY)
+
+
+def test_full_c4_batch_equals_plain_path_persistent_form_and_oracle():
+    """The 256-request batch workload (the bench's batch256_p2 inputs: N 16 to
+    128, 16- and 24-bit words, four key sets) evaluated as one graph-replayed
+    batch: every request's ciphertexts equal its own plan's (the plain path)
+    and the persistent form's; the smallest request also equals the oracle's
+    encrypted evaluation."""
+    from synthetic import batch_requests
+    sp = sf.param_set("P2")
+    p = gsw.Params(sp.n, sp.ell, sp.m, sp.chi)
+    cw = sf.ct_words(sp)
+    reqs = batch_requests(count=256, seed=4, key_sets=4)
+    dims = [(r.N1, r.N2, r.F, r.f) for r in reqs]
+    pubs = {ks: torch.from_numpy(sf.keygen(sp, 1000 + ks).public().view(np.int32)).cuda()
+            for ks in range(4)}
+    b = sf.Batch(sp, dims)
+    d_in = torch.empty((b.info["inputs"], cw), dtype=torch.int32, device="cuda")
+    for i, r in enumerate(reqs):
+        n = r.N1 * r.N2 * 2 * r.F
+        sf.encrypt_bits_device(sp, pubs[r.key_set], r.re, r.im, r.F, r.f, r.seed,
+                               d_in[b.in_off[i]:b.in_off[i] + n])
+    out = torch.empty((b.info["outputs"], cw), dtype=torch.int32, device="cuda")
+    pb = sf.Batch(sp, dims, sf.BATCH_PERSISTENT)
+    assert list(pb.in_off) == list(b.in_off) and list(pb.out_off) == list(b.out_off)
+    scr = torch.empty(max(b.info["scratch_bytes"], pb.info["scratch_bytes"]) // 4 + 1,
+                      dtype=torch.int32, device="cuda")
+    pout = torch.full_like(out, -1)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        b.eval(d_in, out, scr, stream)
+        b.check(stream)
+        pb.eval(d_in, pout, scr, stream)
+        pb.check(stream)
+    torch.cuda.synchronize()
+    assert torch.equal(pout, out)
+    for i, r in enumerate(reqs):
+        n = r.N1 * r.N2 * 2 * r.F
+        want = _single(sp, dims[i], d_in[b.in_off[i]:b.in_off[i] + n])
+        assert torch.equal(out[b.out_off[i]:b.out_off[i] + len(want)], want), (i, dims[i])
+    i = min(range(len(reqs)), key=lambda k: (reqs[k].N1 * reqs[k].F, k))
+    r = reqs[i]
+    ko = gsw.Keys(p, 1000 + r.key_set)
+    ins = []
+    for k in range(r.N1):
+        for part, x in enumerate((r.re[k], r.im[k])):
+            for bit_i, bit in enumerate(fx.to_bits(fx.quantize(x, r.F, r.f), r.F)):
+                ins.append(gsw.encrypt(ko, bit, r.seed, (2 * k + part) * r.F + bit_i))
+    want = evaluate.eval_encrypted(circuit.fft_circuit(r.N1, 1, r.F, r.f), p, ins)
+    got = out[b.out_off[i]:b.out_off[i] + len(want)].cpu().numpy().view(np.uint32)
+    assert np.array_equal(got.reshape(want.shape), want)

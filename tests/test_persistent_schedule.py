@@ -196,3 +196,19 @@ def test_persistent_listing_computes_the_circuit(N1, N2, F, f):
     got = plain_outputs(gates, bits, len(want))
     assert len(got) > 0.9 * len(want)
     assert all(got[i] == want[i] for i in got)
+
+
+def test_listing_rejects_bad_arguments():
+    import ctypes
+    p = sf.param_set("P2")
+    n = ctypes.c_uint64(0)
+    lib = sf.lib()
+    assert lib.sfft_program_gates(ctypes.byref(p), 8, 1, 8, 4, 0, None, 0, None) != 0   # no count
+    assert lib.sfft_program_gates(ctypes.byref(p), 8, 1, 8, 4, 0, None, 0, ctypes.byref(n)) == 0
+    buf = np.zeros(n.value - 1, dtype=sf.GATE_RECORD)
+    assert lib.sfft_program_gates(ctypes.byref(p), 8, 1, 8, 4, 0, ctypes.c_void_p(buf.ctypes.data),
+                                  n.value - 1, ctypes.byref(n)) != 0                      # short buffer
+    with pytest.raises(sf.SfftError):   # linear (exclusive-carry) gates have no persistent schedule
+        sf.program_gates(p, 8, 1, 8, 4, sf.BATCH_PERSISTENT | sf.PLAN_XCARRY)
+    with pytest.raises(sf.SfftError):   # not a power-of-two FFT
+        sf.program_gates(p, 6, 1, 8, 4)
